@@ -8,9 +8,14 @@
       bbar_s = A_s^T (A_s A_s^T)^{-1} b_s,
   and the local update is x_s = (1/rho) Abar_s d_s + bbar_s.
 
-Reading (the paper gives no tolerance): a pivot is accepted when its
+Readings (the paper gives no tolerance): a pivot is accepted when its
 magnitude exceeds 1e-12 * max|A_s|; a reduced zero row is inconsistent when
-|rhs| exceeds 1e-9 * max(1, max|b_s|).
+|rhs| exceeds 1e-9 * max(1, max|b_s|).  Section III-B takes A_s of full row
+rank and applies row reduction only when it is not: so the row reduction
+always decides rank and consistency, and its rows replace A_s only for a
+rank-deficient component.  (Reducing a full-rank block anyway can pivot on a
+tiny impedance entry and leave a badly conditioned A_s A_s^T -- the
+operators are the same in exact arithmetic, not in FP64.)
 """
 from __future__ import annotations
 
@@ -83,10 +88,13 @@ class Precomputed:
 
 
 def precompute(model) -> Precomputed:
-    """Algorithm 1, precomputation: row reduction then Eq. (closed_2) per component."""
+    """Algorithm 1, precomputation: row reduction (when A_s is rank deficient)
+    then Eq. (closed_2) per component."""
     Ab, bb, Ar, br, mr = [], [], [], [], []
     for comp in model.comps:
         A_r, b_r, _ = rref(comp.A, comp.b)
+        if A_r.shape[0] == comp.A.shape[0]:      # already full row rank
+            A_r, b_r = np.array(comp.A, dtype=np.float64), np.array(comp.b, dtype=np.float64)
         Abar, bbar = closed_form(A_r, b_r)
         Ab.append(Abar); bb.append(bbar); Ar.append(A_r); br.append(b_r)
         mr.append(A_r.shape[0])

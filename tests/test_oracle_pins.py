@@ -437,3 +437,37 @@ def test_paper_table3_component_identity():
     S = g["table3"]["IEEE8500"]["S"]
     assert 0 <= t4["n_sum"] / S - t4["n_mean"] < 0.01
     assert 0 <= t4["m_sum"] / S - t4["m_mean"] < 0.01
+
+
+def test_precompute_accurate_on_short_lines():
+    """8500-class short lines give tiny per-unit impedances; the operators
+    must still equal the SVD null-space projector and minimum-norm solution
+    to FP64 accuracy (the library and oracle are compared at 1e-10)."""
+    f = F.feeder_8500(1, n_bus=600)
+    m = OM.build_feeder(f)
+    pre = OP.precompute(m)
+    for s, comp in enumerate(m.comps):
+        if comp.kind != OM.KIND_LINE:
+            continue
+        A = comp.A
+        U, S, Vt = np.linalg.svd(A)
+        N = Vt[A.shape[0]:].T
+        np.testing.assert_allclose(-pre.Abar[s], N @ N.T, atol=1e-12)
+        np.testing.assert_allclose(pre.bbar[s], np.linalg.pinv(A) @ comp.b, atol=1e-12)
+
+
+def test_rank_deficient_component_uses_row_reduction():
+    """A bus phase with nothing attached and no shunt gives a zero balance
+    row (0 = 0): row reduction drops it and the operators still match SVD."""
+    buses = np.zeros(2, F.BUS_DTYPE); buses["phases"] = [7, 7]
+    buses["w_lo"] = 0.9; buses["w_hi"] = 1.1
+    lines = np.zeros(1, F.LINE_DTYPE); lines["from_bus"] = 0; lines["to_bus"] = 1
+    lines["phases"] = 1; lines["in_service"] = 1; lines["r"] = 0.01; lines["x"] = 0.02; lines["tap"] = 1
+    lines["p_lo"] = -1; lines["p_hi"] = 1; lines["q_lo"] = -1; lines["q_hi"] = 1
+    m = OM.build(buses, lines, np.zeros(0, F.GEN_DTYPE), np.zeros(0, F.LOAD_DTYPE))
+    pre = OP.precompute(m)
+    bus1 = m.comps[1]
+    assert bus1.A.shape[0] == 6 and pre.m_red[1] == 2
+    U, S, Vt = np.linalg.svd(bus1.A)
+    N = Vt[2:].T
+    np.testing.assert_allclose(-pre.Abar[1], N @ N.T, atol=1e-12)
