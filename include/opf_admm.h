@@ -1,0 +1,247 @@
+/*
+ * opf_admm.h -- C ABI of the B300 (sm_103a) solver-free componentwise ADMM
+ * for linearized multi-phase optimal power flow in distribution feeders.
+ *
+ * Method (arxiv 2501.08293):
+ *   model       Section II-A, Eqs. (operational), (balance_eqns),
+ *               (volt_load_model) VDLM-1..10, (power_flow_eqns), objective
+ *               sum of pg; abstract LP of Eq. (LP_model).
+ *   decompose   Eq. (OurModel): equality rows stay in the components
+ *               (bus, line, load, generator), every bound moves to the
+ *               global vector x.
+ *   precompute  Section IV-B row reduction and Eq. (closed_2):
+ *               Abar_s = A_s^T (A_s A_s^T)^{-1} A_s - I,
+ *               bbar_s = A_s^T (A_s A_s^T)^{-1} b_s.
+ *   iterate     Algorithm 1: global update Eq. (global_sparse), local update
+ *               Eq. (closed_2), dual update Eq. (ADMM-3); residuals and
+ *               stopping test of Eq. (termination).
+ *
+ * Conventions
+ *   - Every function returns an int32 status (opf_status); nothing throws or
+ *     aborts across the ABI.  opf_last_error() gives a message for the last
+ *     failing call on the calling thread.
+ *   - Input records are read during the call and copied; the caller keeps
+ *     ownership of every buffer it passes.
+ *   - A problem handle owns its host data, its pinned host buffers and (when
+ *     it allocated them itself) its device buffers.  One handle must not be
+ *     used by two threads at once; distinct handles are independent.
+ *   - "stream" arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).  Device work is enqueued on that stream.
+ *   - Per-unit quantities throughout.  Phase sets are bit masks a=1, b=2,
+ *     c=4; per-phase arrays are indexed 0..2 = a, b, c and entries of absent
+ *     phases are ignored on input and written as NaN on output.
+ *   - Bounds may be +-INFINITY (a variable counts as bounded only when both
+ *     bounds are finite, which matters for the initial point).
+ */
+#ifndef OPF_ADMM_H
+#define OPF_ADMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OPF_ABI_VERSION 1
+
+/* ------------------------------------------------------------ status codes */
+enum {
+    OPF_OK = 0,                 /* converged (or finished as asked)              */
+    OPF_NOT_CONVERGED = 1,      /* max_iter reached; the iterate is still valid  */
+    OPF_ERR_INVALID_ARG = -1,   /* bad pointer, size, index, phase set or value  */
+    OPF_ERR_INCONSISTENT = -2,  /* row reduction met 0 = b, b != 0 (Sec. IV-B)   */
+    OPF_ERR_NUMERIC = -3,       /* NaN / Inf in the residuals or a singular Gram */
+    OPF_ERR_OOM = -4,           /* host or device allocation failed              */
+    OPF_ERR_CUDA = -5,          /* a CUDA runtime call failed                    */
+    OPF_ERR_TIMEOUT = -6,       /* a bounded device wait gave up                 */
+    OPF_ERR_STATE = -7          /* call out of order (e.g. solve before upload)  */
+};
+
+/* ----------------------------------------------------------- input records
+ * Layouts are fixed (sizes 104, 376, 128, 104 bytes); opf_record_size()
+ * returns them so bindings can check their own copies.                      */
+
+/* Bus i: squared voltage magnitude bounds (Eq. operational) and shunt
+ * conductance / susceptance g^sh, b^sh (Eq. balance_eqns).                  */
+typedef struct opf_bus {
+    uint8_t phases;
+    uint8_t _pad[7];
+    double w_lo[3], w_hi[3];
+    double g_sh[3], b_sh[3];
+} opf_bus;
+
+/* Line e from bus i (from_bus) to bus j (to_bus), Eq. (power_flow_eqns):
+ * r, x are 3x3 row-major over phases a, b, c (only the rows/columns of the
+ * line's phases are read -- the M^p, M^q sub-block); g_fr, b_fr = g^s_eij,
+ * b^s_eij (from end), g_to, b_to = g^s_eji, b^s_eji (to end); tap = tau_e;
+ * flow bounds apply to both p_eij and p_eji (and q).  Lines with
+ * in_service == 0 are left out of the model.                                */
+typedef struct opf_line {
+    int32_t from_bus, to_bus;
+    uint8_t phases, in_service;
+    uint8_t _pad[6];
+    double r[9], x[9];
+    double g_fr[3], b_fr[3], g_to[3], b_to[3];
+    double tap[3];
+    double p_lo[3], p_hi[3], q_lo[3], q_hi[3];
+} opf_line;
+
+/* Generator k at bus: bounds on pg, qg (Eq. operational) and the linear cost
+ * of pg per phase (the paper's objective is cost = 1).                      */
+typedef struct opf_gen {
+    int32_t bus;
+    uint8_t phases;
+    uint8_t _pad[3];
+    double pg_lo[3], pg_hi[3], qg_lo[3], qg_hi[3];
+    double cost[3];
+} opf_gen;
+
+/* Load l at bus, Eq. (volt_load_model): conn 0 = wye (VDLM-5), 1 = delta
+ * (VDLM-6..10; three-phase only, else OPF_ERR_INVALID_ARG); a, b, alpha,
+ * beta as in VDLM-1/2.                                                      */
+typedef struct opf_load {
+    int32_t bus;
+    uint8_t phases, conn;
+    uint8_t _pad[2];
+    double a[3], b[3], alpha[3], beta[3];
+} opf_load;
+
+/* ------------------------------------------------------------- parameters */
+enum { OPF_CRIT_ABS = 0, OPF_CRIT_REL = 1, OPF_CRIT_BOTH = 2, OPF_CRIT_NEVER = 3 };
+enum { OPF_FP64 = 0, OPF_FP32 = 1 };
+enum { OPF_RES_PAPER = 0 };
+enum { OPF_ENGINE_AUTO = 0, OPF_ENGINE_GRAPH = 1, OPF_ENGINE_HOSTLOOP = 2 };
+
+/* Solve parameters.  criterion ABS: pres <= eps_abs_prim and dres <=
+ * eps_abs_dual; REL: the paper's relative test of Eq. (termination) with
+ * eps_rel; BOTH: both; NEVER: run exactly max_iter iterations.  Residuals
+ * and the test are evaluated every check_every iterations (the stop can be
+ * up to check_every-1 iterations late).  warm_start 0 restarts from the
+ * initial point of Section V-A; 1 continues from the handle's current state
+ * (iteration counter included).  engine GRAPH runs the whole loop as one
+ * CUDA graph with a device-side while node; HOSTLOOP checks from the host.  */
+typedef struct opf_params {
+    double rho;
+    double eps_abs_prim, eps_abs_dual, eps_rel;
+    int32_t criterion;
+    int32_t max_iter;
+    int32_t check_every;
+    int32_t precision;
+    int32_t residual_form;
+    int32_t warm_start;
+    int32_t engine;
+    int32_t _reserved;
+} opf_params;
+
+/* Result of a solve.  iters counts all iterations since the last cold
+ * start; first_rel_iter is the first checked iteration at which the paper's
+ * relative test held (-1 if never); seconds is host wall time of the call. */
+typedef struct opf_info {
+    int32_t status;
+    int32_t iters;
+    int32_t first_rel_iter;
+    int32_t _pad;
+    double pres, dres, eps_prim, eps_dual;
+    double objective;
+    double seconds;
+} opf_info;
+
+/* Sizes of a built problem. */
+typedef struct opf_dims {
+    int32_t n_global;        /* n: global variables (Eq. LP_model column count) */
+    int32_t n_local;         /* sum_s n_s: stacked local copies                 */
+    int32_t n_comp;          /* S                                              */
+    int32_t n_rows;          /* sum_s m_s before row reduction                  */
+    int32_t n_rows_reduced;  /* sum_s m_s after row reduction                   */
+    int32_t max_n;           /* max_s n_s                                      */
+    int32_t n_tiles;         /* warp tiles of the local-update kernel           */
+    int32_t _pad;
+    int64_t sum_n2;          /* sum_s n_s^2 (dense operator entries)            */
+    int64_t device_bytes;    /* bytes opf_problem_upload needs                  */
+} opf_dims;
+
+typedef struct opf_problem opf_problem;
+
+/* ------------------------------------------------------------ entry points */
+
+int32_t opf_abi_version(void);
+/* which: 0 bus, 1 line, 2 gen, 3 load, 4 params, 5 info, 6 dims; else 0.   */
+size_t opf_record_size(int32_t which);
+const char* opf_status_string(int32_t status);
+const char* opf_last_error(void);
+void opf_params_default(opf_params* p);   /* rho 100, ABS 1e-4, eps_rel 1e-3 */
+
+/* Build the model of Section II-A from the records, split it into fine
+ * components (Eq. OurModel), row-reduce each [A_s | b_s] and precompute the
+ * closed-form operators of Eq. (closed_2) in FP64 on the host, then pack
+ * them for the device.  No device memory is touched.
+ * Errors: INVALID_ARG (indices, phases, delta on < 3 phases, lo > hi, NaN),
+ * INCONSISTENT (a component's rows have no solution), OOM.                  */
+int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus,
+                           const opf_line* lines, int32_t n_line,
+                           const opf_gen* gens, int32_t n_gen,
+                           const opf_load* loads, int32_t n_load,
+                           opf_problem** out);
+
+int32_t opf_get_dims(const opf_problem* p, opf_dims* dims);
+
+/* Copy the packed problem to the current CUDA device on `stream`.  With
+ * device_arena != NULL the handle carves all its device buffers out of that
+ * caller-owned region (>= dims.device_bytes bytes, 256-byte aligned; it must
+ * outlive the handle); with NULL it allocates with cudaMallocAsync on
+ * `stream` and frees in opf_destroy.  Leaves the state at the initial point
+ * of Section V-A.                                                           */
+int32_t opf_problem_upload(opf_problem* p, void* device_arena, size_t arena_bytes, void* stream);
+
+/* Run Algorithm 1 on the device until params->criterion holds or
+ * params->max_iter iterations have run.  Blocks until the result is known.
+ * Returns OPF_OK, OPF_NOT_CONVERGED or an error; *info (may be NULL) gets
+ * the residuals of the last check and the objective c^T x in FP64.         */
+int32_t opf_admm_solve(opf_problem* p, const opf_params* params, void* stream, opf_info* info);
+
+/* Current iterate in canonical order, copied to caller host buffers (any of
+ * them may be NULL): x_global[n_global] (the global vector x), x_local and
+ * lam[n_local] (stacked x_s and lambda_s, components in canonical order).
+ * Canonical orders: globals = gens (pg, qg per phase), buses (w), loads (pb,
+ * qb, pd, qd), in-service lines (p_ij, q_ij, p_ji, q_ji); components =
+ * buses, in-service lines, loads, generators; bus locals = w, then for each
+ * in-service line touching the bus (line order) the flow leaving the bus
+ * (p, q), then its loads' (pb, qb), then its generators' (pg, qg); line
+ * locals = p_ij, q_ij, p_ji, q_ji, w_i, w_j; load locals = pb, qb, pd, qd,
+ * w; generator locals = pg, qg (each block over the element's phases).    */
+int32_t opf_get_state(const opf_problem* p, double* x_global, double* x_local, double* lam,
+                      void* stream);
+
+/* Overwrite the local iterate and duals (canonical order, host buffers) for
+ * a warm start; the next solve with warm_start = 1 continues from them.    */
+int32_t opf_set_state(opf_problem* p, const double* x_local, const double* lam, void* stream);
+
+/* Structure in canonical order (any pointer may be NULL): comp_ptr[S+1]
+ * offsets of each component's locals, comp_kind[S] (0 bus, 1 line, 2 load,
+ * 3 gen), comp_index[S] (index in the input records), gidx[n_local] (global
+ * index of each local copy, i.e. B_s), m_reduced[S] (rows kept by row
+ * reduction).                                                               */
+int32_t opf_get_structure(const opf_problem* p, int32_t* comp_ptr, int32_t* comp_kind,
+                          int32_t* comp_index, int32_t* gidx, int32_t* m_reduced);
+
+/* Unscatter the global vector into per-element arrays (host, caller-owned,
+ * 3 doubles per element, NaN for absent phases and out-of-service lines):
+ * w[n_bus*3]; pg, qg[n_gen*3]; p_ij, q_ij, p_ji, q_ji[n_line*3];
+ * pd, qd, pb, qb[n_load*3].  Any pointer may be NULL.                      */
+int32_t opf_get_solution(const opf_problem* p, double* w, double* pg, double* qg,
+                         double* p_ij, double* q_ij, double* p_ji, double* q_ji,
+                         double* pd, double* qd, double* pb, double* qb, void* stream);
+
+/* Host copy of component s's precomputed operator (canonical component
+ * order): P[n_s*n_s] row-major = -Abar_s of Eq. (closed_2) (symmetric) and
+ * bbar[n_s]; either pointer may be NULL.  *n_s (may be NULL) gets n_s.
+ * No device work; valid right after opf_problem_create.                   */
+int32_t opf_get_operator(const opf_problem* p, int32_t s, double* P, double* bbar, int32_t* n_s);
+
+void opf_destroy(opf_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPF_ADMM_H */

@@ -1,0 +1,240 @@
+// extern "C" entry points of libopf_admm (declared in include/opf_admm.h).
+// Every call converts internal exceptions into status codes and records a
+// message retrievable with opf_last_error() on the same thread.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "problem.hpp"
+
+namespace opf {
+size_t device_bytes(const opf_problem* p);
+void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s);
+int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_info* info);
+void device_get_state(const opf_problem* p, double* xg, double* xl, double* lam, cudaStream_t s);
+void device_set_state(opf_problem* p, const double* xl, const double* lam, cudaStream_t s);
+void device_free(opf_problem* p);
+}  // namespace opf
+
+namespace {
+thread_local std::string g_last_error;
+
+template <typename F>
+int32_t guarded(F&& f) {
+    try {
+        g_last_error.clear();
+        return f();
+    } catch (const opf::Error& e) {
+        g_last_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return OPF_ERR_OOM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return OPF_ERR_INVALID_ARG;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return OPF_ERR_INVALID_ARG;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+int32_t opf_abi_version(void) { return OPF_ABI_VERSION; }
+
+size_t opf_record_size(int32_t which) {
+    switch (which) {
+        case 0: return sizeof(opf_bus);
+        case 1: return sizeof(opf_line);
+        case 2: return sizeof(opf_gen);
+        case 3: return sizeof(opf_load);
+        case 4: return sizeof(opf_params);
+        case 5: return sizeof(opf_info);
+        case 6: return sizeof(opf_dims);
+        default: return 0;
+    }
+}
+
+const char* opf_status_string(int32_t s) {
+    switch (s) {
+        case OPF_OK: return "OPF_OK";
+        case OPF_NOT_CONVERGED: return "OPF_NOT_CONVERGED";
+        case OPF_ERR_INVALID_ARG: return "OPF_ERR_INVALID_ARG";
+        case OPF_ERR_INCONSISTENT: return "OPF_ERR_INCONSISTENT";
+        case OPF_ERR_NUMERIC: return "OPF_ERR_NUMERIC";
+        case OPF_ERR_OOM: return "OPF_ERR_OOM";
+        case OPF_ERR_CUDA: return "OPF_ERR_CUDA";
+        case OPF_ERR_TIMEOUT: return "OPF_ERR_TIMEOUT";
+        case OPF_ERR_STATE: return "OPF_ERR_STATE";
+        default: return "OPF_UNKNOWN_STATUS";
+    }
+}
+
+const char* opf_last_error(void) { return g_last_error.c_str(); }
+
+void opf_params_default(opf_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->rho = 100.0;
+    p->eps_abs_prim = 1e-4;
+    p->eps_abs_dual = 1e-4;
+    p->eps_rel = 1e-3;
+    p->criterion = OPF_CRIT_ABS;
+    p->max_iter = 1000000;
+    p->check_every = 50;
+    p->precision = OPF_FP64;
+    p->residual_form = OPF_RES_PAPER;
+    p->warm_start = 0;
+    p->engine = OPF_ENGINE_AUTO;
+}
+
+int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
+                           const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
+                           opf_problem** out) {
+    return guarded([&]() -> int32_t {
+        if (!out) throw opf::Error(OPF_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        opf_problem* p = new opf_problem();
+        try {
+            p->model = opf::build_model(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load);
+            p->ops.reserve(p->model.comps.size());
+            p->canon_comp_ptr.assign(1, 0);
+            for (const auto& c : p->model.comps) {
+                p->ops.push_back(opf::make_operator(c));
+                p->m_reduced.push_back(p->ops.back().m_reduced);
+                p->canon_comp_ptr.push_back(p->canon_comp_ptr.back() + c.n());
+                p->n_rows += c.m;
+                p->n_rows_reduced += p->ops.back().m_reduced;
+            }
+            p->pk = opf::pack(p->model, p->ops);
+        } catch (...) {
+            delete p;
+            throw;
+        }
+        *out = p;
+        return OPF_OK;
+    });
+}
+
+int32_t opf_get_dims(const opf_problem* p, opf_dims* d) {
+    return guarded([&]() -> int32_t {
+        if (!p || !d) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        std::memset(d, 0, sizeof(*d));
+        d->n_global = p->pk.ng;
+        d->n_local = p->pk.nl;
+        d->n_comp = p->pk.ncomp;
+        d->n_rows = (int32_t)p->n_rows;
+        d->n_rows_reduced = (int32_t)p->n_rows_reduced;
+        d->max_n = p->pk.max_n;
+        d->n_tiles = (int32_t)p->pk.tiles.size();
+        d->sum_n2 = p->pk.sum_n2;
+        d->device_bytes = (int64_t)opf::device_bytes(p);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_problem_upload(opf_problem* p, void* arena, size_t arena_bytes, void* stream) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        opf::device_upload(p, arena, arena_bytes, (cudaStream_t)stream);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_admm_solve(opf_problem* p, const opf_params* prm, void* stream, opf_info* info) {
+    return guarded([&]() -> int32_t {
+        if (!p || !prm) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "solve before upload");
+        if (!(prm->rho > 0.0) || !std::isfinite(prm->rho)) throw opf::Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
+        if (prm->check_every < 1 || prm->check_every > 4096) throw opf::Error(OPF_ERR_INVALID_ARG, "check_every out of [1, 4096]");
+        if (prm->max_iter < 0) throw opf::Error(OPF_ERR_INVALID_ARG, "max_iter < 0");
+        if (prm->criterion < 0 || prm->criterion > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad criterion");
+        if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
+        if (prm->residual_form != OPF_RES_PAPER) throw opf::Error(OPF_ERR_INVALID_ARG, "unsupported residual form");
+        if (prm->engine < 0 || prm->engine > 2) throw opf::Error(OPF_ERR_INVALID_ARG, "bad engine");
+        return opf::device_solve(p, *prm, (cudaStream_t)stream, info);
+    });
+}
+
+int32_t opf_get_state(const opf_problem* p, double* xg, double* xl, double* lam, void* stream) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "no device state");
+        opf::device_get_state(p, xg, xl, lam, (cudaStream_t)stream);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_set_state(opf_problem* p, const double* xl, const double* lam, void* stream) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "no device state");
+        opf::device_set_state(p, xl, lam, (cudaStream_t)stream);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_get_structure(const opf_problem* p, int32_t* comp_ptr, int32_t* comp_kind, int32_t* comp_index,
+                          int32_t* gidx, int32_t* m_reduced) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        const int S = (int)p->model.comps.size();
+        if (comp_ptr) std::memcpy(comp_ptr, p->canon_comp_ptr.data(), (S + 1) * sizeof(int32_t));
+        for (int s = 0; s < S; ++s) {
+            const auto& c = p->model.comps[s];
+            if (comp_kind) comp_kind[s] = c.kind;
+            if (comp_index) comp_index[s] = c.index;
+            if (m_reduced) m_reduced[s] = p->m_reduced[s];
+            if (gidx)
+                for (int r = 0; r < c.n(); ++r) gidx[p->canon_comp_ptr[s] + r] = c.gvars[r];
+        }
+        return OPF_OK;
+    });
+}
+
+int32_t opf_get_solution(const opf_problem* p, double* w, double* pg, double* qg, double* p_ij, double* q_ij,
+                         double* p_ji, double* q_ji, double* pd, double* qd, double* pb, double* qb, void* stream) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "no device state");
+        std::vector<double> x(p->pk.ng);
+        opf::device_get_state(p, x.data(), nullptr, nullptr, (cudaStream_t)stream);
+        const opf::Model& M = p->model;
+        auto scat = [&](double* dst, const std::vector<int32_t>& idx) {
+            if (!dst) return;
+            for (size_t k = 0; k < idx.size(); ++k) dst[k] = idx[k] >= 0 ? x[idx[k]] : NAN;
+        };
+        scat(w, M.w_idx); scat(pg, M.pg_idx); scat(qg, M.qg_idx);
+        scat(p_ij, M.pij_idx); scat(q_ij, M.qij_idx); scat(p_ji, M.pji_idx); scat(q_ji, M.qji_idx);
+        scat(pd, M.pd_idx); scat(qd, M.qd_idx); scat(pb, M.pb_idx); scat(qb, M.qb_idx);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_get_operator(const opf_problem* p, int32_t s, double* P, double* bbar, int32_t* n_s) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        if (s < 0 || s >= (int32_t)p->ops.size()) throw opf::Error(OPF_ERR_INVALID_ARG, "component index out of range");
+        const opf::Operator& op = p->ops[s];
+        if (n_s) *n_s = op.n;
+        if (P) std::memcpy(P, op.P.data(), op.P.size() * sizeof(double));
+        if (bbar) std::memcpy(bbar, op.bbar.data(), op.bbar.size() * sizeof(double));
+        return OPF_OK;
+    });
+}
+
+void opf_destroy(opf_problem* p) {
+    if (!p) return;
+    try {
+        if (p->uploaded) opf::device_free(p);
+    } catch (...) {
+    }
+    delete p;
+}
+
+}  // extern "C"

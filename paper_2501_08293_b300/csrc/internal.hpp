@@ -1,0 +1,84 @@
+// Internal host-side structures of libopf_admm (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "opf_admm.h"
+
+namespace opf {
+
+struct Error : std::runtime_error {
+    int32_t status;
+    Error(int32_t s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+enum CompKind { COMP_BUS = 0, COMP_LINE = 1, COMP_LOAD = 2, COMP_GEN = 3 };
+
+// One fine-grained component of Eq. (OurModel): its local variables (as
+// global indices, i.e. the 0-1 map B_s) and its equality rows A_s x_s = b_s
+// (row-major m x n).
+struct Component {
+    int kind = 0;
+    int index = 0;
+    std::vector<int32_t> gvars;
+    int m = 0;
+    std::vector<double> A;
+    std::vector<double> b;
+    int n() const { return (int)gvars.size(); }
+};
+
+// Global vector of Eq. (LP_model) plus lookups for unscattering.
+struct Model {
+    int n = 0;
+    std::vector<double> lo, hi, c;
+    std::vector<uint8_t> is_w;                // squared voltage magnitude
+    std::vector<Component> comps;             // canonical order
+    int n_bus = 0, n_line = 0, n_gen = 0, n_load = 0;
+    // element lookups, -1 for absent phases / out-of-service lines
+    std::vector<int32_t> w_idx, pg_idx, qg_idx;                 // *3
+    std::vector<int32_t> pij_idx, qij_idx, pji_idx, qji_idx;    // n_line*3
+    std::vector<int32_t> pb_idx, qb_idx, pd_idx, qd_idx;        // n_load*3
+};
+
+// Closed-form operator of one component (Eq. closed_2), P = -Abar.
+struct Operator {
+    int n = 0;
+    int m_reduced = 0;
+    std::vector<double> P;      // n x n, symmetric
+    std::vector<double> bbar;   // n
+};
+
+// Work item of the local-update kernel: one warp.  n <= 32: ncomp = 32/n
+// components whose n*ncomp locals map to lanes; n > 32: one component.
+struct Tile {
+    int32_t n;
+    int32_t ncomp;
+    int32_t loc0;   // first local (device order)
+    int32_t mat0;   // first operator element
+};
+
+// Device-ordered problem, ready to upload.
+struct Packed {
+    int ng = 0, nl = 0, ncomp = 0;
+    std::vector<Tile> tiles;
+    std::vector<int32_t> dev_of_canon;   // local: canonical -> device
+    std::vector<int32_t> canon_of_dev;   // local: device -> canonical
+    std::vector<int32_t> gidx;           // device order
+    std::vector<int32_t> gptr, gcol;     // CSR: global -> device locals
+    std::vector<double> invk, cik;       // 1/k_i, c_i/k_i
+    std::vector<double> bbar, xl0;       // device order
+    std::vector<double> P;               // operator elements, tile layout
+    int64_t mat_elems = 0;
+    int64_t sum_n2 = 0;
+    int max_n = 0;
+};
+
+Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
+                  const opf_gen* gens, int ng, const opf_load* loads, int nd);
+Operator make_operator(const Component& c);
+Packed pack(const Model& m, const std::vector<Operator>& ops);
+
+}  // namespace opf

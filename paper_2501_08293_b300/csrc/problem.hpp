@@ -1,0 +1,91 @@
+// The opf_problem handle and the device-side control block.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <utility>
+
+#include "internal.hpp"
+
+namespace opf {
+
+// Device control block: solve parameters written by the host before a
+// solve, iteration state and residuals written by the finalize kernel.
+struct Ctl {
+    double rho, inv_rho, eps_abs_prim, eps_abs_dual, eps_rel;
+    int32_t criterion;
+    int32_t max_iter;     // absolute bound on iter for this solve
+    int32_t K;            // check interval
+    int32_t iter;         // iterations since the last cold start
+    int32_t status;       // CTL_*
+    int32_t first_rel;
+    int32_t stop;
+    int32_t checks;
+    double pres, dres, eps_prim, eps_dual, objective;
+};
+enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_MAXITER = 2, CTL_NUMERIC = 3 };
+
+template <typename T>
+struct View {
+    const T* lo;
+    const T* hi;
+    const T* invk;
+    const T* cik;
+    T* zg;
+    const int32_t* gptr;
+    const int32_t* gcol;
+    T* xl;
+    T* lam;
+    const T* bbar;
+    const T* xl0;
+    const int32_t* gidx;
+    const Tile* tiles;
+    const T* P;
+    const double* cost;
+    double* partials;
+    Ctl* ctl;
+    int32_t ng, nl, ntiles, nparts;
+};
+
+struct DevPrec {            // one precision's arrays
+    void* lo = nullptr; void* hi = nullptr; void* invk = nullptr; void* cik = nullptr; void* zg = nullptr;
+    void* xl = nullptr; void* lam = nullptr; void* bbar = nullptr; void* xl0 = nullptr; void* P = nullptr;
+};
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace opf
+
+struct opf_problem {
+    opf::Model model;
+    std::vector<opf::Operator> ops;
+    opf::Packed pk;
+    std::vector<int32_t> canon_comp_ptr;
+    std::vector<int32_t> m_reduced;
+    int64_t n_rows = 0, n_rows_reduced = 0;
+
+    // device side
+    bool uploaded = false;
+    bool owns_arena = false;
+    int device = -1;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    size_t need_bytes = 0;
+    opf::DevPrec d64, d32;
+    int32_t* gptr = nullptr;
+    int32_t* gcol = nullptr;
+    int32_t* gidx = nullptr;
+    opf::Tile* tiles = nullptr;
+    double* cost = nullptr;
+    double* partials = nullptr;
+    opf::Ctl* ctl = nullptr;
+    opf::Ctl* ctl_host = nullptr;       // pinned mirror
+    int nparts = 0;                     // blocks of the local-update kernel
+    int cur_prec = 0;                   // precision holding the current state
+    bool cold = true;                   // state is at the initial point
+    std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision, K)
+};

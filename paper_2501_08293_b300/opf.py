@@ -1,0 +1,207 @@
+"""Thin Python binding of the C ABI in include/opf_admm.h (ctypes).
+
+Argument marshalling only: every step of the solve runs in libopf_admm.so
+(host precompute in C++, iterations in sm_103a kernels).  There is no CPU
+fallback: importing this module raises if the library is missing, and
+device calls raise if CUDA is unavailable.  PyTorch supplies the device
+memory arena (caching allocator) and the stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import feeders as _F
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libopf_admm.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libopf_admm.so not built ({_LIB_PATH}); run python -m paper_2501_08293_b300.build")
+lib = C.CDLL(_LIB_PATH)
+
+OK, NOT_CONVERGED = 0, 1
+CRIT_ABS, CRIT_REL, CRIT_BOTH, CRIT_NEVER = 0, 1, 2, 3
+FP64, FP32 = 0, 1
+ENGINE_AUTO, ENGINE_GRAPH, ENGINE_HOSTLOOP = 0, 1, 2
+
+
+class Params(C.Structure):
+    _fields_ = [("rho", C.c_double), ("eps_abs_prim", C.c_double), ("eps_abs_dual", C.c_double),
+                ("eps_rel", C.c_double), ("criterion", C.c_int32), ("max_iter", C.c_int32),
+                ("check_every", C.c_int32), ("precision", C.c_int32), ("residual_form", C.c_int32),
+                ("warm_start", C.c_int32), ("engine", C.c_int32), ("_reserved", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("first_rel_iter", C.c_int32),
+                ("_pad", C.c_int32), ("pres", C.c_double), ("dres", C.c_double),
+                ("eps_prim", C.c_double), ("eps_dual", C.c_double), ("objective", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("_")}
+
+
+class Dims(C.Structure):
+    _fields_ = [("n_global", C.c_int32), ("n_local", C.c_int32), ("n_comp", C.c_int32),
+                ("n_rows", C.c_int32), ("n_rows_reduced", C.c_int32), ("max_n", C.c_int32),
+                ("n_tiles", C.c_int32), ("_pad", C.c_int32), ("sum_n2", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int32)
+EXPORTS = {
+    "opf_abi_version": (C.c_int32, []),
+    "opf_record_size": (C.c_size_t, [C.c_int32]),
+    "opf_status_string": (C.c_char_p, [C.c_int32]),
+    "opf_last_error": (C.c_char_p, []),
+    "opf_params_default": (None, [C.POINTER(Params)]),
+    "opf_problem_create": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32,
+                                       C.POINTER(C.c_void_p)]),
+    "opf_get_dims": (C.c_int32, [_P, C.POINTER(Dims)]),
+    "opf_problem_upload": (C.c_int32, [_P, _P, C.c_size_t, _P]),
+    "opf_admm_solve": (C.c_int32, [_P, C.POINTER(Params), _P, C.POINTER(Info)]),
+    "opf_get_state": (C.c_int32, [_P, _D, _D, _D, _P]),
+    "opf_set_state": (C.c_int32, [_P, _D, _D, _P]),
+    "opf_get_structure": (C.c_int32, [_P, _I, _I, _I, _I, _I]),
+    "opf_get_solution": (C.c_int32, [_P] + [_D] * 11 + [_P]),
+    "opf_get_operator": (C.c_int32, [_P, C.c_int32, _D, _D, _I]),
+    "opf_destroy": (None, [_P]),
+}
+for _name, (_res, _args) in EXPORTS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class OpfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.opf_last_error().decode()
+        super().__init__(f"{where}: {lib.opf_status_string(status).decode()} ({status}): {msg}")
+
+
+def _check(st: int, where: str) -> int:
+    if st < 0:
+        raise OpfError(st, where)
+    return st
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib.opf_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Problem:
+    """One feeder: host precompute at construction, device arena from torch."""
+
+    def __init__(self, buses, lines, gens, loads, *, device=None, stream=None, upload=True):
+        self._h = C.c_void_p()
+        self._arrays = [np.ascontiguousarray(a) for a in (buses, lines, gens, loads)]
+        for a, dt in zip(self._arrays, (_F.BUS_DTYPE, _F.LINE_DTYPE, _F.GEN_DTYPE, _F.LOAD_DTYPE)):
+            if a.dtype != dt:
+                raise TypeError(f"record array has dtype {a.dtype}, expected {dt}")
+        b, l, g, d = self._arrays
+        _check(lib.opf_problem_create(b.ctypes.data, len(b), l.ctypes.data, len(l), g.ctypes.data, len(g),
+                                      d.ctypes.data, len(d), C.byref(self._h)), "opf_problem_create")
+        self.dims = Dims()
+        _check(lib.opf_get_dims(self._h, C.byref(self.dims)), "opf_get_dims")
+        self.n_bus, self.n_line, self.n_gen, self.n_load = len(b), len(l), len(g), len(d)
+        self._arena = None
+        if upload:
+            self.upload(device=device, stream=stream)
+
+    @classmethod
+    def from_feeder(cls, f, **kw) -> "Problem":
+        return cls(f.buses, f.lines, f.gens, f.loads, **kw)
+
+    def upload(self, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: the solver has no CPU path")
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(dev):
+            nbytes = int(self.dims.device_bytes)
+            self._arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+            base = self._arena.data_ptr()
+            off = (-base) % 256
+            _check(lib.opf_problem_upload(self._h, C.c_void_p(base + off), nbytes, _stream_handle(stream)),
+                   "opf_problem_upload")
+
+    def solve(self, params: Params | None = None, stream=None, **kw) -> Info:
+        p = params if params is not None else default_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        info = Info()
+        _check(lib.opf_admm_solve(self._h, C.byref(p), _stream_handle(stream), C.byref(info)), "opf_admm_solve")
+        return info
+
+    def state(self, stream=None):
+        xg = np.empty(self.dims.n_global)
+        xl = np.empty(self.dims.n_local)
+        lam = np.empty(self.dims.n_local)
+        _check(lib.opf_get_state(self._h, _dp(xg), _dp(xl), _dp(lam), _stream_handle(stream)), "opf_get_state")
+        return xg, xl, lam
+
+    def set_state(self, xl, lam, stream=None):
+        xl = np.ascontiguousarray(xl, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        _check(lib.opf_set_state(self._h, _dp(xl), _dp(lam), _stream_handle(stream)), "opf_set_state")
+
+    def structure(self):
+        S, nl = self.dims.n_comp, self.dims.n_local
+        ptr = np.empty(S + 1, np.int32); kind = np.empty(S, np.int32); idx = np.empty(S, np.int32)
+        gidx = np.empty(nl, np.int32); mred = np.empty(S, np.int32)
+        ip = lambda a: a.ctypes.data_as(_I)
+        _check(lib.opf_get_structure(self._h, ip(ptr), ip(kind), ip(idx), ip(gidx), ip(mred)), "opf_get_structure")
+        return dict(comp_ptr=ptr, kind=kind, index=idx, gidx=gidx, m_reduced=mred)
+
+    def operator(self, s: int):
+        n = C.c_int32()
+        _check(lib.opf_get_operator(self._h, s, None, None, C.byref(n)), "opf_get_operator")
+        P = np.empty((n.value, n.value))
+        bbar = np.empty(n.value)
+        _check(lib.opf_get_operator(self._h, s, _dp(P), _dp(bbar), None), "opf_get_operator")
+        return P, bbar
+
+    def solution(self, stream=None) -> dict:
+        shp = {"w": self.n_bus, "pg": self.n_gen, "qg": self.n_gen, "p_ij": self.n_line, "q_ij": self.n_line,
+               "p_ji": self.n_line, "q_ji": self.n_line, "pd": self.n_load, "qd": self.n_load,
+               "pb": self.n_load, "qb": self.n_load}
+        out = {k: np.empty((n, 3)) for k, n in shp.items()}
+        _check(lib.opf_get_solution(self._h, *[_dp(out[k]) for k in shp], _stream_handle(stream)),
+               "opf_get_solution")
+        return out
+
+    def close(self):
+        if self._h:
+            lib.opf_destroy(self._h)
+            self._h = C.c_void_p()
+        self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

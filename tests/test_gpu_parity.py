@@ -1,0 +1,189 @@
+"""GPU parity: the sm_103a path through the C ABI against the FP64 oracle on
+the same seeded feeders.
+
+Tolerance (FP64 path): 1e-9 relative, normwise per iterate
+(||gpu - oracle|| <= 1e-9 * max(||oracle||, 1)) for the global vector, the
+stacked locals and the duals, at several iterations; residuals likewise.
+Both sides run Algorithm 1 in FP64 with different summation orders and
+different (but equivalent) precompute factorizations (operators agree to
+~1e-11), and ADMM is non-expansive, so the gap stays at rounding level.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_08293_b300 import feeders as F
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def opf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_08293_b300 import build
+    build.build()
+    from paper_2501_08293_b300 import opf as mod
+    return mod
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1.0))
+
+
+def oracle_solver(f, rho):
+    from oracle import admm as OA, model as OM, precompute as OP
+    m = OM.build_feeder(f)
+    pre = OP.precompute(m)
+    return m, pre, OA.ADMM(m, pre, rho)
+
+
+def run_pair(opf, f, rho, checkpoints, **kw):
+    """Advance GPU (warm-started in chunks) and oracle to each checkpoint."""
+    p = opf.Problem.from_feeder(f)
+    m, pre, s = oracle_solver(f, rho)
+    out = []
+    done = 0
+    for t in checkpoints:
+        info = p.solve(opf.default_params(rho=rho, criterion=opf.CRIT_NEVER, max_iter=t - done,
+                                          check_every=min(t - done, 50), warm_start=int(done > 0), **kw))
+        assert info.iters == t
+        for _ in range(t - done):
+            r = s.step()
+        done = t
+        out.append((t, info, p.state(), (s.x.copy(), s.z.copy(), s.lam.copy()), r))
+    return p, out
+
+
+@pytest.mark.parametrize("maker,rho", [(lambda: F.feeder_13(1), 100.0), (lambda: F.feeder_123(1), 100.0),
+                                       (lambda: F.feeder_tiny(6, 2), 10.0), (lambda: F.feeder_13(3), 1000.0)])
+def test_fp64_per_iterate_parity(opf, maker, rho):
+    f = maker()
+    p, out = run_pair(opf, f, rho, [1, 2, 3, 10, 100, 1000])
+    c = oracle_cost(f)
+    for t, info, (xg, xl, lam), (ox, oz, ol), r in out:
+        assert rel(xg, ox) <= TOL, (t, rel(xg, ox))
+        assert rel(xl, oz) <= TOL, (t, rel(xl, oz))
+        assert rel(lam, ol) <= TOL, (t, rel(lam, ol))
+        assert abs(info.pres - r.pres) <= TOL * max(r.pres, 1e-6)
+        assert abs(info.dres - r.dres) <= TOL * max(r.dres, 1e-6)
+        assert abs(info.eps_prim - r.eps_prim) <= TOL * r.eps_prim
+        assert abs(info.eps_dual - r.eps_dual) <= TOL * max(r.eps_dual, 1e-12)
+        assert abs(info.objective - float(c @ ox)) <= TOL * max(1.0, abs(info.objective))
+    p.close()
+
+
+def oracle_cost(f):
+    from oracle import model as OM
+    return OM.build_feeder(f).c
+
+
+def test_fp64_converges_like_oracle(opf):
+    """Same stopping iteration (check every iteration) and the same
+    solution at ABS 1e-4 on the 13-bus configuration (rho = 100)."""
+    from oracle import admm as OA
+    f = F.feeder_13(1)
+    m, pre, s = oracle_solver(f, 100.0)
+    o = s.run(200000, criterion=OA.CRIT_ABS)
+    p = opf.Problem.from_feeder(f)
+    info = p.solve(opf.default_params(check_every=1))
+    assert info.status == opf.OK
+    assert info.iters == o["iters"]
+    xg, xl, lam = p.state()
+    assert rel(xg, s.x) <= TOL
+    assert abs(info.objective - o["objective"]) <= 1e-9 * abs(o["objective"])
+    assert info.first_rel_iter == o["first_rel"]
+    sol = p.solution()
+    w = sol["w"]
+    for i in range(f.n_bus):
+        for ph in range(3):
+            if (int(f.buses["phases"][i]) >> ph) & 1:
+                assert w[i, ph] == xg[m.gidx["w"][i, ph]]
+            else:
+                assert np.isnan(w[i, ph])
+    p.close()
+
+
+def test_engines_and_chunking_are_bitwise_identical(opf):
+    """Graph engine (device while-node) == host loop == warm-started chunks,
+    bit for bit (fixed-order reductions, no atomics)."""
+    f = F.feeder_123(3)
+    res = []
+    for engine, chunks in ((opf.ENGINE_GRAPH, [300]), (opf.ENGINE_HOSTLOOP, [300]),
+                           (opf.ENGINE_GRAPH, [7, 93, 200])):
+        p = opf.Problem.from_feeder(f)
+        done = 0
+        for c in chunks:
+            info = p.solve(opf.default_params(criterion=opf.CRIT_NEVER, max_iter=c, check_every=10,
+                                              engine=engine, warm_start=int(done > 0)))
+            done += c
+        assert info.iters == 300
+        res.append((p.state(), info.pres, info.dres))
+        p.close()
+    for (a, pa, da) in res[1:]:
+        for x, y in zip(a, res[0][0]):
+            assert np.array_equal(x, y)
+    assert res[1][1] == res[0][1] and res[1][2] == res[0][2]
+
+
+def test_full_size_8500_class_parity(opf):
+    """8500-class feeder (11,932 nodes, S ~ 25k) in the bench's launch
+    configuration: 200 iterations (check every 50) against the oracle."""
+    f = F.feeder_8500(1)
+    p = opf.Problem.from_feeder(f)
+    m, pre, s = oracle_solver(f, 100.0)
+    info = p.solve(opf.default_params(criterion=opf.CRIT_NEVER, max_iter=200, check_every=50))
+    for _ in range(200):
+        r = s.step()
+    xg, xl, lam = p.state()
+    assert rel(xg, s.x) <= TOL and rel(xl, s.z) <= TOL and rel(lam, s.lam) <= TOL
+    assert abs(info.pres - r.pres) <= TOL * r.pres and abs(info.dres - r.dres) <= TOL * r.dres
+    # invariants at full size: bounds hold exactly, local rows hold
+    assert np.all(xg >= m.lo) and np.all(xg <= m.hi)
+    p.close()
+
+
+def test_edge_cases(opf):
+    """max_iter = 0 leaves the initial point; a star feeder whose root bus
+    component has n > 32 (one-warp tile path); a generator-only feeder."""
+    f = F.feeder_13(2)
+    p = opf.Problem.from_feeder(f)
+    info = p.solve(opf.default_params(max_iter=0))
+    _, xl, lam = p.state()
+    m, pre, s = oracle_solver(f, 100.0)
+    assert np.array_equal(xl, s.z) and np.all(lam == 0) and info.iters == 0
+    p.close()
+    # star: 20 single-phase laterals on the root -> root component n = 3 + 20*2 + 6
+    star = F.make_feeder(21, 5, n_loads=20, load_sampler=lambda r: r.uniform(0.01, 0.05),
+                         line_mix=(0.0, 0.0, 1.0), chain_prob=0.0)
+    star.lines["from_bus"] = 0
+    star.parent[1:] = 0
+    ps = opf.Problem.from_feeder(star)
+    assert ps.dims.max_n > 32
+    p2, out = run_pair(opf, star, 100.0, [1, 50, 300])
+    for t, info, (xg, xl, lam), (ox, oz, ol), r in out:
+        assert rel(xg, ox) <= TOL and rel(xl, oz) <= TOL and rel(lam, ol) <= TOL
+    p2.close(); ps.close()
+    buses = np.zeros(1, F.BUS_DTYPE); buses["phases"] = 1; buses["w_lo"] = 0.9; buses["w_hi"] = 1.1
+    gens = np.zeros(1, F.GEN_DTYPE); gens["phases"] = 1; gens["pg_lo"] = 0.2; gens["pg_hi"] = 1
+    gens["qg_lo"] = -1; gens["qg_hi"] = 1; gens["cost"] = 1
+    pg = opf.Problem(buses, np.zeros(0, F.LINE_DTYPE), gens, np.zeros(0, F.LOAD_DTYPE))
+    info = pg.solve(opf.default_params(max_iter=5000, check_every=1))
+    assert info.status == opf.OK
+
+
+def test_fp32_path_reaches_tolerance(opf):
+    """Reduced-precision sweeps (FP32 x/z/dual, FP64 residual accumulation):
+    objective within 1e-4 relative of the FP64 oracle optimum and residuals
+    at the 1e-4 target on the 13-bus configuration."""
+    from oracle import admm as OA
+    f = F.feeder_13(1)
+    m, pre, s = oracle_solver(f, 100.0)
+    o = s.run(400000, eps_abs_prim=1e-7, eps_abs_dual=1e-7)
+    p = opf.Problem.from_feeder(f)
+    info = p.solve(opf.default_params(precision=opf.FP32, max_iter=400000, check_every=10))
+    assert info.status == opf.OK, info.as_dict()
+    assert info.pres <= 1e-4 and info.dres <= 1e-4
+    assert abs(info.objective - o["objective"]) <= 1e-4 * abs(o["objective"])
+    p.close()
