@@ -1,0 +1,289 @@
+"""Benchmark: 8500-class feeder, componentwise ADMM to the 1e-4 residual.
+
+One step = one full solve of the 8500-class synthetic feeder (11,932 nodes,
+~25k components) from the cold initial point of Section V-A to pres, dres
+<= 1e-4 (rho = 100), through the C ABI with the problem resident in HBM.
+value = ADMM iterations per second over the timed solves; ms_per_step is
+the time to the 1e-4 residual.  L2 is flushed (a 256 MB write) before every
+timed solve, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py --impl reference   # the CPU oracle on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "8500-bus ADMM time-to-1e-4 residual & iters/s; served solves/s, p50/p99 latency"
+UNIT = "iters/s"
+WORKLOAD = "synthetic 8500-class feeder (11,932 nodes, 1200 loads, 200 PV), rho=100, ABS 1e-4"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--rho", type=float, default=100.0)
+    ap.add_argument("--check-every", type=int, default=50)
+    ap.add_argument("--max-iter", type=int, default=2_000_000)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def cpu_oracle_rate(feeder, rho, seconds, max_iter=None):
+    """Oracle (as it stands) iterations/s on a bounded sample of the workload."""
+    from oracle import admm as OA, model as OM, precompute as OP
+    m = OM.build_feeder(feeder)
+    pre = OP.precompute(m)
+    s = OA.ADMM(m, pre, rho)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds and (max_iter is None or n < max_iter):
+        s.step()
+        n += 1
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+# ----------------------------------------------------------------- arms
+def run_reference(args):
+    """CPU oracle as the reference arm: each step runs a bounded sample
+    (cold start, a few seconds of iterations) of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2501_08293_b300 import feeders as F
+    f = F.feeder_8500(args.seed)
+    per_step = max(2.0, min(10.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(f, args.rho, 0.5)
+    iters, secs = 0, 0.0
+    for _ in range(args.steps):
+        r, n, dt = cpu_oracle_rate(f, args.rho, per_step)
+        iters += n
+        secs += dt
+    value = iters / secs
+    sample = f"cold-start ADMM iterations for {per_step:.1f} s per step on {WORKLOAD}"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "oracle": "numpy/scipy FP64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def kernel_times(prob, params, stream):
+    """Average microseconds per launch of each kernel, measured with CUDA
+    events on the solve stream around graphs of back-to-back launches
+    (opf_profile_kernels); the iterate is restored afterwards."""
+    return prob.profile_kernels(params, reps=200, stream=stream)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+
+    prec = opf.FP64 if args.precision == "fp64" else opf.FP32
+    f = F.feeder_8500(args.seed)           # replicas: every rank solves its own copy
+    prob = opf.Problem.from_feeder(f)
+    d = prob.dims
+    params = opf.default_params(rho=args.rho, precision=prec, check_every=args.check_every,
+                                max_iter=args.max_iter)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        prob.solve(params)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times, iters, infos = [], 0, []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = prob.solve(params)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            iters += info.iters
+            infos.append(info.as_dict())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    tot = sum(times)
+    iters_all = float(iters)
+    if world > 1:
+        t = torch.tensor([tot], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+        it = torch.tensor([float(iters)], device="cuda")
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        iters_all = float(it.item())
+    value = iters_all / tot
+    ms_per_step = 1e3 * tot / args.steps
+
+    # roofline of the dominant kernel (local update + dual): algorithmic
+    # bytes per launch = operators (w * sum n_s^2) + per local: gidx (4),
+    # gathered x, lambda, old z, bbar reads and z, lambda writes (6 w) + tiles
+    w = 8 if prec == opf.FP64 else 4
+    bytes_x = w * d.sum_n2 + d.n_local * (4 + 6 * w) + 16 * d.n_tiles
+    flops_x = 2 * d.sum_n2
+    kt = kernel_times(prob, params, stream)
+
+    # e2e: host records -> create (host precompute) -> upload (H2D) -> solve
+    # -> solution (D2H), all through the public API
+    e2e_times, e2e_iters = [], 0
+    h2d = int(d.device_bytes)
+    d2h = 8 * 3 * (2 * len(f.gens) + len(f.buses) + 4 * len(f.lines) + 4 * len(f.loads))
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = opf.Problem.from_feeder(f)
+        inf2 = p2.solve(params)
+        p2.solution()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_iters += inf2.iters
+        p2.close()
+    e2e_value = e2e_iters / sum(e2e_times)
+
+    launches = 0
+    for inf in infos:
+        n = inf["iters"]
+        launches += 2 * n + (n + args.check_every - 1) // args.check_every + 2
+
+    peaks, kind = measured_peaks()
+    achieved = bytes_x / (kt["x"] * 1e-6) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == opf.FP64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "precision": args.precision, "check_every": args.check_every,
+                   "l2": "flushed (256 MB write) before each timed solve",
+                   "S": d.n_comp, "n_global": d.n_global, "n_local": d.n_local, "sum_n2": d.sum_n2},
+        "time_to_tol_s": ms_per_step / 1e3,
+        "iters_per_solve": iters / args.steps,
+        "final": {k: infos[-1][k] for k in ("status", "iters", "pres", "dres", "objective")},
+        "roofline": {"kernel": "x_kernel (local update + dual update)", "bound": "hbm",
+                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_kind": kind,
+                     "bytes_per_launch": bytes_x, "flops_per_launch": flops_x,
+                     "kernel_us": kt},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "seconds_per_step": sum(e2e_times) / len(e2e_times)},
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, n, dt = cpu_oracle_rate(f, args.rho, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{n} cold-start iterations ({dt:.1f} s) of the same feeder, "
+                                         f"FP64 numpy/scipy, single thread"}
+    if rank == 0:
+        print(json.dumps(out))
+    prob.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

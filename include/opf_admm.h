@@ -233,6 +233,16 @@ int32_t opf_get_solution(const opf_problem* p, double* w, double* pg, double* qg
                          double* p_ij, double* q_ij, double* p_ji, double* q_ji,
                          double* pd, double* qd, double* pb, double* qb, void* stream);
 
+/* Average device duration in microseconds of each kernel of an iteration,
+ * as launched inside the solve graph: for each kernel a CUDA graph of
+ * `reps` back-to-back launches is timed with CUDA events on `stream`.
+ * us[0] = global update, us[1] = local update + dual update, us[2] = local
+ * update with residual partials, us[3] = residual finalize.  Uses
+ * params->rho and params->precision; the iterate, duals and iteration
+ * counter are saved before and restored after (scratch is allocated with
+ * cudaMallocAsync on `stream` and freed before returning).                 */
+int32_t opf_profile_kernels(opf_problem* p, const opf_params* params, int32_t reps, void* stream, double* us);
+
 /* Host copy of component s's precomputed operator (canonical component
  * order): P[n_s*n_s] row-major = -Abar_s of Eq. (closed_2) (symmetric) and
  * bbar[n_s]; either pointer may be NULL.  *n_s (may be NULL) gets n_s.

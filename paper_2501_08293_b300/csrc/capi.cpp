@@ -17,6 +17,7 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
 void device_get_state(const opf_problem* p, double* xg, double* xl, double* lam, cudaStream_t s);
 void device_set_state(opf_problem* p, const double* xl, const double* lam, cudaStream_t s);
 void device_free(opf_problem* p);
+void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us);
 }  // namespace opf
 
 namespace {
@@ -212,6 +213,18 @@ int32_t opf_get_solution(const opf_problem* p, double* w, double* pg, double* qg
         scat(w, M.w_idx); scat(pg, M.pg_idx); scat(qg, M.qg_idx);
         scat(p_ij, M.pij_idx); scat(q_ij, M.qij_idx); scat(p_ji, M.pji_idx); scat(q_ji, M.qji_idx);
         scat(pd, M.pd_idx); scat(qd, M.qd_idx); scat(pb, M.pb_idx); scat(qb, M.qb_idx);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_profile_kernels(opf_problem* p, const opf_params* prm, int32_t reps, void* stream, double* us) {
+    return guarded([&]() -> int32_t {
+        if (!p || !prm || !us) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "profile before upload");
+        if (reps < 1 || reps > 100000) throw opf::Error(OPF_ERR_INVALID_ARG, "reps out of [1, 100000]");
+        if (!(prm->rho > 0.0)) throw opf::Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
+        if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
+        opf::device_profile(p, *prm, reps, (cudaStream_t)stream, us);
         return OPF_OK;
     });
 }

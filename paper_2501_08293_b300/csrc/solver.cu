@@ -558,6 +558,80 @@ void device_set_state(opf_problem* p, const double* xl, const double* lam, cudaS
     p->cold = false;
 }
 
+namespace {
+
+template <typename T>
+double time_graph(opf_problem* p, int which, int reps, cudaStream_t s) {
+    const DevPrec& d = sizeof(T) == 8 ? p->d64 : p->d32;
+    View<T> v = view_of<T>(p, d);
+    const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
+    cudaStream_t cs;
+    OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    OPF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < reps; ++r) {
+        if (which == 0) z_kernel<T><<<zb, kZThreads, 0, cs>>>(v, 0);
+        else if (which <= 2) x_kernel<T><<<p->nparts, kXWarps * 32, 0, cs>>>(v, 0);
+        else finalize_kernel<T><<<1, kFinThreads, 0, cs>>>(v, 0, 0);
+    }
+    OPF_CUDA(cudaStreamEndCapture(cs, &g));
+    OPF_CUDA(cudaStreamDestroy(cs));
+    OPF_CUDA(cudaGraphInstantiate(&ge, g, 0));
+    cudaEvent_t e0, e1;
+    OPF_CUDA(cudaEventCreate(&e0));
+    OPF_CUDA(cudaEventCreate(&e1));
+    OPF_CUDA(cudaGraphLaunch(ge, s));            // warm
+    OPF_CUDA(cudaEventRecord(e0, s));
+    OPF_CUDA(cudaGraphLaunch(ge, s));
+    OPF_CUDA(cudaEventRecord(e1, s));
+    OPF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    OPF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    return 1e3 * (double)ms / reps;
+}
+
+}  // namespace
+
+void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us) {
+    DeviceGuard g(p->device);
+    const int prec = prm.precision;
+    sync_state_to(p, prec, s);
+    const DevPrec& d = prec == OPF_FP64 ? p->d64 : p->d32;
+    const size_t w = prec == OPF_FP64 ? 8 : 4;
+    const size_t nl = p->pk.nl, ng = p->pk.ng;
+    char* save = nullptr;
+    const size_t bytes = 2 * nl * w + ng * w + sizeof(Ctl);
+    OPF_CUDA(cudaMallocAsync((void**)&save, bytes, s));
+    OPF_CUDA(cudaMemcpyAsync(save, d.xl, nl * w, cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync(save + nl * w, d.lam, nl * w, cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync(save + 2 * nl * w, d.zg, ng * w, cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync(save + 2 * nl * w + ng * w, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    OPF_CUDA(cudaStreamSynchronize(s));
+    // control block for timing: no launch is skipped (huge bound); K = 1 makes
+    // every local-update launch compute residual partials (which == 2)
+    Ctl c = *p->ctl_host;
+    c.rho = prm.rho; c.inv_rho = 1.0 / prm.rho; c.iter = 0; c.max_iter = INT32_MAX;
+    for (int which = 0; which < 4; ++which) {
+        c.K = (which == 2) ? 1 : (1 << 20);
+        c.iter = 0;
+        *p->ctl_host = c;
+        OPF_CUDA(cudaMemcpyAsync(p->ctl, p->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        us[which] = prec == OPF_FP64 ? time_graph<double>(p, which, reps, s) : time_graph<float>(p, which, reps, s);
+    }
+    OPF_CUDA(cudaMemcpyAsync(d.xl, save, nl * w, cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync(d.lam, save + nl * w, nl * w, cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync(d.zg, save + 2 * nl * w, ng * w, cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync(p->ctl, save + 2 * nl * w + ng * w, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
+    OPF_CUDA(cudaFreeAsync(save, s));
+    OPF_CUDA(cudaStreamSynchronize(s));
+}
+
 void device_free(opf_problem* p) {
     DeviceGuard g(p->device);
     for (auto& kv : p->graphs) {

@@ -69,6 +69,7 @@ EXPORTS = {
     "opf_get_structure": (C.c_int32, [_P, _I, _I, _I, _I, _I]),
     "opf_get_solution": (C.c_int32, [_P] + [_D] * 11 + [_P]),
     "opf_get_operator": (C.c_int32, [_P, C.c_int32, _D, _D, _I]),
+    "opf_profile_kernels": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
     "opf_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in EXPORTS.items():
@@ -156,6 +157,14 @@ class Problem:
         info = Info()
         _check(lib.opf_admm_solve(self._h, C.byref(p), _stream_handle(stream), C.byref(info)), "opf_admm_solve")
         return info
+
+    def profile_kernels(self, params: Params | None = None, reps: int = 200, stream=None) -> dict:
+        """Average microseconds per launch of each kernel (CUDA events)."""
+        p = params if params is not None else default_params()
+        us = np.zeros(4)
+        _check(lib.opf_profile_kernels(self._h, C.byref(p), reps, _stream_handle(stream), _dp(us)),
+               "opf_profile_kernels")
+        return dict(z=us[0], x=us[1], x_partials=us[2], finalize=us[3])
 
     def state(self, stream=None):
         xg = np.empty(self.dims.n_global)
