@@ -111,7 +111,7 @@ typedef struct opf_load {
 enum { OPF_CRIT_ABS = 0, OPF_CRIT_REL = 1, OPF_CRIT_BOTH = 2, OPF_CRIT_NEVER = 3 };
 enum { OPF_FP64 = 0, OPF_FP32 = 1 };
 enum { OPF_RES_PAPER = 0 };
-enum { OPF_ENGINE_AUTO = 0, OPF_ENGINE_GRAPH = 1, OPF_ENGINE_HOSTLOOP = 2 };
+enum { OPF_ENGINE_AUTO = 0, OPF_ENGINE_GRAPH = 1, OPF_ENGINE_HOSTLOOP = 2, OPF_ENGINE_PERSISTENT = 3 };
 
 /* Solve parameters.  criterion ABS: pres <= eps_abs_prim and dres <=
  * eps_abs_dual; REL: the paper's relative test of Eq. (termination) with
@@ -120,7 +120,11 @@ enum { OPF_ENGINE_AUTO = 0, OPF_ENGINE_GRAPH = 1, OPF_ENGINE_HOSTLOOP = 2 };
  * up to check_every-1 iterations late).  warm_start 0 restarts from the
  * initial point of Section V-A; 1 continues from the handle's current state
  * (iteration counter included).  engine GRAPH runs the whole loop as one
- * CUDA graph with a device-side while node; HOSTLOOP checks from the host.  */
+ * CUDA graph with a device-side while node; HOSTLOOP checks from the host;
+ * PERSISTENT runs it as one cooperative kernel whose CTAs own feeder chunks
+ * and wait only on neighbouring chunks (every wait bounded in time, see
+ * opf_debug_config); AUTO picks PERSISTENT when the chunks fit co-resident
+ * on the device, else GRAPH.                                                */
 typedef struct opf_params {
     double rho;
     double eps_abs_prim, eps_abs_dual, eps_rel;
@@ -156,7 +160,7 @@ typedef struct opf_dims {
     int32_t n_rows_reduced;  /* sum_s m_s after row reduction                   */
     int32_t max_n;           /* max_s n_s                                      */
     int32_t n_tiles;         /* warp tiles of the local-update kernel           */
-    int32_t _pad;
+    int32_t n_blocks;        /* feeder chunks = CTAs of the local update        */
     int64_t sum_n2;          /* sum_s n_s^2 (dense operator entries)            */
     int64_t device_bytes;    /* bytes opf_problem_upload needs                  */
 } opf_dims;
@@ -242,6 +246,18 @@ int32_t opf_get_solution(const opf_problem* p, double* w, double* pg, double* qg
  * counter are saved before and restored after (scratch is allocated with
  * cudaMallocAsync on `stream` and freed before returning).                 */
 int32_t opf_profile_kernels(opf_problem* p, const opf_params* params, int32_t reps, void* stream, double* us);
+
+/* Engine that OPF_ENGINE_AUTO selects for this problem and precision on the
+ * problem's device (OPF_ENGINE_PERSISTENT or OPF_ENGINE_GRAPH).            */
+int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine);
+
+/* Test and tuning hook (the paper has no counterpart): wait_limit_ns bounds
+ * every device-side wait of the persistent engine (default 2e9 ns; a wait
+ * that expires makes the solve return OPF_ERR_TIMEOUT with an undefined
+ * iterate, and the device stays usable); withhold_block >= 0 makes that CTA
+ * never publish its iteration flag, so its neighbours' waits expire (used by
+ * the failure-detection test); -1 restores normal operation.              */
+int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block);
 
 /* Host copy of component s's precomputed operator (canonical component
  * order): P[n_s*n_s] row-major = -Abar_s of Eq. (closed_2) (symmetric) and

@@ -17,6 +17,7 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
 void device_get_state(const opf_problem* p, double* xg, double* xl, double* lam, cudaStream_t s);
 void device_set_state(opf_problem* p, const double* xl, const double* lam, cudaStream_t s);
 void device_free(opf_problem* p);
+int device_auto_engine(const opf_problem* p, int precision);
 void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us);
 }  // namespace opf
 
@@ -133,6 +134,7 @@ int32_t opf_get_dims(const opf_problem* p, opf_dims* d) {
         d->n_rows_reduced = (int32_t)p->n_rows_reduced;
         d->max_n = p->pk.max_n;
         d->n_tiles = (int32_t)p->pk.tiles.size();
+        d->n_blocks = p->pk.nblocks;
         d->sum_n2 = p->pk.sum_n2;
         d->device_bytes = (int64_t)opf::device_bytes(p);
         return OPF_OK;
@@ -157,7 +159,7 @@ int32_t opf_admm_solve(opf_problem* p, const opf_params* prm, void* stream, opf_
         if (prm->criterion < 0 || prm->criterion > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad criterion");
         if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
         if (prm->residual_form != OPF_RES_PAPER) throw opf::Error(OPF_ERR_INVALID_ARG, "unsupported residual form");
-        if (prm->engine < 0 || prm->engine > 2) throw opf::Error(OPF_ERR_INVALID_ARG, "bad engine");
+        if (prm->engine < 0 || prm->engine > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad engine");
         return opf::device_solve(p, *prm, (cudaStream_t)stream, info);
     });
 }
@@ -225,6 +227,29 @@ int32_t opf_profile_kernels(opf_problem* p, const opf_params* prm, int32_t reps,
         if (!(prm->rho > 0.0)) throw opf::Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
         if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
         opf::device_profile(p, *prm, reps, (cudaStream_t)stream, us);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine) {
+    return guarded([&]() -> int32_t {
+        if (!p || !engine) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "problem not uploaded");
+        if (precision != OPF_FP64 && precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
+        *engine = opf::device_auto_engine(p, precision);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        if (wait_limit_ns < 1000 || wait_limit_ns > 600000000000LL)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "wait limit out of [1 us, 600 s]");
+        if (withhold_block < -1 || withhold_block >= p->pk.nblocks)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "withhold_block out of range");
+        p->timeout_ns = (unsigned long long)wait_limit_ns;
+        p->skip_block = withhold_block;
         return OPF_OK;
     });
 }

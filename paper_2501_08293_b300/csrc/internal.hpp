@@ -37,6 +37,7 @@ struct Model {
     std::vector<uint8_t> is_w;                // squared voltage magnitude
     std::vector<Component> comps;             // canonical order
     int n_bus = 0, n_line = 0, n_gen = 0, n_load = 0;
+    std::vector<int32_t> line_from, line_to, load_bus, gen_bus;   // topology
     // element lookups, -1 for absent phases / out-of-service lines
     std::vector<int32_t> w_idx, pg_idx, qg_idx;                 // *3
     std::vector<int32_t> pij_idx, qij_idx, pji_idx, qji_idx;    // n_line*3
@@ -51,19 +52,36 @@ struct Operator {
     std::vector<double> bbar;   // n
 };
 
-// Work item of the local-update kernel: one warp.  n <= 32: ncomp = 32/n
-// components whose n*ncomp locals map to lanes; n > 32: one component.
+// Work item of the local-update kernel: one warp.  Small tiles hold whole
+// components (sizes n_g <= 32, sum n_g = L <= 32 lanes, nmax = max n_g);
+// a big tile holds one component with n > 32 (flag big = 1).
 struct Tile {
-    int32_t n;
-    int32_t ncomp;
     int32_t loc0;   // first local (device order)
     int32_t mat0;   // first operator element
+    int16_t L;      // lanes used (small) or n (big)
+    int16_t nmax;   // loop length: max n_g over the tile's components
+    int32_t big;
+};
+
+// One CTA's share of a problem: a contiguous chunk of the component order
+// (a DFS over the feeder, so chunks are subtrees with few neighbours).
+struct BlockInfo {
+    int32_t tile0, tile1;   // tiles [tile0, tile1)
+    int32_t halo0, halo1;   // globals read by the chunk [halo0, halo1)
+    int32_t nbr0, nbr1;     // neighbour CTAs (share a global) [nbr0, nbr1)
+    int32_t loc0, loc1;     // locals [loc0, loc1)
 };
 
 // Device-ordered problem, ready to upload.
 struct Packed {
     int ng = 0, nl = 0, ncomp = 0;
+    int nblocks = 0;
     std::vector<Tile> tiles;
+    std::vector<BlockInfo> blocks;
+    std::vector<int32_t> halo_gid;       // global id per halo entry
+    std::vector<uint8_t> halo_own;       // 1 if this chunk writes x_i (first copy)
+    std::vector<int32_t> nbrs;
+    std::vector<int32_t> meta;           // per local: hidx | n << 16 | base lane << 24
     std::vector<int32_t> dev_of_canon;   // local: canonical -> device
     std::vector<int32_t> canon_of_dev;   // local: device -> canonical
     std::vector<int32_t> gidx;           // device order
@@ -74,11 +92,12 @@ struct Packed {
     int64_t mat_elems = 0;
     int64_t sum_n2 = 0;
     int max_n = 0;
+    int max_halo = 0;                    // largest chunk halo (shared memory)
 };
 
 Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
                   const opf_gen* gens, int ng, const opf_load* loads, int nd);
 Operator make_operator(const Component& c);
-Packed pack(const Model& m, const std::vector<Operator>& ops);
+Packed pack(const Model& m, const std::vector<Operator>& ops, int nblocks_hint = 0);
 
 }  // namespace opf

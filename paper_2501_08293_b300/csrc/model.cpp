@@ -121,6 +121,9 @@ Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
 
     Model M;
     M.n_bus = nb; M.n_line = nl; M.n_gen = ng; M.n_load = nd;
+    for (int e = 0; e < nl; ++e) { M.line_from.push_back(lines[e].from_bus); M.line_to.push_back(lines[e].to_bus); }
+    for (int l = 0; l < nd; ++l) M.load_bus.push_back(loads[l].bus);
+    for (int k = 0; k < ng; ++k) M.gen_bus.push_back(gens[k].bus);
     auto var = [&](double lo, double hi, double c, bool w) {
         M.lo.push_back(lo); M.hi.push_back(hi); M.c.push_back(c); M.is_w.push_back(w ? 1 : 0);
         return (int32_t)(M.lo.size() - 1);

@@ -1,20 +1,25 @@
 // Device layout of the problem.
 //
-// Components are grouped by size n_s and cut into warp tiles:
-//   n <= 32: one tile holds k = floor(32/n) components of the same n; lane
-//            (g, r) = (lane / n, lane % n) owns local r of component g.
-//            Operator elements are stored column by column across the
-//            tile's lanes: element (c, lane) at mat0 + c*L + lane holds
-//            P_g[c][r] (L = k n), so step c of the GEMV is one contiguous,
-//            coalesced load for the whole warp.  P_g is symmetric, so column
-//            c is also row c.
-//   n > 32:  one component per tile; element (c, r) at mat0 + c*n + r.
-// Tiles are ordered by decreasing n; components keep canonical order
-// within a size.  Device local order follows the tiles, so a tile's locals
-// (x_s, lambda_s, bbar_s, gidx) are contiguous and lane-indexed.
-// The global update reads the copies of global i through a CSR list
-// (gptr/gcol) in canonical order; invk = 1/k_i and cik = c_i/k_i carry
-// (B^T B)^{-1} and (B^T B)^{-1} c of Eq. (global_sparse).
+// 1. Component order for locality: a depth-first walk over the feeder; each
+//    bus brings its own component, the in-service line that reaches it
+//    (emitted when its second end is visited), its loads and its generators.
+// 2. The order is cut into `nblocks` contiguous chunks of about equal work
+//    (n_s^2 + 4 n_s + 16 per component); chunk b is processed by CTA b.
+// 3. Inside a chunk, components are sorted by decreasing n and packed into
+//    warp tiles first-fit-decreasing: a small tile holds components with
+//    sum n_g <= 32 lanes, lane (g, r) owning local r of component g; a
+//    component with n > 32 gets a whole warp (big tile).
+//    Small-tile operator elements are stored column by column across the
+//    lanes: element (c, lane) at mat0 + c*L + lane holds P_g[c][r] (zero
+//    when c >= n_g), so step c of the GEMV is one contiguous load for the
+//    warp.  P_g is symmetric, so column c is also row c.  Big tiles store
+//    (c, r) at mat0 + c*n + r.
+// 4. Per chunk: the distinct globals its locals copy (its "halo"), which of
+//    them it owns (holds their first copy, so it writes x_i), and its
+//    neighbour chunks (chunks that copy one of its globals).
+// The global update also has a CSR list of each global's copies (gptr/gcol,
+// canonical order); invk = 1/k_i and cik = c_i/k_i carry (B^T B)^{-1} and
+// (B^T B)^{-1} c of Eq. (global_sparse).
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -23,67 +28,186 @@
 
 namespace opf {
 
-Packed pack(const Model& M, const std::vector<Operator>& ops) {
+namespace {
+
+std::vector<int> locality_order(const Model& M) {
+    const int nb = M.n_bus;
+    // component index per element
+    std::vector<int> bus_comp(nb, -1), line_comp(M.n_line, -1);
+    std::vector<std::vector<int>> loads_at(nb), gens_at(nb), lines_at(nb);
+    for (int s = 0; s < (int)M.comps.size(); ++s) {
+        const Component& c = M.comps[s];
+        if (c.kind == COMP_BUS) bus_comp[c.index] = s;
+        else if (c.kind == COMP_LINE) line_comp[c.index] = s;
+        else if (c.kind == COMP_LOAD) loads_at[M.load_bus[c.index]].push_back(s);
+        else gens_at[M.gen_bus[c.index]].push_back(s);
+    }
+    for (int e = 0; e < M.n_line; ++e)
+        if (line_comp[e] >= 0) {
+            lines_at[M.line_from[e]].push_back(e);
+            lines_at[M.line_to[e]].push_back(e);
+        }
+    std::vector<int> order;
+    order.reserve(M.comps.size());
+    std::vector<char> seen(nb, 0), line_done(M.n_line, 0);
+    std::vector<int> stack;
+    for (int root = 0; root < nb; ++root) {
+        if (seen[root]) continue;
+        stack.push_back(root);
+        while (!stack.empty()) {
+            const int u = stack.back();
+            stack.pop_back();
+            if (seen[u]) continue;
+            seen[u] = 1;
+            order.push_back(bus_comp[u]);
+            for (int e : lines_at[u]) {
+                const int v = M.line_from[e] == u ? M.line_to[e] : M.line_from[e];
+                if (seen[v] && !line_done[e]) {          // second end visited
+                    line_done[e] = 1;
+                    order.push_back(line_comp[e]);
+                }
+            }
+            for (int s : loads_at[u]) order.push_back(s);
+            for (int s : gens_at[u]) order.push_back(s);
+            for (auto it = lines_at[u].rbegin(); it != lines_at[u].rend(); ++it) {
+                const int v = M.line_from[*it] == u ? M.line_to[*it] : M.line_from[*it];
+                if (!seen[v]) stack.push_back(v);
+            }
+        }
+    }
+    return order;
+}
+
+}  // namespace
+
+Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) {
     Packed K;
     K.ng = M.n;
     K.ncomp = (int)M.comps.size();
     std::vector<int64_t> cptr(K.ncomp + 1, 0);
+    int64_t work_total = 0;
     for (int s = 0; s < K.ncomp; ++s) {
-        cptr[s + 1] = cptr[s] + M.comps[s].n();
-        K.sum_n2 += (int64_t)M.comps[s].n() * M.comps[s].n();
-        K.max_n = std::max(K.max_n, M.comps[s].n());
+        const int n = M.comps[s].n();
+        cptr[s + 1] = cptr[s] + n;
+        K.sum_n2 += (int64_t)n * n;
+        K.max_n = std::max(K.max_n, n);
+        work_total += (int64_t)n * n + 4 * n + 16;
     }
     if (cptr[K.ncomp] > INT32_MAX / 2) throw Error(OPF_ERR_INVALID_ARG, "problem too large");
     K.nl = (int)cptr[K.ncomp];
-    if (K.max_n > 256) throw Error(OPF_ERR_INVALID_ARG, "a component has more than 256 local variables");
+    if (K.max_n > 255) throw Error(OPF_ERR_INVALID_ARG, "a component has more than 255 local variables");
 
-    // component order: by decreasing n, canonical within a size
-    std::vector<int> order(K.ncomp);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return M.comps[a].n() > M.comps[b].n(); });
+    // ---- chunks
+    int nblk = nblocks_hint;
+    if (nblk <= 0) nblk = (int)std::min<int64_t>(592, std::max<int64_t>(1, work_total / 4096));
+    nblk = std::max(1, std::min(nblk, std::max(1, K.ncomp)));
+    const std::vector<int> order = locality_order(M);
+    std::vector<int> chunk_start;   // index into order
+    {
+        int64_t acc = 0;
+        int b = 0;
+        chunk_start.push_back(0);
+        for (int q = 0; q < (int)order.size(); ++q) {
+            const int n = M.comps[order[q]].n();
+            acc += (int64_t)n * n + 4 * n + 16;
+            if (b + 1 < nblk && acc * nblk >= (int64_t)(b + 1) * work_total && q + 1 < (int)order.size()) {
+                chunk_start.push_back(q + 1);
+                ++b;
+            }
+        }
+        chunk_start.push_back((int)order.size());
+    }
+    K.nblocks = (int)chunk_start.size() - 1;
 
     K.dev_of_canon.assign(K.nl, -1);
     K.canon_of_dev.assign(K.nl, -1);
+    K.meta.assign(K.nl, 0);
+    std::vector<int> comp_block(K.ncomp, -1);
     int loc = 0;
     int64_t mat = 0;
-    size_t pos = 0;
-    while (pos < order.size()) {
-        const int n = M.comps[order[pos]].n();
-        if (n == 0) { ++pos; continue; }
-        int k = n <= 32 ? 32 / n : 1;
-        size_t end = pos;
-        while (end < order.size() && (int)(end - pos) < k && M.comps[order[end]].n() == n) ++end;
-        const int kk = (int)(end - pos);
-        mat = (mat + 3) & ~int64_t(3);           // 32-byte aligned tile start (f64)
-        Tile t;
-        t.n = n; t.ncomp = kk; t.loc0 = loc;
-        if (mat > INT32_MAX) throw Error(OPF_ERR_INVALID_ARG, "problem too large");
-        t.mat0 = (int32_t)mat;
-        K.tiles.push_back(t);
-        const int L = kk * n;
-        K.P.resize((size_t)mat + (size_t)n * (n <= 32 ? L : n), 0.0);
-        for (int g = 0; g < kk; ++g) {
-            const int s = order[pos + g];
-            const Operator& op = ops[s];
-            for (int r = 0; r < n; ++r) {
-                K.dev_of_canon[cptr[s] + r] = loc + g * n + r;
-                K.canon_of_dev[loc + g * n + r] = (int32_t)(cptr[s] + r);
+    for (int b = 0; b < K.nblocks; ++b) {
+        BlockInfo bi;
+        bi.tile0 = (int)K.tiles.size();
+        bi.loc0 = loc;
+        std::vector<int> comps(order.begin() + chunk_start[b], order.begin() + chunk_start[b + 1]);
+        std::stable_sort(comps.begin(), comps.end(),
+                         [&](int a, int c) { return M.comps[a].n() > M.comps[c].n(); });
+        for (int s : comps) comp_block[s] = b;
+        // first-fit-decreasing into warps
+        std::vector<std::vector<int>> warps;
+        std::vector<int> lanes;
+        for (int s : comps) {
+            const int n = M.comps[s].n();
+            if (n == 0) continue;
+            if (n > 32) {
+                warps.push_back({s});
+                lanes.push_back(-1);
+                continue;
             }
-            for (int c = 0; c < n; ++c)
-                for (int r = 0; r < n; ++r) {
-                    const double v = op.P[(size_t)c * n + r];
-                    if (n <= 32) K.P[(size_t)mat + (size_t)c * L + g * n + r] = v;
-                    else K.P[(size_t)mat + (size_t)c * n + r] = v;
+            bool placed = false;
+            for (size_t w = 0; w < warps.size(); ++w)
+                if (lanes[w] >= 0 && lanes[w] + n <= 32) {
+                    warps[w].push_back(s);
+                    lanes[w] += n;
+                    placed = true;
+                    break;
                 }
+            if (!placed) {
+                warps.push_back({s});
+                lanes.push_back(n);
+            }
         }
-        mat += (int64_t)n * (n <= 32 ? L : n);
-        loc += L;
-        pos = end;
+        for (size_t w = 0; w < warps.size(); ++w) {
+            mat = (mat + 3) & ~int64_t(3);   // 32-byte aligned tile start (f64)
+            if (mat > INT32_MAX) throw Error(OPF_ERR_INVALID_ARG, "problem too large");
+            Tile t;
+            t.loc0 = loc;
+            t.mat0 = (int32_t)mat;
+            if (lanes[w] < 0) {
+                const int s = warps[w][0], n = M.comps[s].n();
+                t.L = (int16_t)n; t.nmax = (int16_t)n; t.big = 1;
+                K.P.resize((size_t)mat + (size_t)n * n, 0.0);
+                for (int c = 0; c < n; ++c)
+                    for (int r = 0; r < n; ++r) K.P[(size_t)mat + (size_t)c * n + r] = ops[s].P[(size_t)c * n + r];
+                for (int r = 0; r < n; ++r) {
+                    K.dev_of_canon[cptr[s] + r] = loc + r;
+                    K.canon_of_dev[loc + r] = (int32_t)(cptr[s] + r);
+                    K.meta[loc + r] = (n << 16);
+                }
+                mat += (int64_t)n * n;
+                loc += n;
+            } else {
+                const int L = lanes[w];
+                int nmax = 0;
+                for (int s : warps[w]) nmax = std::max(nmax, M.comps[s].n());
+                t.L = (int16_t)L; t.nmax = (int16_t)nmax; t.big = 0;
+                K.P.resize((size_t)mat + (size_t)nmax * L, 0.0);
+                int base = 0;
+                for (int s : warps[w]) {
+                    const int n = M.comps[s].n();
+                    for (int r = 0; r < n; ++r) {
+                        const int lane = base + r;
+                        K.dev_of_canon[cptr[s] + r] = loc + lane;
+                        K.canon_of_dev[loc + lane] = (int32_t)(cptr[s] + r);
+                        K.meta[loc + lane] = (n << 16) | (base << 24);
+                        for (int c = 0; c < n; ++c)
+                            K.P[(size_t)mat + (size_t)c * L + lane] = ops[s].P[(size_t)c * n + r];
+                    }
+                    base += n;
+                }
+                mat += (int64_t)nmax * L;
+                loc += L;
+            }
+            K.tiles.push_back(t);
+        }
+        bi.tile1 = (int)K.tiles.size();
+        bi.loc1 = loc;
+        K.blocks.push_back(bi);
     }
+    if (loc != K.nl) throw Error(OPF_ERR_INVALID_ARG, "internal: locals not all placed");
     K.mat_elems = (int64_t)K.P.size();
 
-    // local vectors in device order
+    // ---- local vectors in device order
     K.gidx.resize(K.nl);
     K.bbar.resize(K.nl);
     K.xl0.resize(K.nl);
@@ -103,7 +227,7 @@ Packed pack(const Model& M, const std::vector<Operator>& ops) {
             ++kcount[g];
         }
     }
-    // CSR of copies, canonical order
+    // ---- CSR of copies, canonical order
     K.gptr.assign(K.ng + 1, 0);
     for (int i = 0; i < K.ng; ++i) {
         if (kcount[i] == 0) throw Error(OPF_ERR_INVALID_ARG, "a global variable has no local copy");
@@ -120,6 +244,45 @@ Packed pack(const Model& M, const std::vector<Operator>& ops) {
     for (int i = 0; i < K.ng; ++i) {
         K.invk[i] = 1.0 / (double)kcount[i];
         K.cik[i] = M.c[i] / (double)kcount[i];
+    }
+
+    // ---- halos, owners, neighbours
+    std::vector<int> owner(K.ng, -1);          // block of the first copy (device order)
+    std::vector<int> block_of_loc(K.nl);
+    for (int b = 0; b < K.nblocks; ++b)
+        for (int j = K.blocks[b].loc0; j < K.blocks[b].loc1; ++j) block_of_loc[j] = b;
+    for (int j = 0; j < K.nl; ++j)
+        if (owner[K.gidx[j]] < 0) owner[K.gidx[j]] = block_of_loc[j];
+    std::vector<int> hmark(K.ng, -1), hpos(K.ng, 0), bmark(K.nblocks, -1);
+    for (int b = 0; b < K.nblocks; ++b) {
+        BlockInfo& bi = K.blocks[b];
+        bi.halo0 = (int)K.halo_gid.size();
+        for (int j = bi.loc0; j < bi.loc1; ++j) {
+            const int g = K.gidx[j];
+            if (hmark[g] != b) {
+                hmark[g] = b;
+                hpos[g] = (int)K.halo_gid.size() - bi.halo0;
+                K.halo_gid.push_back(g);
+                K.halo_own.push_back(owner[g] == b ? 1 : 0);
+            }
+            if (hpos[g] > 0xFFFF) throw Error(OPF_ERR_INVALID_ARG, "chunk halo too large");
+            K.meta[j] |= hpos[g];
+        }
+        bi.halo1 = (int)K.halo_gid.size();
+        K.max_halo = std::max(K.max_halo, bi.halo1 - bi.halo0);
+        bi.nbr0 = (int)K.nbrs.size();
+        for (int h = bi.halo0; h < bi.halo1; ++h) {
+            const int g = K.halo_gid[h];
+            for (int q = K.gptr[g]; q < K.gptr[g + 1]; ++q) {
+                const int d = block_of_loc[K.gcol[q]];
+                if (d != b && bmark[d] != b) {
+                    bmark[d] = b;
+                    K.nbrs.push_back(d);
+                }
+            }
+        }
+        std::sort(K.nbrs.begin() + bi.nbr0, K.nbrs.end());
+        bi.nbr1 = (int)K.nbrs.size();
     }
     return K;
 }

@@ -11,7 +11,7 @@
 namespace opf {
 
 // Device control block: solve parameters written by the host before a
-// solve, iteration state and residuals written by the finalize kernel.
+// solve, iteration state and residuals written by the kernels.
 struct Ctl {
     double rho, inv_rho, eps_abs_prim, eps_abs_dual, eps_rel;
     int32_t criterion;
@@ -23,8 +23,15 @@ struct Ctl {
     int32_t stop;
     int32_t checks;
     double pres, dres, eps_prim, eps_dual, objective;
+    // persistent engine
+    unsigned long long arrive;    // check tickets taken
+    unsigned long long timeout_ns;
+    int32_t decided;              // checks decided
+    int32_t abort;                // a wait gave up: every CTA leaves
+    int32_t skip_block;           // test hook: this CTA withholds its flag (-1: none)
+    int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait
 };
-enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_MAXITER = 2, CTL_NUMERIC = 3 };
+enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_MAXITER = 2, CTL_NUMERIC = 3, CTL_TIMEOUT = 4 };
 
 template <typename T>
 struct View {
@@ -37,20 +44,29 @@ struct View {
     const int32_t* gcol;
     T* xl;
     T* lam;
+    T* xl2;           // ping-pong partners of xl, lam (persistent engine)
+    T* lam2;
     const T* bbar;
     const T* xl0;
     const int32_t* gidx;
+    const int32_t* meta;
     const Tile* tiles;
+    const BlockInfo* blocks;
+    const int32_t* halo_gid;
+    const uint8_t* halo_own;
+    const int32_t* nbrs;
+    int32_t* flags;
     const T* P;
     const double* cost;
     double* partials;
     Ctl* ctl;
-    int32_t ng, nl, ntiles, nparts;
+    int32_t ng, nl, nblocks;
 };
 
 struct DevPrec {            // one precision's arrays
     void* lo = nullptr; void* hi = nullptr; void* invk = nullptr; void* cik = nullptr; void* zg = nullptr;
-    void* xl = nullptr; void* lam = nullptr; void* bbar = nullptr; void* xl0 = nullptr; void* P = nullptr;
+    void* xl = nullptr; void* lam = nullptr; void* xl2 = nullptr; void* lam2 = nullptr;
+    void* bbar = nullptr; void* xl0 = nullptr; void* P = nullptr;
 };
 
 struct GraphEntry {
@@ -74,18 +90,24 @@ struct opf_problem {
     int device = -1;
     char* arena = nullptr;
     size_t arena_bytes = 0;
-    size_t need_bytes = 0;
     opf::DevPrec d64, d32;
     int32_t* gptr = nullptr;
     int32_t* gcol = nullptr;
     int32_t* gidx = nullptr;
+    int32_t* meta = nullptr;
     opf::Tile* tiles = nullptr;
+    opf::BlockInfo* blocks = nullptr;
+    int32_t* halo_gid = nullptr;
+    uint8_t* halo_own = nullptr;
+    int32_t* nbrs = nullptr;
+    int32_t* flags = nullptr;
     double* cost = nullptr;
     double* partials = nullptr;
     opf::Ctl* ctl = nullptr;
     opf::Ctl* ctl_host = nullptr;       // pinned mirror
-    int nparts = 0;                     // blocks of the local-update kernel
     int cur_prec = 0;                   // precision holding the current state
     bool cold = true;                   // state is at the initial point
+    unsigned long long timeout_ns = 2000000000ull;   // bounded waits (persistent engine)
+    int skip_block = -1;                              // test hook
     std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision, K)
 };

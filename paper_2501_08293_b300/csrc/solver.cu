@@ -1,22 +1,33 @@
 // sm_103a kernels and the solve engines of the componentwise ADMM.
 //
-// One iteration of Algorithm 1 is two kernels:
-//   z_kernel  global update, Eq. (global_sparse): for every global i, the
-//             copies' (x_j - lambda_j / rho) are summed over the CSR list in a
-//             fixed order, scaled by 1/k_i, shifted by -c_i/(rho k_i) and
-//             clipped to [lo_i, hi_i].  One thread per global, no atomics.
-//   x_kernel  local update, Eq. (closed_2), fused with the dual update of
-//             Eq. (ADMM-3) and the residual sums of Eq. (termination): per
-//             component u = B_s x + lambda_s / rho, x_s = P_s u + bbar_s
-//             (P_s = -Abar_s), lambda_s += rho (B_s x - x_s).  One warp per
-//             tile of components (see pack.cpp), operator elements streamed
-//             with coalesced loads, u broadcast by warp shuffles.  On check
-//             iterations each block writes five FP64 partial sums
-//             (||Bx - z||^2, ||z - z_prev||^2, ||Bx||^2, ||z||^2, ||lambda||^2).
-// finalize_kernel sums the block partials in a fixed order (deterministic),
-// forms pres, dres, eps_prim, eps_dual, applies the stopping rule and, in the
-// graph engine, sets the condition of the device-side while node so the
-// whole solve runs as one CUDA graph launch without host round trips.
+// Algorithm 1, one iteration:
+//   global update, Eq. (global_sparse): for every global i the copies'
+//     (x_j - lambda_j / rho) are summed over its CSR list in a fixed order,
+//     scaled by 1/k_i, shifted by -c_i/(rho k_i), clipped to [lo_i, hi_i].
+//   local update, Eq. (closed_2), fused with the dual update, Eq. (ADMM-3),
+//     and the residual sums of Eq. (termination): per component
+//     u = B_s x + lambda_s / rho, x_s = P_s u + bbar_s (P_s = -Abar_s),
+//     lambda_s += rho (B_s x - x_s).  One warp per tile of components (see
+//     pack.cpp); operator columns are contiguous across lanes, u is
+//     broadcast by warp shuffles.  On check iterations each CTA writes five
+//     FP64 partial sums: ||Bx - z||^2, ||z - z_prev||^2, ||Bx||^2, ||z||^2,
+//     ||lambda||^2; they are summed in a fixed order (deterministic).
+//
+// Engines:
+//   GRAPH       z_kernel + x_kernel per iteration and finalize_kernel every
+//               K iterations, captured once as the body of a device-side
+//               while node: one graph launch runs the whole solve.
+//   HOSTLOOP    the same kernels, stop test read back by the host.
+//   PERSISTENT  one cooperative launch for the whole solve.  CTA b owns a
+//               chunk of components; each iteration it recomputes the global
+//               update for the globals its chunk copies (its halo) into
+//               shared memory from ping-pong x_s / lambda buffers, then runs
+//               the local and dual updates.  CTAs synchronize only with their
+//               neighbours (chunks sharing a global) through per-CTA
+//               iteration flags (release / acquire); every K iterations a
+//               ticket counter elects the last CTA to finalize the residuals.
+//               Every wait is bounded in time: on expiry the CTA records
+//               where, sets OPF_ERR_TIMEOUT and all CTAs leave.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -35,34 +46,183 @@ namespace opf {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                   \
     } while (0)
 
-constexpr int kXWarps = 8;          // warps per block of x_kernel
-constexpr int kXBlocksMax = 148 * 8;
+constexpr int kXWarps = 8;          // warps per CTA of x_kernel / persistent_kernel
 constexpr int kZThreads = 256;
 constexpr int kFinThreads = 256;
 constexpr int kMaxBigN = 256;
 
-// ------------------------------------------------------------------ kernels
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+
+// Eq. (global_sparse) for global g from the copies in (xr, lr).
+template <typename T, bool CG>
+__device__ __forceinline__ T global_value(const View<T>& v, int g, const T* xr, const T* lr, T inv_rho) {
+    const int b = v.gptr[g], e = v.gptr[g + 1];
+    T s = 0;
+    for (int j = b; j < e; ++j) {
+        const int l = v.gcol[j];
+        if (CG) s += ldcg(xr + l) - ldcg(lr + l) * inv_rho;
+        else s += xr[l] - lr[l] * inv_rho;
+    }
+    const T xh = s * v.invk[g] - v.cik[g] * inv_rho;
+    return fmin(fmax(xh, v.lo[g]), v.hi[g]);
+}
+
+// Local update + dual update of one tile (Eq. closed_2, Eq. ADMM-3).
+// getv(j, meta) returns the gathered global value (B_s x)_j for local j.
+template <typename T, typename GETV>
+__device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int lane, T rho, T inv_rho,
+                                            const T* xr, const T* lr, T* xw, T* lw, bool want, double* acc,
+                                            T* us, GETV getv) {
+    if (!tl.big) {
+        const int L = tl.L, nmax = tl.nmax;
+        const bool act = lane < L;
+        const int j = tl.loc0 + lane;
+        int n = 0, base = 0;
+        T vv = 0, lo = 0, xo = 0, u = 0;
+        if (act) {
+            const int m = v.meta[j];
+            n = (m >> 16) & 0xFF;
+            base = (m >> 24) & 0xFF;
+            vv = getv(j, m);
+            lo = ldcg(lr + j);
+            xo = ldcg(xr + j);
+            u = vv + lo * inv_rho;
+        }
+        const T* Pm = v.P + tl.mat0 + lane;
+        T y = 0;
+#pragma unroll 4
+        for (int c = 0; c < nmax; ++c) {
+            const T uc = __shfl_sync(0xffffffffu, u, (base + c) & 31);
+            if (act && c < n) y = fma(Pm[c * L], uc, y);
+        }
+        if (act) {
+            const T xn = y + v.bbar[j];
+            const T ln = lo + rho * (vv - xn);
+            xw[j] = xn;
+            lw[j] = ln;
+            if (want) {
+                const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
+                acc[0] += pr * pr; acc[1] += dz * dz;
+                acc[2] += (double)vv * (double)vv; acc[3] += (double)xn * (double)xn; acc[4] += (double)ln * (double)ln;
+            }
+        }
+    } else {
+        const int n = tl.nmax;
+        for (int r = lane; r < n; r += 32) {
+            const int j = tl.loc0 + r;
+            us[r] = getv(j, v.meta[j]) + ldcg(lr + j) * inv_rho;
+        }
+        __syncwarp();
+        const T* Pm = v.P + tl.mat0;
+        for (int r = lane; r < n; r += 32) {
+            T y = 0;
+            for (int c = 0; c < n; ++c) y = fma(Pm[c * n + r], us[c], y);
+            const int j = tl.loc0 + r;
+            const T vv = getv(j, v.meta[j]);
+            const T lo = ldcg(lr + j), xo = ldcg(xr + j);
+            const T xn = y + v.bbar[j];
+            const T ln = lo + rho * (vv - xn);
+            xw[j] = xn;
+            lw[j] = ln;
+            if (want) {
+                const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
+                acc[0] += pr * pr; acc[1] += dz * dz;
+                acc[2] += (double)vv * (double)vv; acc[3] += (double)xn * (double)xn; acc[4] += (double)ln * (double)ln;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// CTA-wide fixed-order reduction of acc[5]; threads 0..4 write out[0..4].
+__device__ __forceinline__ void cta_partials(double* acc, double (*red)[5], double* out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < 5; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0)
+        for (int k = 0; k < 5; ++k) red[warp][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double s = 0;
+        for (int w = 0; w < kXWarps; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// Fixed-order sum of nparts partial records (8 doubles each) by one CTA of
+// kFinThreads threads; thread 0 gets the five sums in tot.
+__device__ __forceinline__ void sum_partials(const double* partials, int nparts, double (*sh)[kFinThreads],
+                                             double* tot, bool cg) {
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nparts; b += kFinThreads)
+        for (int k = 0; k < 5; ++k) s[k] += cg ? __ldcg(partials + (size_t)b * 8 + k) : partials[(size_t)b * 8 + k];
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) tot[k] = sh[k][0];
+}
+
+// Eq. (termination) from the five sums after `it` iterations; returns stop.
+__device__ __forceinline__ int decide(Ctl* ctl, const double* s, int it) {
+    const double pres = sqrt(s[0]);
+    const double dres = ctl->rho * sqrt(s[1]);
+    const double ep = ctl->eps_rel * fmax(sqrt(s[2]), sqrt(s[3]));
+    const double ed = ctl->eps_rel * sqrt(s[4]);
+    ctl->pres = pres; ctl->dres = dres; ctl->eps_prim = ep; ctl->eps_dual = ed;
+    ctl->checks += 1;
+    const bool ok_abs = pres <= ctl->eps_abs_prim && dres <= ctl->eps_abs_dual;
+    const bool ok_rel = pres <= ep && dres <= ed;
+    if (ok_rel && ctl->first_rel < 0) ctl->first_rel = it;
+    const int cr = ctl->criterion;
+    const bool conv = (cr == OPF_CRIT_ABS && ok_abs) || (cr == OPF_CRIT_REL && ok_rel) ||
+                      (cr == OPF_CRIT_BOTH && ok_abs && ok_rel);
+    if (!isfinite(pres) || !isfinite(dres)) {
+        ctl->status = CTL_NUMERIC;
+        return 1;
+    }
+    if (conv) {
+        ctl->status = CTL_CONVERGED;
+        return 1;
+    }
+    if (it >= ctl->max_iter) {
+        ctl->status = CTL_MAXITER;
+        return 1;
+    }
+    return 0;
+}
+
+// ----------------------------------------------------- graph / hostloop
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) z_kernel(View<T> v, int q) {
     const Ctl* ctl = v.ctl;
     if (ctl->iter + q >= ctl->max_iter) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.ng) return;
-    const T inv_rho = (T)ctl->inv_rho;
-    const int b = v.gptr[i], e = v.gptr[i + 1];
-    T s = 0;
-    for (int j = b; j < e; ++j) {
-        const int l = v.gcol[j];
-        s += v.xl[l] - v.lam[l] * inv_rho;
-    }
-    const T xh = s * v.invk[i] - v.cik[i] * inv_rho;
-    v.zg[i] = fmin(fmax(xh, v.lo[i]), v.hi[i]);
-}
-
-__device__ __forceinline__ double warp_sum(double a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    return a;
+    v.zg[i] = global_value<T, false>(v, i, v.xl, v.lam, (T)ctl->inv_rho);
 }
 
 template <typename T>
@@ -75,77 +235,15 @@ __global__ void __launch_bounds__(kXWarps * 32) x_kernel(View<T> v, int q) {
     __shared__ T us[kXWarps][kMaxBigN];
     __shared__ double red[kXWarps][5];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-    for (int t = blockIdx.x * kXWarps + warp; t < v.ntiles; t += gridDim.x * kXWarps) {
-        const Tile tl = v.tiles[t];
-        const int n = tl.n;
-        if (n <= 32) {
-            const int L = tl.ncomp * n;
-            const bool act = lane < L;
-            const int base = (lane / n) * n;
-            const int j = tl.loc0 + lane;
-            T vv = 0, lo = 0, xo = 0, u = 0;
-            if (act) {
-                vv = v.zg[v.gidx[j]];
-                lo = v.lam[j];
-                xo = v.xl[j];
-                u = vv + lo * inv_rho;
-            }
-            const T* Pm = v.P + tl.mat0 + lane;
-            T y = 0;
-#pragma unroll 4
-            for (int c = 0; c < n; ++c) {
-                const T uc = __shfl_sync(0xffffffffu, u, (base + c) & 31);
-                if (act) y = fma(Pm[(size_t)c * L], uc, y);
-            }
-            if (act) {
-                const T xn = y + v.bbar[j];
-                const T ln = lo + rho * (vv - xn);
-                v.xl[j] = xn;
-                v.lam[j] = ln;
-                if (want) {
-                    const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
-                    a0 += pr * pr; a1 += dz * dz;
-                    a2 += (double)vv * (double)vv; a3 += (double)xn * (double)xn; a4 += (double)ln * (double)ln;
-                }
-            }
-        } else {
-            for (int r = lane; r < n; r += 32) {
-                const int j = tl.loc0 + r;
-                us[warp][r] = v.zg[v.gidx[j]] + v.lam[j] * inv_rho;
-            }
-            __syncwarp();
-            const T* Pm = v.P + tl.mat0;
-            for (int r = lane; r < n; r += 32) {
-                T y = 0;
-                for (int c = 0; c < n; ++c) y = fma(Pm[(size_t)c * n + r], us[warp][c], y);
-                const int j = tl.loc0 + r;
-                const T vv = v.zg[v.gidx[j]];
-                const T lo = v.lam[j], xo = v.xl[j];
-                const T xn = y + v.bbar[j];
-                const T ln = lo + rho * (vv - xn);
-                v.xl[j] = xn;
-                v.lam[j] = ln;
-                if (want) {
-                    const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
-                    a0 += pr * pr; a1 += dz * dz;
-                    a2 += (double)vv * (double)vv; a3 += (double)xn * (double)xn; a4 += (double)ln * (double)ln;
-                }
-            }
-            __syncwarp();
-        }
-    }
+    const BlockInfo bi = v.blocks[blockIdx.x];
+    double acc[5] = {0, 0, 0, 0, 0};
+    const T* zg = v.zg;
+    const int32_t* gidx = v.gidx;
+    auto getv = [zg, gidx](int j, int) { return zg[gidx[j]]; };
+    for (int t = bi.tile0 + warp; t < bi.tile1; t += kXWarps)
+        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
     if (!want) return;
-    a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
-    if (lane == 0) {
-        red[warp][0] = a0; red[warp][1] = a1; red[warp][2] = a2; red[warp][3] = a3; red[warp][4] = a4;
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double s = 0;
-        for (int w = 0; w < kXWarps; ++w) s += red[w][threadIdx.x];
-        v.partials[(size_t)blockIdx.x * 8 + threadIdx.x] = s;
-    }
+    cta_partials(acc, red, v.partials + (size_t)blockIdx.x * 8);
 }
 
 template <typename T>
@@ -154,47 +252,146 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(View<T> v, cudaGr
     const int iter = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
     const int ndone = max(0, min(K, maxit - iter));
     __shared__ double sh[5][kFinThreads];
-    double s[5] = {0, 0, 0, 0, 0};
-    if (ndone > 0)
-        for (int b = threadIdx.x; b < v.nparts; b += kFinThreads)
-            for (int k = 0; k < 5; ++k) s[k] += v.partials[(size_t)b * 8 + k];
-    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = s[k];
-    __syncthreads();
-    for (int w = kFinThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-        __syncthreads();
-    }
+    __shared__ double tot[5];
+    if (ndone > 0) sum_partials(v.partials, v.nblocks, sh, tot, false);
     if (threadIdx.x != 0) return;
     const int it = iter + ndone;
     ctl->iter = it;
     int stop = 0;
-    if (ndone > 0) {
-        const double pres = sqrt(sh[0][0]);
-        const double dres = ctl->rho * sqrt(sh[1][0]);
-        const double ep = ctl->eps_rel * fmax(sqrt(sh[2][0]), sqrt(sh[3][0]));
-        const double ed = ctl->eps_rel * sqrt(sh[4][0]);
-        ctl->pres = pres; ctl->dres = dres; ctl->eps_prim = ep; ctl->eps_dual = ed;
-        ctl->checks += 1;
-        const bool ok_abs = pres <= ctl->eps_abs_prim && dres <= ctl->eps_abs_dual;
-        const bool ok_rel = pres <= ep && dres <= ed;
-        if (ok_rel && ctl->first_rel < 0) ctl->first_rel = it;
-        const int cr = ctl->criterion;
-        const bool conv = (cr == OPF_CRIT_ABS && ok_abs) || (cr == OPF_CRIT_REL && ok_rel) ||
-                          (cr == OPF_CRIT_BOTH && ok_abs && ok_rel);
-        if (!isfinite(pres) || !isfinite(dres)) {
-            ctl->status = CTL_NUMERIC; stop = 1;
-        } else if (conv) {
-            ctl->status = CTL_CONVERGED; stop = 1;
-        }
-    }
+    if (ndone > 0) stop = decide(ctl, tot, it);
     if (!stop && it >= maxit) {
-        ctl->status = CTL_MAXITER; stop = 1;
+        ctl->status = CTL_MAXITER;
+        stop = 1;
     }
     ctl->stop = stop;
     if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
+// ------------------------------------------------------------- persistent
+// Bounded wait until every neighbour CTA has completed `t` iterations.
+// Returns false when the deadline passed or another CTA aborted.
+template <typename T>
+__device__ bool wait_neighbours(const View<T>& v, const BlockInfo& bi, int t, unsigned long long tmo, int* s_ok) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long deadline = now_ns() + tmo;
+        for (int q = bi.nbr0; q < bi.nbr1 && ok; ++q) {
+            const int32_t* f = v.flags + v.nbrs[q];
+            while (ld_acquire(f) < t) {
+                if (ld_acquire(&v.ctl->abort)) { ok = 0; break; }
+                if (now_ns() > deadline) {
+                    if (atomicCAS(&v.ctl->abort, 0, 1) == 0) { v.ctl->status = CTL_TIMEOUT; v.ctl->timeout_where = 1; }
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    const bool r = *s_ok != 0;
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* zs = reinterpret_cast<T*>(smem_raw);
+    __shared__ T us[kXWarps][kMaxBigN];
+    __shared__ double red[kXWarps][5];
+    __shared__ double sh[5][kFinThreads];
+    __shared__ double tot[5];
+    __shared__ int s_last, s_stop, s_ok;
+    Ctl* ctl = v.ctl;
+    const int b = blockIdx.x;
+    const BlockInfo bi = v.blocks[b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it0 = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
+    const T rho = (T)ctl->rho, inv_rho = (T)ctl->inv_rho;
+    const unsigned long long tmo = ctl->timeout_ns;
+    const bool withhold = (ctl->skip_block == b);
+    int t = 0, checkno = 0;
+    bool done = it0 >= maxit;
+    while (!done) {
+        if (t > 0 && !wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+        const T* xr = (t & 1) ? v.xl2 : v.xl;
+        const T* lr = (t & 1) ? v.lam2 : v.lam;
+        T* xw = (t & 1) ? v.xl : v.xl2;
+        T* lw = (t & 1) ? v.lam : v.lam2;
+        // global update of the chunk's halo, Eq. (global_sparse)
+        for (int h = bi.halo0 + threadIdx.x; h < bi.halo1; h += blockDim.x) {
+            const int g = v.halo_gid[h];
+            const T z = global_value<T, true>(v, g, xr, lr, inv_rho);
+            zs[h - bi.halo0] = z;
+            if (v.halo_own[h]) v.zg[g] = z;
+        }
+        __syncthreads();
+        const int nrem = maxit - (it0 + t);
+        const bool check = ((t + 1) % K == 0) || nrem == 1;
+        double acc[5] = {0, 0, 0, 0, 0};
+        auto getv = [zs](int, int m) { return zs[m & 0xFFFF]; };
+        for (int q = bi.tile0 + warp; q < bi.tile1; q += kXWarps)
+            tile_update<T>(v, v.tiles[q], lane, rho, inv_rho, xr, lr, xw, lw, check, acc, us[warp], getv);
+        __syncthreads();
+        ++t;
+        if (threadIdx.x == 0 && !withhold) {
+            __threadfence();
+            st_release(v.flags + b, t);
+        }
+        if (check) {
+            cta_partials(acc, red, v.partials + (size_t)b * 8);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const unsigned long long ticket = atomicAdd(&ctl->arrive, 1ull);
+                s_last = ticket == (unsigned long long)v.nblocks * (checkno + 1) - 1;
+            }
+            __syncthreads();
+            if (s_last) {
+                sum_partials(v.partials, v.nblocks, sh, tot, true);
+                if (threadIdx.x == 0) {
+                    ctl->iter = it0 + t;
+                    ctl->stop = decide(ctl, tot, it0 + t);
+                    __threadfence();
+                    st_release(&ctl->decided, checkno + 1);
+                }
+            }
+            if (threadIdx.x == 0) {
+                int ok = 1;
+                const unsigned long long deadline = now_ns() + tmo;
+                while (ld_acquire(&ctl->decided) < checkno + 1) {
+                    if (ld_acquire(&ctl->abort)) { ok = 0; break; }
+                    if (now_ns() > deadline) {
+                        if (atomicCAS(&ctl->abort, 0, 1) == 0) { ctl->status = CTL_TIMEOUT; ctl->timeout_where = 2; }
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                s_ok = ok;
+                s_stop = ok ? ld_acquire(&ctl->stop) : 1;
+            }
+            __syncthreads();
+            ++checkno;
+            if (!s_ok) return;
+            if (s_stop) done = true;
+        }
+        if (it0 + t >= maxit) done = true;
+    }
+    // after an odd count the newest iterate is in the second buffer: move the
+    // chunk's locals home once the neighbours have finished reading
+    if (t & 1) {
+        if (!wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+        for (int j = bi.loc0 + threadIdx.x; j < bi.loc1; j += blockDim.x) {
+            v.xl[j] = __ldcg(v.xl2 + j);
+            v.lam[j] = __ldcg(v.lam2 + j);
+        }
+    }
+}
+
+// ------------------------------------------------------------ misc kernels
 template <typename T>
 __global__ void init_kernel(View<T> v) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,12 +444,12 @@ struct Arena {
 
 struct Layout {
     size_t lo, hi, invk, cik, zg, lo32, hi32, invk32, cik32, zg32;
-    size_t gptr, gcol, gidx, tiles, cost, partials, ctl;
-    size_t xl, lam, bbar, xl0, xl32, lam32, bbar32, xl0_32, P64, P32;
+    size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, flags, cost, partials, ctl;
+    size_t xl, lam, xl2, lam2, bbar, xl0, xl32, lam32, xl2_32, lam2_32, bbar32, xl0_32, P64, P32;
     size_t total;
 };
 
-Layout layout_of(const opf_problem* p, int nparts) {
+Layout layout_of(const opf_problem* p) {
     const Packed& k = p->pk;
     Arena a;
     Layout L;
@@ -261,31 +458,32 @@ Layout layout_of(const opf_problem* p, int nparts) {
     L.lo32 = a.take<float>(k.ng); L.hi32 = a.take<float>(k.ng); L.invk32 = a.take<float>(k.ng);
     L.cik32 = a.take<float>(k.ng); L.zg32 = a.take<float>(k.ng);
     L.gptr = a.take<int32_t>(k.ng + 1); L.gcol = a.take<int32_t>(k.nl); L.gidx = a.take<int32_t>(k.nl);
-    L.tiles = a.take<Tile>(k.tiles.size()); L.cost = a.take<double>(k.ng);
-    L.partials = a.take<double>((size_t)nparts * 8); L.ctl = a.take<Ctl>(1);
-    L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.bbar = a.take<double>(k.nl); L.xl0 = a.take<double>(k.nl);
-    L.xl32 = a.take<float>(k.nl); L.lam32 = a.take<float>(k.nl); L.bbar32 = a.take<float>(k.nl); L.xl0_32 = a.take<float>(k.nl);
+    L.meta = a.take<int32_t>(k.nl);
+    L.tiles = a.take<Tile>(k.tiles.size()); L.blocks = a.take<BlockInfo>(k.blocks.size());
+    L.halo_gid = a.take<int32_t>(k.halo_gid.size()); L.halo_own = a.take<uint8_t>(k.halo_own.size());
+    L.nbrs = a.take<int32_t>(k.nbrs.size() + 1); L.flags = a.take<int32_t>(k.nblocks);
+    L.cost = a.take<double>(k.ng);
+    L.partials = a.take<double>((size_t)k.nblocks * 8); L.ctl = a.take<Ctl>(1);
+    L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.xl2 = a.take<double>(k.nl); L.lam2 = a.take<double>(k.nl);
+    L.bbar = a.take<double>(k.nl); L.xl0 = a.take<double>(k.nl);
+    L.xl32 = a.take<float>(k.nl); L.lam32 = a.take<float>(k.nl); L.xl2_32 = a.take<float>(k.nl); L.lam2_32 = a.take<float>(k.nl);
+    L.bbar32 = a.take<float>(k.nl); L.xl0_32 = a.take<float>(k.nl);
     L.P64 = a.take<double>(k.mat_elems); L.P32 = a.take<float>(k.mat_elems);
     L.total = (a.off + 255) & ~size_t(255);
     return L;
-}
-
-int nparts_of(const opf_problem* p) {
-    const int nt = (int)p->pk.tiles.size();
-    int nb = (nt + kXWarps - 1) / kXWarps;
-    if (nb < 1) nb = 1;
-    if (nb > kXBlocksMax) nb = kXBlocksMax;
-    return nb;
 }
 
 template <typename T>
 View<T> view_of(const opf_problem* p, const DevPrec& d) {
     View<T> v;
     v.lo = (const T*)d.lo; v.hi = (const T*)d.hi; v.invk = (const T*)d.invk; v.cik = (const T*)d.cik;
-    v.zg = (T*)d.zg; v.gptr = p->gptr; v.gcol = p->gcol; v.xl = (T*)d.xl; v.lam = (T*)d.lam;
-    v.bbar = (const T*)d.bbar; v.xl0 = (const T*)d.xl0; v.gidx = p->gidx; v.tiles = p->tiles;
+    v.zg = (T*)d.zg; v.gptr = p->gptr; v.gcol = p->gcol;
+    v.xl = (T*)d.xl; v.lam = (T*)d.lam; v.xl2 = (T*)d.xl2; v.lam2 = (T*)d.lam2;
+    v.bbar = (const T*)d.bbar; v.xl0 = (const T*)d.xl0; v.gidx = p->gidx; v.meta = p->meta;
+    v.tiles = p->tiles; v.blocks = p->blocks; v.halo_gid = p->halo_gid; v.halo_own = p->halo_own;
+    v.nbrs = p->nbrs; v.flags = p->flags;
     v.P = (const T*)d.P; v.cost = p->cost; v.partials = p->partials; v.ctl = p->ctl;
-    v.ng = p->pk.ng; v.nl = p->pk.nl; v.ntiles = (int)p->pk.tiles.size(); v.nparts = p->nparts;
+    v.ng = p->pk.ng; v.nl = p->pk.nl; v.nblocks = p->pk.nblocks;
     return v;
 }
 
@@ -301,9 +499,11 @@ struct DeviceGuard {
 };
 
 template <typename T>
+const DevPrec& prec_of(const opf_problem* p) { return sizeof(T) == 8 ? p->d64 : p->d32; }
+
+template <typename T>
 void enqueue_init(opf_problem* p, cudaStream_t s) {
-    const DevPrec& d = sizeof(T) == 8 ? p->d64 : p->d32;
-    View<T> v = view_of<T>(p, d);
+    View<T> v = view_of<T>(p, prec_of<T>(p));
     const int n = std::max(p->pk.nl, p->pk.ng) + 1;
     init_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(v);
     OPF_CUDA(cudaGetLastError());
@@ -311,19 +511,18 @@ void enqueue_init(opf_problem* p, cudaStream_t s) {
 
 template <typename T>
 void enqueue_iterations(opf_problem* p, int K, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
-    const DevPrec& d = sizeof(T) == 8 ? p->d64 : p->d32;
-    View<T> v = view_of<T>(p, d);
+    View<T> v = view_of<T>(p, prec_of<T>(p));
     const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
     for (int q = 0; q < K; ++q) {
         z_kernel<T><<<zb, kZThreads, 0, s>>>(v, q);
-        x_kernel<T><<<p->nparts, kXWarps * 32, 0, s>>>(v, q);
+        x_kernel<T><<<p->pk.nblocks, kXWarps * 32, 0, s>>>(v, q);
     }
     finalize_kernel<T><<<1, kFinThreads, 0, s>>>(v, h, use_cond);
     OPF_CUDA(cudaGetLastError());
 }
 
 template <typename T>
-GraphEntry& get_graph(opf_problem* p, int K, cudaStream_t s) {
+GraphEntry& get_graph(opf_problem* p, int K) {
     const int prec = sizeof(T) == 8 ? OPF_FP64 : OPF_FP32;
     auto key = std::make_pair(prec, K);
     auto it = p->graphs.find(key);
@@ -340,7 +539,6 @@ GraphEntry& get_graph(opf_problem* p, int K, cudaStream_t s) {
     cudaGraphNode_t cnode;
     OPF_CUDA(cudaGraphAddNode(&cnode, g.graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    // capture one body (K iterations + finalize) into the while node's graph
     cudaStream_t cs;
     OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     OPF_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -356,15 +554,51 @@ GraphEntry& get_graph(opf_problem* p, int K, cudaStream_t s) {
     OPF_CUDA(cudaStreamEndCapture(cs, &captured));
     OPF_CUDA(cudaStreamDestroy(cs));
     OPF_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
-    (void)s;
     return p->graphs.emplace(key, g).first->second;
 }
 
 template <typename T>
+size_t persistent_smem(const opf_problem* p) { return (size_t)std::max(1, p->pk.max_halo) * sizeof(T); }
+
+template <typename T>
+bool persistent_fits(const opf_problem* p) {
+    const size_t smem = persistent_smem<T>(p);
+    if (smem > 160 * 1024) return false;
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop) return false;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(persistent_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<T>, kXWarps * 32, smem) != cudaSuccess)
+        return false;
+    return (long long)per_sm * sms >= p->pk.nblocks;
+}
+
+template <typename T>
+void launch_persistent(opf_problem* p, cudaStream_t s) {
+    View<T> v = view_of<T>(p, prec_of<T>(p));
+    const size_t smem = persistent_smem<T>(p);
+    void* args[] = {&v};
+    OPF_CUDA(cudaMemsetAsync(p->flags, 0, sizeof(int32_t) * p->pk.nblocks, s));
+    OPF_CUDA(cudaLaunchCooperativeKernel((const void*)persistent_kernel<T>, dim3(p->pk.nblocks),
+                                         dim3(kXWarps * 32), args, smem, s));
+}
+
+template <typename T>
 void run_solve(opf_problem* p, const opf_params& prm, cudaStream_t s) {
-    const int engine = prm.engine == OPF_ENGINE_AUTO ? OPF_ENGINE_GRAPH : prm.engine;
-    if (engine == OPF_ENGINE_GRAPH) {
-        GraphEntry& g = get_graph<T>(p, prm.check_every, s);
+    int engine = prm.engine;
+    if (engine == OPF_ENGINE_AUTO) engine = persistent_fits<T>(p) ? OPF_ENGINE_PERSISTENT : OPF_ENGINE_GRAPH;
+    if (engine == OPF_ENGINE_PERSISTENT) {
+        if (!persistent_fits<T>(p))
+            throw Error(OPF_ERR_INVALID_ARG, "persistent engine: the chunks do not fit co-resident on this device");
+        launch_persistent<T>(p, s);
+        OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        OPF_CUDA(cudaStreamSynchronize(s));
+    } else if (engine == OPF_ENGINE_GRAPH) {
+        GraphEntry& g = get_graph<T>(p, prm.check_every);
         OPF_CUDA(cudaGraphLaunch(g.exec, s));
         OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         OPF_CUDA(cudaStreamSynchronize(s));
@@ -376,8 +610,8 @@ void run_solve(opf_problem* p, const opf_params& prm, cudaStream_t s) {
             if (p->ctl_host->stop) break;
         }
     }
-    const DevPrec& d = sizeof(T) == 8 ? p->d64 : p->d32;
-    objective_kernel<T><<<1, 256, 0, s>>>(view_of<T>(p, d));
+    if (p->ctl_host->status == CTL_TIMEOUT) return;
+    objective_kernel<T><<<1, 256, 0, s>>>(view_of<T>(p, prec_of<T>(p)));
     OPF_CUDA(cudaGetLastError());
     OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     OPF_CUDA(cudaStreamSynchronize(s));
@@ -405,14 +639,53 @@ void sync_state_to(opf_problem* p, int prec, cudaStream_t s) {
     p->cur_prec = prec;
 }
 
+template <typename T>
+double time_graph(opf_problem* p, int which, int reps, cudaStream_t s) {
+    View<T> v = view_of<T>(p, prec_of<T>(p));
+    const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
+    cudaStream_t cs;
+    OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    OPF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < reps; ++r) {
+        if (which == 0) z_kernel<T><<<zb, kZThreads, 0, cs>>>(v, 0);
+        else if (which <= 2) x_kernel<T><<<p->pk.nblocks, kXWarps * 32, 0, cs>>>(v, 0);
+        else finalize_kernel<T><<<1, kFinThreads, 0, cs>>>(v, 0, 0);
+    }
+    OPF_CUDA(cudaStreamEndCapture(cs, &g));
+    OPF_CUDA(cudaStreamDestroy(cs));
+    OPF_CUDA(cudaGraphInstantiate(&ge, g, 0));
+    cudaEvent_t e0, e1;
+    OPF_CUDA(cudaEventCreate(&e0));
+    OPF_CUDA(cudaEventCreate(&e1));
+    OPF_CUDA(cudaGraphLaunch(ge, s));            // warm
+    OPF_CUDA(cudaEventRecord(e0, s));
+    OPF_CUDA(cudaGraphLaunch(ge, s));
+    OPF_CUDA(cudaEventRecord(e1, s));
+    OPF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    OPF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    return 1e3 * (double)ms / reps;
+}
+
 }  // namespace
 
-size_t device_bytes(const opf_problem* p) { return layout_of(p, nparts_of(p)).total; }
+size_t device_bytes(const opf_problem* p) { return layout_of(p).total; }
+
+int device_auto_engine(const opf_problem* p, int precision) {
+    DeviceGuard g(p->device);
+    const bool ok = precision == OPF_FP64 ? persistent_fits<double>(p) : persistent_fits<float>(p);
+    return ok ? OPF_ENGINE_PERSISTENT : OPF_ENGINE_GRAPH;
+}
 
 void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     if (p->uploaded) throw Error(OPF_ERR_STATE, "problem already uploaded");
-    const int np = nparts_of(p);
-    const Layout L = layout_of(p, np);
+    const Layout L = layout_of(p);
     OPF_CUDA(cudaGetDevice(&p->device));
     if (arena) {
         if (bytes < L.total) throw Error(OPF_ERR_INVALID_ARG, "device arena too small");
@@ -426,20 +699,23 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
         p->owns_arena = true;
     }
     p->arena_bytes = L.total;
-    p->nparts = np;
     char* a = p->arena;
     const Packed& k = p->pk;
     p->d64.lo = a + L.lo; p->d64.hi = a + L.hi; p->d64.invk = a + L.invk; p->d64.cik = a + L.cik; p->d64.zg = a + L.zg;
     p->d32.lo = a + L.lo32; p->d32.hi = a + L.hi32; p->d32.invk = a + L.invk32; p->d32.cik = a + L.cik32; p->d32.zg = a + L.zg32;
-    p->d64.xl = a + L.xl; p->d64.lam = a + L.lam; p->d64.bbar = a + L.bbar; p->d64.xl0 = a + L.xl0; p->d64.P = a + L.P64;
-    p->d32.xl = a + L.xl32; p->d32.lam = a + L.lam32; p->d32.bbar = a + L.bbar32; p->d32.xl0 = a + L.xl0_32; p->d32.P = a + L.P32;
+    p->d64.xl = a + L.xl; p->d64.lam = a + L.lam; p->d64.xl2 = a + L.xl2; p->d64.lam2 = a + L.lam2;
+    p->d64.bbar = a + L.bbar; p->d64.xl0 = a + L.xl0; p->d64.P = a + L.P64;
+    p->d32.xl = a + L.xl32; p->d32.lam = a + L.lam32; p->d32.xl2 = a + L.xl2_32; p->d32.lam2 = a + L.lam2_32;
+    p->d32.bbar = a + L.bbar32; p->d32.xl0 = a + L.xl0_32; p->d32.P = a + L.P32;
     p->gptr = (int32_t*)(a + L.gptr); p->gcol = (int32_t*)(a + L.gcol); p->gidx = (int32_t*)(a + L.gidx);
-    p->tiles = (Tile*)(a + L.tiles); p->cost = (double*)(a + L.cost); p->partials = (double*)(a + L.partials);
+    p->meta = (int32_t*)(a + L.meta); p->tiles = (Tile*)(a + L.tiles); p->blocks = (BlockInfo*)(a + L.blocks);
+    p->halo_gid = (int32_t*)(a + L.halo_gid); p->halo_own = (uint8_t*)(a + L.halo_own);
+    p->nbrs = (int32_t*)(a + L.nbrs); p->flags = (int32_t*)(a + L.flags);
+    p->cost = (double*)(a + L.cost); p->partials = (double*)(a + L.partials);
     p->ctl = (Ctl*)(a + L.ctl);
     if (!p->ctl_host) OPF_CUDA(cudaMallocHost((void**)&p->ctl_host, sizeof(Ctl)));
     std::memset(p->ctl_host, 0, sizeof(Ctl));
 
-    // host staging of every array (pageable; the copies are synchronized below)
     auto h2d = [&](void* dst, const void* src, size_t n) {
         if (n) OPF_CUDA(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s));
     };
@@ -454,13 +730,19 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     h2d(p->d64.invk, k.invk.data(), k.ng * 8); h2d(p->d64.cik, k.cik.data(), k.ng * 8);
     h2d32(p->d32.lo, M.lo); h2d32(p->d32.hi, M.hi); h2d32(p->d32.invk, k.invk); h2d32(p->d32.cik, k.cik);
     h2d(p->gptr, k.gptr.data(), (k.ng + 1) * 4); h2d(p->gcol, k.gcol.data(), k.nl * 4); h2d(p->gidx, k.gidx.data(), k.nl * 4);
+    h2d(p->meta, k.meta.data(), k.nl * 4);
     h2d(p->tiles, k.tiles.data(), k.tiles.size() * sizeof(Tile));
+    h2d(p->blocks, k.blocks.data(), k.blocks.size() * sizeof(BlockInfo));
+    h2d(p->halo_gid, k.halo_gid.data(), k.halo_gid.size() * 4);
+    h2d(p->halo_own, k.halo_own.data(), k.halo_own.size());
+    h2d(p->nbrs, k.nbrs.data(), k.nbrs.size() * 4);
     h2d(p->cost, M.c.data(), k.ng * 8);
     h2d(p->d64.bbar, k.bbar.data(), k.nl * 8); h2d(p->d64.xl0, k.xl0.data(), k.nl * 8);
     h2d32(p->d32.bbar, k.bbar); h2d32(p->d32.xl0, k.xl0);
     h2d(p->d64.P, k.P.data(), k.mat_elems * 8);
     h2d32(p->d32.P, k.P);
-    OPF_CUDA(cudaMemsetAsync(p->partials, 0, (size_t)np * 8 * sizeof(double), s));
+    OPF_CUDA(cudaMemsetAsync(p->partials, 0, (size_t)k.nblocks * 8 * sizeof(double), s));
+    OPF_CUDA(cudaMemsetAsync(p->flags, 0, (size_t)k.nblocks * sizeof(int32_t), s));
     OPF_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(Ctl), s));
     enqueue_init<double>(p, s);
     enqueue_init<float>(p, s);
@@ -481,7 +763,6 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
     } else {
         sync_state_to(p, prec, s);
     }
-    // parameters -> device control block (iteration state kept)
     OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     OPF_CUDA(cudaStreamSynchronize(s));
     Ctl c = *p->ctl_host;
@@ -491,6 +772,8 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
     const long long mi = (long long)c.iter + prm.max_iter;
     c.max_iter = (int32_t)(mi > INT32_MAX ? INT32_MAX : mi);
     c.status = CTL_RUNNING; c.stop = 0;
+    c.arrive = 0; c.decided = 0; c.abort = 0; c.timeout_where = 0;
+    c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
     *p->ctl_host = c;
     OPF_CUDA(cudaMemcpyAsync(p->ctl, p->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     if (prm.max_iter > 0) {
@@ -504,6 +787,7 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
     int32_t st = OPF_NOT_CONVERGED;
     if (r.status == CTL_CONVERGED) st = OPF_OK;
     else if (r.status == CTL_NUMERIC) st = OPF_ERR_NUMERIC;
+    else if (r.status == CTL_TIMEOUT) st = OPF_ERR_TIMEOUT;
     else if (prm.criterion == OPF_CRIT_NEVER && r.status == CTL_MAXITER) st = OPF_OK;
     if (info) {
         info->status = st;
@@ -513,6 +797,9 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
         info->objective = r.objective;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    if (st == OPF_ERR_TIMEOUT)
+        throw Error(OPF_ERR_TIMEOUT, "persistent engine: a bounded wait expired (site " +
+                                         std::to_string(r.timeout_where) + "); the iterate is undefined");
     return st;
 }
 
@@ -558,45 +845,6 @@ void device_set_state(opf_problem* p, const double* xl, const double* lam, cudaS
     p->cold = false;
 }
 
-namespace {
-
-template <typename T>
-double time_graph(opf_problem* p, int which, int reps, cudaStream_t s) {
-    const DevPrec& d = sizeof(T) == 8 ? p->d64 : p->d32;
-    View<T> v = view_of<T>(p, d);
-    const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
-    cudaStream_t cs;
-    OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    OPF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    for (int r = 0; r < reps; ++r) {
-        if (which == 0) z_kernel<T><<<zb, kZThreads, 0, cs>>>(v, 0);
-        else if (which <= 2) x_kernel<T><<<p->nparts, kXWarps * 32, 0, cs>>>(v, 0);
-        else finalize_kernel<T><<<1, kFinThreads, 0, cs>>>(v, 0, 0);
-    }
-    OPF_CUDA(cudaStreamEndCapture(cs, &g));
-    OPF_CUDA(cudaStreamDestroy(cs));
-    OPF_CUDA(cudaGraphInstantiate(&ge, g, 0));
-    cudaEvent_t e0, e1;
-    OPF_CUDA(cudaEventCreate(&e0));
-    OPF_CUDA(cudaEventCreate(&e1));
-    OPF_CUDA(cudaGraphLaunch(ge, s));            // warm
-    OPF_CUDA(cudaEventRecord(e0, s));
-    OPF_CUDA(cudaGraphLaunch(ge, s));
-    OPF_CUDA(cudaEventRecord(e1, s));
-    OPF_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    OPF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaGraphExecDestroy(ge);
-    cudaGraphDestroy(g);
-    return 1e3 * (double)ms / reps;
-}
-
-}  // namespace
-
 void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us) {
     DeviceGuard g(p->device);
     const int prec = prm.precision;
@@ -616,7 +864,7 @@ void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_
     // control block for timing: no launch is skipped (huge bound); K = 1 makes
     // every local-update launch compute residual partials (which == 2)
     Ctl c = *p->ctl_host;
-    c.rho = prm.rho; c.inv_rho = 1.0 / prm.rho; c.iter = 0; c.max_iter = INT32_MAX;
+    c.rho = prm.rho; c.inv_rho = 1.0 / prm.rho; c.max_iter = INT32_MAX;
     for (int which = 0; which < 4; ++which) {
         c.K = (which == 2) ? 1 : (1 << 20);
         c.iter = 0;

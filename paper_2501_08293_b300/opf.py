@@ -23,7 +23,7 @@ lib = C.CDLL(_LIB_PATH)
 OK, NOT_CONVERGED = 0, 1
 CRIT_ABS, CRIT_REL, CRIT_BOTH, CRIT_NEVER = 0, 1, 2, 3
 FP64, FP32 = 0, 1
-ENGINE_AUTO, ENGINE_GRAPH, ENGINE_HOSTLOOP = 0, 1, 2
+ENGINE_AUTO, ENGINE_GRAPH, ENGINE_HOSTLOOP, ENGINE_PERSISTENT = 0, 1, 2, 3
 
 
 class Params(C.Structure):
@@ -46,7 +46,7 @@ class Info(C.Structure):
 class Dims(C.Structure):
     _fields_ = [("n_global", C.c_int32), ("n_local", C.c_int32), ("n_comp", C.c_int32),
                 ("n_rows", C.c_int32), ("n_rows_reduced", C.c_int32), ("max_n", C.c_int32),
-                ("n_tiles", C.c_int32), ("_pad", C.c_int32), ("sum_n2", C.c_int64),
+                ("n_tiles", C.c_int32), ("n_blocks", C.c_int32), ("sum_n2", C.c_int64),
                 ("device_bytes", C.c_int64)]
 
 
@@ -70,6 +70,8 @@ EXPORTS = {
     "opf_get_solution": (C.c_int32, [_P] + [_D] * 11 + [_P]),
     "opf_get_operator": (C.c_int32, [_P, C.c_int32, _D, _D, _I]),
     "opf_profile_kernels": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
+    "opf_debug_config": (C.c_int32, [_P, C.c_int64, C.c_int32]),
+    "opf_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
     "opf_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in EXPORTS.items():
@@ -165,6 +167,14 @@ class Problem:
         _check(lib.opf_profile_kernels(self._h, C.byref(p), reps, _stream_handle(stream), _dp(us)),
                "opf_profile_kernels")
         return dict(z=us[0], x=us[1], x_partials=us[2], finalize=us[3])
+
+    def persistent_ok(self, params: Params) -> bool:
+        e = C.c_int32()
+        _check(lib.opf_engine_for(self._h, params.precision, C.byref(e)), "opf_engine_for")
+        return e.value == ENGINE_PERSISTENT
+
+    def debug_config(self, wait_limit_ns: int = 2_000_000_000, withhold_block: int = -1):
+        _check(lib.opf_debug_config(self._h, int(wait_limit_ns), int(withhold_block)), "opf_debug_config")
 
     def state(self, stream=None):
         xg = np.empty(self.dims.n_global)

@@ -166,7 +166,8 @@ def test_edge_cases(opf):
         assert rel(xg, ox) <= TOL and rel(xl, oz) <= TOL and rel(lam, ol) <= TOL
     p2.close(); ps.close()
     buses = np.zeros(1, F.BUS_DTYPE); buses["phases"] = 1; buses["w_lo"] = 0.9; buses["w_hi"] = 1.1
-    gens = np.zeros(1, F.GEN_DTYPE); gens["phases"] = 1; gens["pg_lo"] = 0.2; gens["pg_hi"] = 1
+    # feasible only at pg = 0 (no load, no shunt): pg in [0, 1]
+    gens = np.zeros(1, F.GEN_DTYPE); gens["phases"] = 1; gens["pg_lo"] = 0.0; gens["pg_hi"] = 1
     gens["qg_lo"] = -1; gens["qg_hi"] = 1; gens["cost"] = 1
     pg = opf.Problem(buses, np.zeros(0, F.LINE_DTYPE), gens, np.zeros(0, F.LOAD_DTYPE))
     info = pg.solve(opf.default_params(max_iter=5000, check_every=1))
@@ -187,3 +188,66 @@ def test_fp32_path_reaches_tolerance(opf):
     assert info.pres <= 1e-4 and info.dres <= 1e-4
     assert abs(info.objective - o["objective"]) <= 1e-4 * abs(o["objective"])
     p.close()
+
+
+@pytest.mark.parametrize("maker,rho", [(lambda: F.feeder_13(1), 100.0), (lambda: F.feeder_123(1), 10.0),
+                                       (lambda: F.feeder_123(2), 1000.0)])
+def test_persistent_engine_parity(opf, maker, rho):
+    """Persistent engine (neighbour-synchronized CTAs, halo global update in
+    shared memory, ping-pong buffers) against the oracle per iterate, with
+    odd and even chunk lengths (the final copy-home path)."""
+    f = maker()
+    p, out = run_pair(opf, f, rho, [1, 2, 5, 37, 300, 1001], engine=opf.ENGINE_PERSISTENT)
+    assert p.dims.n_blocks >= 1
+    for t, info, (xg, xl, lam), (ox, oz, ol), r in out:
+        assert rel(xg, ox) <= TOL, (t, rel(xg, ox))
+        assert rel(xl, oz) <= TOL, (t, rel(xl, oz))
+        assert rel(lam, ol) <= TOL, (t, rel(lam, ol))
+        assert abs(info.pres - r.pres) <= TOL * max(r.pres, 1e-6)
+        assert abs(info.dres - r.dres) <= TOL * max(r.dres, 1e-6)
+    p.close()
+
+
+def test_persistent_matches_graph_engine_8500(opf):
+    """Both engines on the 8500-class feeder (hundreds of CTAs): same
+    iterate to rounding after 500 iterations, same stopping decision."""
+    f = F.feeder_8500(1)
+    res = []
+    for engine in (opf.ENGINE_GRAPH, opf.ENGINE_PERSISTENT):
+        p = opf.Problem.from_feeder(f)
+        assert p.dims.n_blocks > 100
+        info = p.solve(opf.default_params(criterion=opf.CRIT_NEVER, max_iter=500, check_every=50, engine=engine))
+        res.append((p.state(), info))
+        p.close()
+    (a, ia), (b, ib) = res
+    for x, y in zip(a, b):
+        assert rel(x, y) <= 1e-12
+    assert ia.iters == ib.iters == 500
+    assert abs(ia.pres - ib.pres) <= 1e-10 * ia.pres and abs(ia.dres - ib.dres) <= 1e-10 * ia.dres
+    # converging solves stop at the same check
+    f = F.feeder_13(1)
+    its = []
+    for engine in (opf.ENGINE_GRAPH, opf.ENGINE_PERSISTENT):
+        p = opf.Problem.from_feeder(f)
+        its.append(p.solve(opf.default_params(check_every=10, engine=engine)).iters)
+        p.close()
+    assert its[0] == its[1]
+
+
+def test_persistent_wait_expires_cleanly(opf):
+    """Failure detection on the device without a fault: one CTA withholds its
+    iteration flag, its neighbours' bounded waits expire (50 ms), the solve
+    returns OPF_ERR_TIMEOUT, and the same context then solves normally."""
+    f = F.feeder_123(1)
+    p = opf.Problem.from_feeder(f)
+    assert p.dims.n_blocks >= 2
+    p.debug_config(wait_limit_ns=50_000_000, withhold_block=1)
+    with pytest.raises(opf.OpfError) as ei:
+        p.solve(opf.default_params(criterion=opf.CRIT_NEVER, max_iter=1000, check_every=50,
+                                   engine=opf.ENGINE_PERSISTENT))
+    assert ei.value.status == -6
+    p.debug_config(wait_limit_ns=2_000_000_000, withhold_block=-1)
+    p2, out = run_pair(opf, f, 100.0, [50], engine=opf.ENGINE_PERSISTENT)
+    t, info, (xg, xl, lam), (ox, oz, ol), r = out[0]
+    assert rel(xg, ox) <= TOL and rel(xl, oz) <= TOL
+    p.close(); p2.close()
