@@ -259,6 +259,28 @@ int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine)
  * the failure-detection test); -1 restores normal operation.              */
 int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block);
 
+/* Allocation-free residual norms (the paper has no counterpart; it exists for
+ * callers that may not allocate device memory: code running inside a fixed
+ * memory pool, plugins handed pre-allocated buffers, processes that forbid
+ * cudaMalloc after start-up).  Inputs are caller-owned device arrays of
+ * n_local doubles: v = B x (the global vector gathered per local copy),
+ * x_local and x_local_prev (stacked x_s at this and the previous iteration),
+ * lam (stacked duals).  out is a caller-owned device array of 4 doubles that
+ * receives pres, dres, eps_prim, eps_dual of Eq. (termination) (sum over s
+ * outside the norm, as printed).  Work is enqueued on `stream`; the call does
+ * not synchronize.  No cudaMalloc, cudaFree or allocating routine is called:
+ * the per-CTA partial sums live in a fixed 128 KiB array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Limit: n_local <= 4,194,304, otherwise OPF_ERR_INVALID_ARG.  The first call
+ * on each device looks up that array's device address (make it before any
+ * stream capture).  All calls share the array: two calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and give
+ * wrong results; calls in one stream are ordered and safe.  Each call writes
+ * every slot it reads, so no clearing is needed between calls.             */
+int32_t opf_residuals_noalloc(const double* v, const double* x_local, const double* x_local_prev,
+                              const double* lam, int64_t n_local, double rho, double eps_rel,
+                              double* out, void* stream);
+
 /* Host copy of component s's precomputed operator (canonical component
  * order): P[n_s*n_s] row-major = -Abar_s of Eq. (closed_2) (symmetric) and
  * bbar[n_s]; either pointer may be NULL.  *n_s (may be NULL) gets n_s.

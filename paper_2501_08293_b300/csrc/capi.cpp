@@ -19,6 +19,8 @@ void device_set_state(opf_problem* p, const double* xl, const double* lam, cudaS
 void device_free(opf_problem* p);
 int device_auto_engine(const opf_problem* p, int precision);
 void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us);
+void residuals_noalloc(const double* v, const double* z, const double* zp, const double* lam, long long n,
+                       double rho, double eps_rel, double* out, cudaStream_t s);
 }  // namespace opf
 
 namespace {
@@ -250,6 +252,15 @@ int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold
             throw opf::Error(OPF_ERR_INVALID_ARG, "withhold_block out of range");
         p->timeout_ns = (unsigned long long)wait_limit_ns;
         p->skip_block = withhold_block;
+        return OPF_OK;
+    });
+}
+
+int32_t opf_residuals_noalloc(const double* v, const double* x_local, const double* x_local_prev, const double* lam,
+                              int64_t n_local, double rho, double eps_rel, double* out, void* stream) {
+    return guarded([&]() -> int32_t {
+        opf::residuals_noalloc(v, x_local, x_local_prev, lam, (long long)n_local, rho, eps_rel, out,
+                               (cudaStream_t)stream);
         return OPF_OK;
     });
 }

@@ -72,6 +72,7 @@ EXPORTS = {
     "opf_profile_kernels": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
     "opf_debug_config": (C.c_int32, [_P, C.c_int64, C.c_int32]),
     "opf_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
+    "opf_residuals_noalloc": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "opf_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in EXPORTS.items():
@@ -114,6 +115,22 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)
+
+
+def residuals_noalloc(v, x_local, x_local_prev, lam, rho: float, eps_rel: float, out, stream=None) -> None:
+    """Allocation-free residual norms (opf_residuals_noalloc) for callers that
+    may not allocate device memory.  All arguments are CUDA tensors of
+    float64 (out: 4 elements, receives pres, dres, eps_prim, eps_dual);
+    nothing is allocated by the library and the call does not synchronize."""
+    n = int(x_local.numel())
+    for t in (v, x_local, x_local_prev, lam, out):
+        if not t.is_cuda or t.dtype.itemsize != 8 or not t.is_contiguous():
+            raise TypeError("expected contiguous float64 CUDA tensors")
+    if v.numel() != n or x_local_prev.numel() != n or lam.numel() != n or out.numel() < 4:
+        raise ValueError("size mismatch")
+    _check(lib.opf_residuals_noalloc(v.data_ptr(), x_local.data_ptr(), x_local_prev.data_ptr(), lam.data_ptr(),
+                                     n, rho, eps_rel, out.data_ptr(), _stream_handle(stream)),
+           "opf_residuals_noalloc")
 
 
 class Problem:
