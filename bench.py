@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent", "hostloop"])
     ap.add_argument("--rho", type=float, default=10.0)
     ap.add_argument("--check-every", type=int, default=50)
-    ap.add_argument("--max-iter", type=int, default=2_000_000)
+    ap.add_argument("--max-iter", type=int, default=4_000_000)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

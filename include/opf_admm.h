@@ -163,6 +163,10 @@ typedef struct opf_dims {
     int32_t n_blocks;        /* feeder chunks = CTAs of the local update        */
     int64_t sum_n2;          /* sum_s n_s^2 (dense operator entries)            */
     int64_t device_bytes;    /* bytes opf_problem_upload needs                  */
+    int32_t max_chunk_locals;    /* largest chunk: locals                       */
+    int32_t max_chunk_halo;      /* largest chunk: globals it copies            */
+    int32_t max_chunk_operator;  /* largest chunk: operator elements            */
+    int32_t max_chunk_copies;    /* largest chunk: halo copy-list entries       */
 } opf_dims;
 
 typedef struct opf_problem opf_problem;
@@ -187,6 +191,22 @@ int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus,
                            const opf_gen* gens, int32_t n_gen,
                            const opf_load* loads, int32_t n_load,
                            opf_problem** out);
+
+/* Layout options for opf_problem_create_ex.  chunks = number of feeder
+ * chunks (CTAs of the local update; 0 = automatic: about one per 4096 units
+ * of n_s^2 + 4 n_s + 16, at most 296).  Batches give each instance a share
+ * of the device so that all of them run co-resident.                      */
+typedef struct opf_create_options {
+    int32_t chunks;
+    int32_t _reserved[7];
+} opf_create_options;
+
+/* opf_problem_create with layout options (NULL = defaults).                */
+int32_t opf_problem_create_ex(const opf_bus* buses, int32_t n_bus,
+                              const opf_line* lines, int32_t n_line,
+                              const opf_gen* gens, int32_t n_gen,
+                              const opf_load* loads, int32_t n_load,
+                              const opf_create_options* options, opf_problem** out);
 
 int32_t opf_get_dims(const opf_problem* p, opf_dims* dims);
 
@@ -256,8 +276,12 @@ int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine)
  * that expires makes the solve return OPF_ERR_TIMEOUT with an undefined
  * iterate, and the device stays usable); withhold_block >= 0 makes that CTA
  * never publish its iteration flag, so its neighbours' waits expire (used by
- * the failure-detection test); -1 restores normal operation.              */
-int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block);
+ * the failure-detection test), -1 restores normal operation;
+ * persistent_variant selects the persistent kernel: 0 automatic (shared-
+ * memory iterate when it fits, else global-memory iterate), 1 global-memory
+ * iterate, 2 shared-memory iterate (OPF_ERR_INVALID_ARG at solve time if it
+ * does not fit co-resident).                                               */
+int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block, int32_t persistent_variant);
 
 /* Allocation-free residual norms (the paper has no counterpart; it exists for
  * callers that may not allocate device memory: code running inside a fixed

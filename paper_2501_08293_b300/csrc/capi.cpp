@@ -97,12 +97,14 @@ void opf_params_default(opf_params* p) {
     p->engine = OPF_ENGINE_AUTO;
 }
 
-int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
-                           const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
-                           opf_problem** out) {
+int32_t opf_problem_create_ex(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
+                              const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
+                              const opf_create_options* options, opf_problem** out) {
     return guarded([&]() -> int32_t {
         if (!out) throw opf::Error(OPF_ERR_INVALID_ARG, "out is NULL");
         *out = nullptr;
+        const int chunks = options ? options->chunks : 0;
+        if (chunks < 0 || chunks > 65536) throw opf::Error(OPF_ERR_INVALID_ARG, "chunks out of [0, 65536]");
         opf_problem* p = new opf_problem();
         try {
             p->model = opf::build_model(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load);
@@ -115,7 +117,7 @@ int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus, const opf_line* 
                 p->n_rows += c.m;
                 p->n_rows_reduced += p->ops.back().m_reduced;
             }
-            p->pk = opf::pack(p->model, p->ops);
+            p->pk = opf::pack(p->model, p->ops, chunks);
         } catch (...) {
             delete p;
             throw;
@@ -123,6 +125,12 @@ int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus, const opf_line* 
         *out = p;
         return OPF_OK;
     });
+}
+
+int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
+                           const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
+                           opf_problem** out) {
+    return opf_problem_create_ex(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load, nullptr, out);
 }
 
 int32_t opf_get_dims(const opf_problem* p, opf_dims* d) {
@@ -139,6 +147,10 @@ int32_t opf_get_dims(const opf_problem* p, opf_dims* d) {
         d->n_blocks = p->pk.nblocks;
         d->sum_n2 = p->pk.sum_n2;
         d->device_bytes = (int64_t)opf::device_bytes(p);
+        d->max_chunk_locals = p->pk.max_loc;
+        d->max_chunk_halo = p->pk.max_halo;
+        d->max_chunk_operator = p->pk.max_mat;
+        d->max_chunk_copies = p->pk.max_copies;
         return OPF_OK;
     });
 }
@@ -243,15 +255,17 @@ int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine)
     });
 }
 
-int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block) {
+int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block, int32_t persistent_variant) {
     return guarded([&]() -> int32_t {
         if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
         if (wait_limit_ns < 1000 || wait_limit_ns > 600000000000LL)
             throw opf::Error(OPF_ERR_INVALID_ARG, "wait limit out of [1 us, 600 s]");
         if (withhold_block < -1 || withhold_block >= p->pk.nblocks)
             throw opf::Error(OPF_ERR_INVALID_ARG, "withhold_block out of range");
+        if (persistent_variant < 0 || persistent_variant > 2) throw opf::Error(OPF_ERR_INVALID_ARG, "bad persistent variant");
         p->timeout_ns = (unsigned long long)wait_limit_ns;
         p->skip_block = withhold_block;
+        p->force_variant = persistent_variant;
         return OPF_OK;
     });
 }

@@ -70,6 +70,8 @@ struct BlockInfo {
     int32_t halo0, halo1;   // globals read by the chunk [halo0, halo1)
     int32_t nbr0, nbr1;     // neighbour CTAs (share a global) [nbr0, nbr1)
     int32_t loc0, loc1;     // locals [loc0, loc1)
+    int32_t mat0, mat1;     // operator elements [mat0, mat1) of the chunk's tiles
+    int32_t cp0, cp1;       // copy list entries of the chunk's halo [cp0, cp1)
 };
 
 // Device-ordered problem, ready to upload.
@@ -81,7 +83,9 @@ struct Packed {
     std::vector<int32_t> halo_gid;       // global id per halo entry
     std::vector<uint8_t> halo_own;       // 1 if this chunk writes x_i (first copy)
     std::vector<int32_t> nbrs;
-    std::vector<int32_t> meta;           // per local: hidx | n << 16 | base lane << 24
+    std::vector<int32_t> meta;           // per local: hidx | n << 16 | base lane << 24 | exported << 30
+    std::vector<int32_t> hcp;            // per halo entry (+1): start of its copy list in hci
+    std::vector<int32_t> hci;            // copy of a halo global: chunk-relative local (>= 0) or ~device local (< 0)
     std::vector<int32_t> dev_of_canon;   // local: canonical -> device
     std::vector<int32_t> canon_of_dev;   // local: device -> canonical
     std::vector<int32_t> gidx;           // device order
@@ -93,6 +97,10 @@ struct Packed {
     int64_t sum_n2 = 0;
     int max_n = 0;
     int max_halo = 0;                    // largest chunk halo (shared memory)
+    int max_loc = 0;                     // largest chunk local count
+    int max_mat = 0;                     // largest chunk operator span (elements)
+    int max_copies = 0;                  // largest chunk halo copy list
+    int max_big = 0;                     // largest component with n > 32 (0: none)
 };
 
 Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <string>
 
 #include "internal.hpp"
 
@@ -78,6 +79,61 @@ std::vector<int> locality_order(const Model& M) {
     return order;
 }
 
+// Every index the kernels dereference, checked once on the host: a layout
+// that fails here is an internal error, never a device fault.
+void validate(const Packed& K) {
+    auto fail = [](const char* what) { throw Error(OPF_ERR_INVALID_ARG, std::string("internal layout check: ") + what); };
+    std::vector<char> seen(K.nl, 0);
+    if ((int)K.blocks.size() != K.nblocks || K.hcp.size() != K.halo_gid.size() + 1) fail("sizes");
+    for (int b = 0; b < K.nblocks; ++b) {
+        const BlockInfo& bi = K.blocks[b];
+        if (bi.loc0 < 0 || bi.loc1 > K.nl || bi.loc0 > bi.loc1) fail("chunk locals");
+        if (bi.mat0 < 0 || bi.mat1 > K.mat_elems || bi.mat0 > bi.mat1 || (bi.mat0 & 3)) fail("chunk operators");
+        if (bi.tile0 < 0 || bi.tile1 > (int)K.tiles.size() || bi.tile0 > bi.tile1) fail("chunk tiles");
+        const int nh = bi.halo1 - bi.halo0;
+        if (nh < 0 || nh > K.max_halo || nh > 0x10000) fail("chunk halo");
+        if (bi.loc1 - bi.loc0 > K.max_loc || bi.mat1 - bi.mat0 > K.max_mat || bi.cp1 - bi.cp0 > K.max_copies) fail("maxima");
+        for (int q = bi.nbr0; q < bi.nbr1; ++q)
+            if (K.nbrs[q] < 0 || K.nbrs[q] >= K.nblocks || K.nbrs[q] == b) fail("neighbour");
+        for (int t = bi.tile0; t < bi.tile1; ++t) {
+            const Tile& tl = K.tiles[t];
+            const int lanes = tl.L;
+            const int64_t span = tl.big ? (int64_t)tl.L * tl.L : (int64_t)tl.nmax * tl.L;
+            if (tl.loc0 < bi.loc0 || tl.loc0 + lanes > bi.loc1) fail("tile locals");
+            if (tl.mat0 < bi.mat0 || tl.mat0 + span > bi.mat1 || (tl.mat0 & 3)) fail("tile operators");
+            if (!tl.big && (lanes < 1 || lanes > 32 || tl.nmax < 1 || tl.nmax > 32)) fail("small tile shape");
+            if (tl.big && (tl.nmax != tl.L || tl.L <= 32 || tl.L > 255)) fail("big tile shape");
+            for (int r = 0; r < lanes; ++r) {
+                const int j = tl.loc0 + r;
+                if (seen[j]) fail("local placed twice");
+                seen[j] = 1;
+                const int m = K.meta[j], n = (m >> 16) & 0xFF, base = (m >> 24) & 0x1F;
+                if ((m & 0xFFFF) >= nh) fail("halo index");
+                if (!tl.big && (n < 1 || n > tl.nmax || base + n > lanes || r < base || r >= base + n)) fail("lane meta");
+                if (K.halo_gid[bi.halo0 + (m & 0xFFFF)] != K.gidx[j]) fail("halo entry of a local");
+            }
+        }
+        if (bi.cp0 != K.hcp[bi.halo0] || bi.cp1 != K.hcp[bi.halo1]) fail("copy list range");
+        for (int h = bi.halo0; h < bi.halo1; ++h) {
+            const int g = K.halo_gid[h];
+            if (g < 0 || g >= K.ng) fail("halo global");
+            if (K.hcp[h + 1] - K.hcp[h] != K.gptr[g + 1] - K.gptr[g]) fail("copy count");
+            for (int q = K.hcp[h]; q < K.hcp[h + 1]; ++q) {
+                const int c = K.hci[q];
+                if (c >= 0) {
+                    if (c >= bi.loc1 - bi.loc0 || K.gidx[bi.loc0 + c] != g) fail("internal copy");
+                } else {
+                    const int l = ~c;
+                    if (l < 0 || l >= K.nl || (l >= bi.loc0 && l < bi.loc1) || K.gidx[l] != g) fail("external copy");
+                    if (!(K.meta[l] & (1 << 30))) fail("external copy not exported");
+                }
+            }
+        }
+    }
+    for (int j = 0; j < K.nl; ++j)
+        if (!seen[j]) fail("local not placed");
+}
+
 }  // namespace
 
 Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) {
@@ -99,7 +155,7 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
 
     // ---- chunks
     int nblk = nblocks_hint;
-    if (nblk <= 0) nblk = (int)std::min<int64_t>(592, std::max<int64_t>(1, work_total / 4096));
+    if (nblk <= 0) nblk = (int)std::min<int64_t>(296, std::max<int64_t>(1, work_total / 4096));
     nblk = std::max(1, std::min(nblk, std::max(1, K.ncomp)));
     const std::vector<int> order = locality_order(M);
     std::vector<int> chunk_start;   // index into order
@@ -129,6 +185,8 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         BlockInfo bi;
         bi.tile0 = (int)K.tiles.size();
         bi.loc0 = loc;
+        mat = (mat + 3) & ~int64_t(3);
+        bi.mat0 = (int32_t)mat;
         std::vector<int> comps(order.begin() + chunk_start[b], order.begin() + chunk_start[b + 1]);
         std::stable_sort(comps.begin(), comps.end(),
                          [&](int a, int c) { return M.comps[a].n() > M.comps[c].n(); });
@@ -140,6 +198,7 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
             const int n = M.comps[s].n();
             if (n == 0) continue;
             if (n > 32) {
+                K.max_big = std::max(K.max_big, n);
                 warps.push_back({s});
                 lanes.push_back(-1);
                 continue;
@@ -202,6 +261,9 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         }
         bi.tile1 = (int)K.tiles.size();
         bi.loc1 = loc;
+        bi.mat1 = (int32_t)mat;
+        K.max_loc = std::max(K.max_loc, bi.loc1 - bi.loc0);
+        K.max_mat = std::max(K.max_mat, bi.mat1 - bi.mat0);
         K.blocks.push_back(bi);
     }
     if (loc != K.nl) throw Error(OPF_ERR_INVALID_ARG, "internal: locals not all placed");
@@ -270,6 +332,23 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         }
         bi.halo1 = (int)K.halo_gid.size();
         K.max_halo = std::max(K.max_halo, bi.halo1 - bi.halo0);
+        // copy lists of the halo globals, canonical copy order; a copy held by
+        // this chunk is referenced by its chunk-relative local index
+        bi.cp0 = (int)K.hci.size();
+        for (int h = bi.halo0; h < bi.halo1; ++h) {
+            K.hcp.push_back((int)K.hci.size());
+            const int g = K.halo_gid[h];
+            for (int q = K.gptr[g]; q < K.gptr[g + 1]; ++q) {
+                const int l = K.gcol[q];
+                if (l >= bi.loc0 && l < bi.loc1) K.hci.push_back(l - bi.loc0);
+                else {
+                    K.hci.push_back(~l);
+                    K.meta[l] |= (1 << 30);        // read by another chunk: exported
+                }
+            }
+        }
+        bi.cp1 = (int)K.hci.size();
+        K.max_copies = std::max(K.max_copies, bi.cp1 - bi.cp0);
         bi.nbr0 = (int)K.nbrs.size();
         for (int h = bi.halo0; h < bi.halo1; ++h) {
             const int g = K.halo_gid[h];
@@ -284,6 +363,8 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         std::sort(K.nbrs.begin() + bi.nbr0, K.nbrs.end());
         bi.nbr1 = (int)K.nbrs.size();
     }
+    K.hcp.push_back((int)K.hci.size());
+    validate(K);
     return K;
 }
 

@@ -55,6 +55,8 @@ struct View {
     const int32_t* halo_gid;
     const uint8_t* halo_own;
     const int32_t* nbrs;
+    const int32_t* hcp;
+    const int32_t* hci;
     int32_t* flags;
     const T* P;
     const double* cost;
@@ -100,6 +102,8 @@ struct opf_problem {
     int32_t* halo_gid = nullptr;
     uint8_t* halo_own = nullptr;
     int32_t* nbrs = nullptr;
+    int32_t* hcp = nullptr;
+    int32_t* hci = nullptr;
     int32_t* flags = nullptr;
     double* cost = nullptr;
     double* partials = nullptr;
@@ -109,5 +113,6 @@ struct opf_problem {
     bool cold = true;                   // state is at the initial point
     unsigned long long timeout_ns = 2000000000ull;   // bounded waits (persistent engine)
     int skip_block = -1;                              // test hook
+    int force_variant = 0;                            // persistent kernel: 0 auto, 1 global, 2 shared
     std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision, K)
 };

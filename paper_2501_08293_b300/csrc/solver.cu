@@ -102,7 +102,7 @@ __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int
         if (act) {
             const int m = v.meta[j];
             n = (m >> 16) & 0xFF;
-            base = (m >> 24) & 0xFF;
+            base = (m >> 24) & 0x1F;
             vv = getv(j, m);
             lo = ldcg(lr + j);
             xo = ldcg(xr + j);
@@ -184,6 +184,27 @@ __device__ __forceinline__ void sum_partials(const double* partials, int nparts,
     }
     if (threadIdx.x == 0)
         for (int k = 0; k < 5; ++k) tot[k] = sh[k][0];
+}
+
+// Fixed-order sum of nparts partial records by one CTA using only the
+// per-warp scratch red[][5]: thread-strided sums, a fixed shuffle tree per
+// warp, then warps in order.  Thread 0 gets the five sums in tot.
+__device__ __forceinline__ void sum_partials_small(const double* partials, int nparts, double (*red)[5], double* tot) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+        for (int k = 0; k < 5; ++k) s[k] += __ldcg(partials + (size_t)b * 8 + k);
+    for (int k = 0; k < 5; ++k) s[k] = warp_sum(s[k]);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < 5; ++k) red[warp][k] = s[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) {
+            double a = 0;
+            for (int w = 0; w < kXWarps; ++w) a += red[w][k];
+            tot[k] = a;
+        }
 }
 
 // Eq. (termination) from the five sums after `it` iterations; returns stop.
@@ -268,14 +289,15 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(View<T> v, cudaGr
 }
 
 // ------------------------------------------------------------- persistent
-// Bounded wait until every neighbour CTA has completed `t` iterations.
+// Bounded wait until every neighbour CTA has completed `t` iterations: each
+// thread polls one neighbour's flag (acquire), the CTA combines the results.
 // Returns false when the deadline passed or another CTA aborted.
 template <typename T>
-__device__ bool wait_neighbours(const View<T>& v, const BlockInfo& bi, int t, unsigned long long tmo, int* s_ok) {
-    if (threadIdx.x == 0) {
-        int ok = 1;
+__device__ bool wait_neighbours(const View<T>& v, const BlockInfo& bi, int t, unsigned long long tmo, int*) {
+    int ok = 1;
+    if (bi.nbr1 > bi.nbr0) {
         const unsigned long long deadline = now_ns() + tmo;
-        for (int q = bi.nbr0; q < bi.nbr1 && ok; ++q) {
+        for (int q = bi.nbr0 + threadIdx.x; q < bi.nbr1 && ok; q += blockDim.x) {
             const int32_t* f = v.flags + v.nbrs[q];
             while (ld_acquire(f) < t) {
                 if (ld_acquire(&v.ctl->abort)) { ok = 0; break; }
@@ -284,15 +306,11 @@ __device__ bool wait_neighbours(const View<T>& v, const BlockInfo& bi, int t, un
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(20);
             }
         }
-        *s_ok = ok;
     }
-    __syncthreads();
-    const bool r = *s_ok != 0;
-    __syncthreads();
-    return r;
+    return __syncthreads_and(ok) != 0;
 }
 
 template <typename T>
@@ -391,6 +409,266 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
     }
 }
 
+// ----------------------------------------------- persistent, shared-memory
+// Per-launch shared-memory plan (byte offsets; every region 16-byte aligned).
+struct SmemPlan {
+    int P, xs, ls, bb, mt, zs, hlo, hhi, hik, hck, hp, hc, us, big, total;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Same iteration as persistent_kernel, but the chunk's operators (staged once
+// by TMA bulk copies), its local iterate, duals, bbar, meta and the halo's
+// bounds, scalings and copy lists stay in shared memory for the whole solve.
+// Only copies read by another chunk (the "exported" locals) are written to
+// the global ping-pong buffers each iteration; only copies held by another
+// chunk are read from them.
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32) persistent_smem_kernel(View<T> v, SmemPlan sp) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    T* sP = reinterpret_cast<T*>(sm + sp.P);
+    T* xs = reinterpret_cast<T*>(sm + sp.xs);
+    T* ls = reinterpret_cast<T*>(sm + sp.ls);
+    T* bb = reinterpret_cast<T*>(sm + sp.bb);
+    int* mt = reinterpret_cast<int*>(sm + sp.mt);
+    T* zs = reinterpret_cast<T*>(sm + sp.zs);
+    T* hlo = reinterpret_cast<T*>(sm + sp.hlo);
+    T* hhi = reinterpret_cast<T*>(sm + sp.hhi);
+    T* hik = reinterpret_cast<T*>(sm + sp.hik);
+    T* hck = reinterpret_cast<T*>(sm + sp.hck);
+    int* hp = reinterpret_cast<int*>(sm + sp.hp);
+    int* hc = reinterpret_cast<int*>(sm + sp.hc);
+    T* usw = reinterpret_cast<T*>(sm + sp.us);          // big-tile staging, sp.big per warp
+    __shared__ double red[kXWarps][5];
+    __shared__ double tot[5];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_last, s_stop, s_ok;
+    Ctl* ctl = v.ctl;
+    const int b = blockIdx.x;
+    const BlockInfo bi = v.blocks[b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it0 = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
+    const T rho = (T)ctl->rho, inv_rho = (T)ctl->inv_rho;
+    const unsigned long long tmo = ctl->timeout_ns;
+    const bool withhold = (ctl->skip_block == b);
+    const int nloc = bi.loc1 - bi.loc0, nh = bi.halo1 - bi.halo0, ncp = bi.cp1 - bi.cp0;
+
+    // ---- prologue: operators by TMA bulk copies, the rest by plain loads
+    const unsigned pbytes = (unsigned)(((size_t)(bi.mat1 - bi.mat0) * sizeof(T) + 15) & ~size_t(15));
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && pbytes) {
+        mbar_expect_tx(&mbar, pbytes);
+        const char* src = reinterpret_cast<const char*>(v.P + bi.mat0);
+        for (unsigned off = 0; off < pbytes; off += 32768u) {
+            const unsigned len = min(32768u, pbytes - off);
+            bulk_g2s(reinterpret_cast<char*>(sP) + off, src + off, len, &mbar);
+        }
+    }
+    for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
+        xs[j] = v.xl[bi.loc0 + j];
+        ls[j] = v.lam[bi.loc0 + j];
+        bb[j] = v.bbar[bi.loc0 + j];
+        mt[j] = v.meta[bi.loc0 + j];
+    }
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        const int g = v.halo_gid[bi.halo0 + h];
+        hlo[h] = v.lo[g]; hhi[h] = v.hi[g]; hik[h] = v.invk[g]; hck[h] = v.cik[g];
+        hp[h] = v.hcp[bi.halo0 + h] - bi.cp0;
+    }
+    if (threadIdx.x == 0) hp[nh] = ncp;
+    for (int q = threadIdx.x; q < ncp; q += blockDim.x) hc[q] = v.hci[bi.cp0 + q];
+    int ok = 1;
+    if (pbytes) {
+        const unsigned long long deadline = now_ns() + tmo;
+        while (!mbar_try_wait(&mbar, 0)) {
+            if (now_ns() > deadline) {
+                if (atomicCAS(&ctl->abort, 0, 1) == 0) { ctl->status = CTL_TIMEOUT; ctl->timeout_where = 4; }
+                ok = 0;
+                break;
+            }
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        // give the copy in flight a second bounded chance to land before leaving
+        const unsigned long long deadline = now_ns() + tmo;
+        while (!mbar_try_wait(&mbar, 0) && now_ns() < deadline) {
+        }
+        return;
+    }
+
+    int t = 0, checkno = 0;
+    bool done = it0 >= maxit;
+    while (!done) {
+        if (t > 0 && !wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+        const T* xr = (t & 1) ? v.xl2 : v.xl;
+        const T* lr = (t & 1) ? v.lam2 : v.lam;
+        T* xw = (t & 1) ? v.xl : v.xl2;
+        T* lw = (t & 1) ? v.lam : v.lam2;
+        // global update of the halo, Eq. (global_sparse), copies in CSR order
+        for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+            T sum = 0;
+            for (int q = hp[h]; q < hp[h + 1]; ++q) {
+                const int c = hc[q];
+                if (c >= 0) sum += xs[c] - ls[c] * inv_rho;
+                else sum += __ldcg(xr + ~c) - __ldcg(lr + ~c) * inv_rho;
+            }
+            const T xh = sum * hik[h] - hck[h] * inv_rho;
+            zs[h] = fmin(fmax(xh, hlo[h]), hhi[h]);
+        }
+        __syncthreads();
+        const int nrem = maxit - (it0 + t);
+        const bool check = ((t + 1) % K == 0) || nrem == 1;
+        double acc[5] = {0, 0, 0, 0, 0};
+        // local + dual updates, Eq. (closed_2) and Eq. (ADMM-3)
+        for (int q = bi.tile0 + warp; q < bi.tile1; q += kXWarps) {
+            const Tile tl = v.tiles[q];
+            const int jl0 = tl.loc0 - bi.loc0;
+            const T* Pt = sP + (tl.mat0 - bi.mat0);
+            if (!tl.big) {
+                const int L = tl.L, nmax = tl.nmax;
+                const bool act = lane < L;
+                const int jl = jl0 + lane;
+                int n = 0, base = 0, m = 0;
+                T vv = 0, lo = 0, xo = 0, u = 0;
+                if (act) {
+                    m = mt[jl];
+                    n = (m >> 16) & 0xFF;
+                    base = (m >> 24) & 0x1F;
+                    vv = zs[m & 0xFFFF];
+                    lo = ls[jl];
+                    xo = xs[jl];
+                    u = vv + lo * inv_rho;
+                }
+                T y = 0;
+#pragma unroll 4
+                for (int c = 0; c < nmax; ++c) {
+                    const T uc = __shfl_sync(0xffffffffu, u, (base + c) & 31);
+                    if (act && c < n) y = fma(Pt[c * L + lane], uc, y);
+                }
+                if (act) {
+                    const T xn = y + bb[jl];
+                    const T ln = lo + rho * (vv - xn);
+                    xs[jl] = xn;
+                    ls[jl] = ln;
+                    if (m & (1 << 30)) {
+                        xw[bi.loc0 + jl] = xn;
+                        lw[bi.loc0 + jl] = ln;
+                    }
+                    if (check) {
+                        const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
+                        acc[0] += pr * pr; acc[1] += dz * dz;
+                        acc[2] += (double)vv * (double)vv; acc[3] += (double)xn * (double)xn;
+                        acc[4] += (double)ln * (double)ln;
+                    }
+                }
+            } else {
+                const int n = tl.nmax;
+                T* us = usw + warp * sp.big;
+                for (int r = lane; r < n; r += 32) us[r] = zs[mt[jl0 + r] & 0xFFFF] + ls[jl0 + r] * inv_rho;
+                __syncwarp();
+                for (int r = lane; r < n; r += 32) {
+                    T y = 0;
+                    for (int c = 0; c < n; ++c) y = fma(Pt[c * n + r], us[c], y);
+                    const int jl = jl0 + r;
+                    const int m = mt[jl];
+                    const T vv = zs[m & 0xFFFF];
+                    const T lo = ls[jl], xo = xs[jl];
+                    const T xn = y + bb[jl];
+                    const T ln = lo + rho * (vv - xn);
+                    xs[jl] = xn;
+                    ls[jl] = ln;
+                    if (m & (1 << 30)) {
+                        xw[bi.loc0 + jl] = xn;
+                        lw[bi.loc0 + jl] = ln;
+                    }
+                    if (check) {
+                        const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
+                        acc[0] += pr * pr; acc[1] += dz * dz;
+                        acc[2] += (double)vv * (double)vv; acc[3] += (double)xn * (double)xn;
+                        acc[4] += (double)ln * (double)ln;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        ++t;
+        if (threadIdx.x == 0 && !withhold) {
+            __threadfence();
+            st_release(v.flags + b, t);
+        }
+        if (check) {
+            cta_partials(acc, red, v.partials + (size_t)b * 8);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const unsigned long long ticket = atomicAdd(&ctl->arrive, 1ull);
+                s_last = ticket == (unsigned long long)v.nblocks * (checkno + 1) - 1;
+            }
+            __syncthreads();
+            if (s_last) {
+                sum_partials_small(v.partials, v.nblocks, red, tot);
+                if (threadIdx.x == 0) {
+                    ctl->iter = it0 + t;
+                    ctl->stop = decide(ctl, tot, it0 + t);
+                    __threadfence();
+                    st_release(&ctl->decided, checkno + 1);
+                }
+            }
+            if (threadIdx.x == 0) {
+                int okw = 1;
+                const unsigned long long deadline = now_ns() + tmo;
+                while (ld_acquire(&ctl->decided) < checkno + 1) {
+                    if (ld_acquire(&ctl->abort)) { okw = 0; break; }
+                    if (now_ns() > deadline) {
+                        if (atomicCAS(&ctl->abort, 0, 1) == 0) { ctl->status = CTL_TIMEOUT; ctl->timeout_where = 2; }
+                        okw = 0;
+                        break;
+                    }
+                    __nanosleep(20);
+                }
+                s_ok = okw;
+                s_stop = okw ? ld_acquire(&ctl->stop) : 1;
+            }
+            __syncthreads();
+            ++checkno;
+            if (!s_ok) return;
+            if (s_stop) done = true;
+        }
+        if (it0 + t >= maxit) done = true;
+    }
+    // epilogue: owners publish the last global update; once every neighbour
+    // has finished, the chunk's iterate goes back to the primary buffers
+    for (int h = threadIdx.x; h < nh; h += blockDim.x)
+        if (v.halo_own[bi.halo0 + h]) v.zg[v.halo_gid[bi.halo0 + h]] = zs[h];
+    if (!wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+    for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
+        v.xl[bi.loc0 + j] = xs[j];
+        v.lam[bi.loc0 + j] = ls[j];
+    }
+}
+
 // ------------------------------------------------------------ misc kernels
 template <typename T>
 __global__ void init_kernel(View<T> v) {
@@ -444,7 +722,7 @@ struct Arena {
 
 struct Layout {
     size_t lo, hi, invk, cik, zg, lo32, hi32, invk32, cik32, zg32;
-    size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, flags, cost, partials, ctl;
+    size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, ctl;
     size_t xl, lam, xl2, lam2, bbar, xl0, xl32, lam32, xl2_32, lam2_32, bbar32, xl0_32, P64, P32;
     size_t total;
 };
@@ -461,14 +739,17 @@ Layout layout_of(const opf_problem* p) {
     L.meta = a.take<int32_t>(k.nl);
     L.tiles = a.take<Tile>(k.tiles.size()); L.blocks = a.take<BlockInfo>(k.blocks.size());
     L.halo_gid = a.take<int32_t>(k.halo_gid.size()); L.halo_own = a.take<uint8_t>(k.halo_own.size());
-    L.nbrs = a.take<int32_t>(k.nbrs.size() + 1); L.flags = a.take<int32_t>(k.nblocks);
+    L.nbrs = a.take<int32_t>(k.nbrs.size() + 1);
+    L.hcp = a.take<int32_t>(k.hcp.size()); L.hci = a.take<int32_t>(k.hci.size() + 1);
+    L.flags = a.take<int32_t>(k.nblocks);
     L.cost = a.take<double>(k.ng);
     L.partials = a.take<double>((size_t)k.nblocks * 8); L.ctl = a.take<Ctl>(1);
     L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.xl2 = a.take<double>(k.nl); L.lam2 = a.take<double>(k.nl);
     L.bbar = a.take<double>(k.nl); L.xl0 = a.take<double>(k.nl);
     L.xl32 = a.take<float>(k.nl); L.lam32 = a.take<float>(k.nl); L.xl2_32 = a.take<float>(k.nl); L.lam2_32 = a.take<float>(k.nl);
     L.bbar32 = a.take<float>(k.nl); L.xl0_32 = a.take<float>(k.nl);
-    L.P64 = a.take<double>(k.mat_elems); L.P32 = a.take<float>(k.mat_elems);
+    // operators, padded so a chunk's 16-byte-rounded bulk copy stays inside
+    L.P64 = a.take<double>(k.mat_elems + 8); L.P32 = a.take<float>(k.mat_elems + 8);
     L.total = (a.off + 255) & ~size_t(255);
     return L;
 }
@@ -481,7 +762,7 @@ View<T> view_of(const opf_problem* p, const DevPrec& d) {
     v.xl = (T*)d.xl; v.lam = (T*)d.lam; v.xl2 = (T*)d.xl2; v.lam2 = (T*)d.lam2;
     v.bbar = (const T*)d.bbar; v.xl0 = (const T*)d.xl0; v.gidx = p->gidx; v.meta = p->meta;
     v.tiles = p->tiles; v.blocks = p->blocks; v.halo_gid = p->halo_gid; v.halo_own = p->halo_own;
-    v.nbrs = p->nbrs; v.flags = p->flags;
+    v.nbrs = p->nbrs; v.hcp = p->hcp; v.hci = p->hci; v.flags = p->flags;
     v.P = (const T*)d.P; v.cost = p->cost; v.partials = p->partials; v.ctl = p->ctl;
     v.ng = p->pk.ng; v.nl = p->pk.nl; v.nblocks = p->pk.nblocks;
     return v;
@@ -561,30 +842,78 @@ template <typename T>
 size_t persistent_smem(const opf_problem* p) { return (size_t)std::max(1, p->pk.max_halo) * sizeof(T); }
 
 template <typename T>
-bool persistent_fits(const opf_problem* p) {
-    const size_t smem = persistent_smem<T>(p);
-    if (smem > 160 * 1024) return false;
-    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+SmemPlan smem_plan(const opf_problem* p) {
+    const Packed& k = p->pk;
+    SmemPlan sp;
+    int off = 0;
+    auto take = [&](size_t bytes) {
+        const int o = off;
+        off += (int)((bytes + 15) & ~size_t(15));
+        return o;
+    };
+    const size_t w = sizeof(T);
+    sp.P = take((size_t)k.max_mat * w + 16);
+    sp.xs = take((size_t)k.max_loc * w); sp.ls = take((size_t)k.max_loc * w);
+    sp.bb = take((size_t)k.max_loc * w); sp.mt = take((size_t)k.max_loc * 4);
+    sp.zs = take((size_t)k.max_halo * w); sp.hlo = take((size_t)k.max_halo * w); sp.hhi = take((size_t)k.max_halo * w);
+    sp.hik = take((size_t)k.max_halo * w); sp.hck = take((size_t)k.max_halo * w);
+    sp.hp = take((size_t)(k.max_halo + 1) * 4); sp.hc = take((size_t)std::max(1, k.max_copies) * 4);
+    sp.big = k.max_big;
+    sp.us = take((size_t)kXWarps * k.max_big * w);
+    sp.total = off;
+    return sp;
+}
+
+// Can every chunk's CTA be co-resident with `smem` dynamic bytes?
+template <typename KernelT>
+bool coop_fits(KernelT kernel, size_t smem, int nblocks) {
+    int dev = 0, coop = 0, sms = 0, per_sm = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!coop) return false;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(persistent_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop || smem > (size_t)optin) return false;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
         return false;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<T>, kXWarps * 32, smem) != cudaSuccess)
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kXWarps * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
         return false;
-    return (long long)per_sm * sms >= p->pk.nblocks;
+    }
+    return (long long)per_sm * sms >= nblocks;
 }
+
+// 0: none, 1: persistent (global-memory iterate), 2: persistent (shared-memory iterate)
+template <typename T>
+int persistent_variant(const opf_problem* p) {
+    const bool smem_ok = coop_fits(persistent_smem_kernel<T>, (size_t)smem_plan<T>(p).total, p->pk.nblocks);
+    if (p->force_variant == 2) return smem_ok ? 2 : 0;
+    if (p->force_variant != 1 && smem_ok) return 2;
+    if (coop_fits(persistent_kernel<T>, persistent_smem<T>(p), p->pk.nblocks)) return 1;
+    return 0;
+}
+
+template <typename T>
+bool persistent_fits(const opf_problem* p) { return persistent_variant<T>(p) != 0; }
 
 template <typename T>
 void launch_persistent(opf_problem* p, cudaStream_t s) {
     View<T> v = view_of<T>(p, prec_of<T>(p));
-    const size_t smem = persistent_smem<T>(p);
-    void* args[] = {&v};
     OPF_CUDA(cudaMemsetAsync(p->flags, 0, sizeof(int32_t) * p->pk.nblocks, s));
-    OPF_CUDA(cudaLaunchCooperativeKernel((const void*)persistent_kernel<T>, dim3(p->pk.nblocks),
-                                         dim3(kXWarps * 32), args, smem, s));
+    const int variant = persistent_variant<T>(p);
+    if (variant == 2) {
+        SmemPlan sp = smem_plan<T>(p);
+        void* args[] = {&v, &sp};
+        OPF_CUDA(cudaLaunchCooperativeKernel((const void*)persistent_smem_kernel<T>, dim3(p->pk.nblocks),
+                                             dim3(kXWarps * 32), args, (size_t)sp.total, s));
+    } else if (variant == 1) {
+        void* args[] = {&v};
+        OPF_CUDA(cudaLaunchCooperativeKernel((const void*)persistent_kernel<T>, dim3(p->pk.nblocks),
+                                             dim3(kXWarps * 32), args, persistent_smem<T>(p), s));
+    } else {
+        throw Error(OPF_ERR_INVALID_ARG, "persistent engine: the chunks do not fit co-resident on this device");
+    }
 }
 
 template <typename T>
@@ -711,6 +1040,7 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     p->meta = (int32_t*)(a + L.meta); p->tiles = (Tile*)(a + L.tiles); p->blocks = (BlockInfo*)(a + L.blocks);
     p->halo_gid = (int32_t*)(a + L.halo_gid); p->halo_own = (uint8_t*)(a + L.halo_own);
     p->nbrs = (int32_t*)(a + L.nbrs); p->flags = (int32_t*)(a + L.flags);
+    p->hcp = (int32_t*)(a + L.hcp); p->hci = (int32_t*)(a + L.hci);
     p->cost = (double*)(a + L.cost); p->partials = (double*)(a + L.partials);
     p->ctl = (Ctl*)(a + L.ctl);
     if (!p->ctl_host) OPF_CUDA(cudaMallocHost((void**)&p->ctl_host, sizeof(Ctl)));
@@ -736,9 +1066,13 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     h2d(p->halo_gid, k.halo_gid.data(), k.halo_gid.size() * 4);
     h2d(p->halo_own, k.halo_own.data(), k.halo_own.size());
     h2d(p->nbrs, k.nbrs.data(), k.nbrs.size() * 4);
+    h2d(p->hcp, k.hcp.data(), k.hcp.size() * 4);
+    h2d(p->hci, k.hci.data(), k.hci.size() * 4);
     h2d(p->cost, M.c.data(), k.ng * 8);
     h2d(p->d64.bbar, k.bbar.data(), k.nl * 8); h2d(p->d64.xl0, k.xl0.data(), k.nl * 8);
     h2d32(p->d32.bbar, k.bbar); h2d32(p->d32.xl0, k.xl0);
+    OPF_CUDA(cudaMemsetAsync(a + L.P64, 0, (k.mat_elems + 8) * 8, s));
+    OPF_CUDA(cudaMemsetAsync(a + L.P32, 0, (k.mat_elems + 8) * 4, s));
     h2d(p->d64.P, k.P.data(), k.mat_elems * 8);
     h2d32(p->d32.P, k.P);
     OPF_CUDA(cudaMemsetAsync(p->partials, 0, (size_t)k.nblocks * 8 * sizeof(double), s));

@@ -33,6 +33,10 @@ class Params(C.Structure):
                 ("warm_start", C.c_int32), ("engine", C.c_int32), ("_reserved", C.c_int32)]
 
 
+class CreateOptions(C.Structure):
+    _fields_ = [("chunks", C.c_int32), ("_reserved", C.c_int32 * 7)]
+
+
 class Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("first_rel_iter", C.c_int32),
                 ("_pad", C.c_int32), ("pres", C.c_double), ("dres", C.c_double),
@@ -47,7 +51,9 @@ class Dims(C.Structure):
     _fields_ = [("n_global", C.c_int32), ("n_local", C.c_int32), ("n_comp", C.c_int32),
                 ("n_rows", C.c_int32), ("n_rows_reduced", C.c_int32), ("max_n", C.c_int32),
                 ("n_tiles", C.c_int32), ("n_blocks", C.c_int32), ("sum_n2", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("max_chunk_locals", C.c_int32),
+                ("max_chunk_halo", C.c_int32), ("max_chunk_operator", C.c_int32),
+                ("max_chunk_copies", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -61,6 +67,8 @@ EXPORTS = {
     "opf_params_default": (None, [C.POINTER(Params)]),
     "opf_problem_create": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32,
                                        C.POINTER(C.c_void_p)]),
+    "opf_problem_create_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32,
+                                          C.POINTER(CreateOptions), C.POINTER(C.c_void_p)]),
     "opf_get_dims": (C.c_int32, [_P, C.POINTER(Dims)]),
     "opf_problem_upload": (C.c_int32, [_P, _P, C.c_size_t, _P]),
     "opf_admm_solve": (C.c_int32, [_P, C.POINTER(Params), _P, C.POINTER(Info)]),
@@ -70,7 +78,7 @@ EXPORTS = {
     "opf_get_solution": (C.c_int32, [_P] + [_D] * 11 + [_P]),
     "opf_get_operator": (C.c_int32, [_P, C.c_int32, _D, _D, _I]),
     "opf_profile_kernels": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
-    "opf_debug_config": (C.c_int32, [_P, C.c_int64, C.c_int32]),
+    "opf_debug_config": (C.c_int32, [_P, C.c_int64, C.c_int32, C.c_int32]),
     "opf_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
     "opf_residuals_noalloc": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "opf_destroy": (None, [_P]),
@@ -136,15 +144,18 @@ def residuals_noalloc(v, x_local, x_local_prev, lam, rho: float, eps_rel: float,
 class Problem:
     """One feeder: host precompute at construction, device arena from torch."""
 
-    def __init__(self, buses, lines, gens, loads, *, device=None, stream=None, upload=True):
+    def __init__(self, buses, lines, gens, loads, *, device=None, stream=None, upload=True, chunks: int = 0):
         self._h = C.c_void_p()
         self._arrays = [np.ascontiguousarray(a) for a in (buses, lines, gens, loads)]
         for a, dt in zip(self._arrays, (_F.BUS_DTYPE, _F.LINE_DTYPE, _F.GEN_DTYPE, _F.LOAD_DTYPE)):
             if a.dtype != dt:
                 raise TypeError(f"record array has dtype {a.dtype}, expected {dt}")
         b, l, g, d = self._arrays
-        _check(lib.opf_problem_create(b.ctypes.data, len(b), l.ctypes.data, len(l), g.ctypes.data, len(g),
-                                      d.ctypes.data, len(d), C.byref(self._h)), "opf_problem_create")
+        opts = CreateOptions()
+        opts.chunks = int(chunks)
+        _check(lib.opf_problem_create_ex(b.ctypes.data, len(b), l.ctypes.data, len(l), g.ctypes.data, len(g),
+                                         d.ctypes.data, len(d), C.byref(opts), C.byref(self._h)),
+               "opf_problem_create_ex")
         self.dims = Dims()
         _check(lib.opf_get_dims(self._h, C.byref(self.dims)), "opf_get_dims")
         self.n_bus, self.n_line, self.n_gen, self.n_load = len(b), len(l), len(g), len(d)
@@ -190,8 +201,9 @@ class Problem:
         _check(lib.opf_engine_for(self._h, params.precision, C.byref(e)), "opf_engine_for")
         return e.value == ENGINE_PERSISTENT
 
-    def debug_config(self, wait_limit_ns: int = 2_000_000_000, withhold_block: int = -1):
-        _check(lib.opf_debug_config(self._h, int(wait_limit_ns), int(withhold_block)), "opf_debug_config")
+    def debug_config(self, wait_limit_ns: int = 2_000_000_000, withhold_block: int = -1, variant: int = 0):
+        _check(lib.opf_debug_config(self._h, int(wait_limit_ns), int(withhold_block), int(variant)),
+               "opf_debug_config")
 
     def state(self, stream=None):
         xg = np.empty(self.dims.n_global)
