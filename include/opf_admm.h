@@ -313,6 +313,25 @@ int32_t opf_get_operator(const opf_problem* p, int32_t s, double* P, double* bba
 
 void opf_destroy(opf_problem* p);
 
+/* ------------------------------------------------------------------ batch
+ * Many feeders solved together in one cooperative launch (the batch
+ * dimension of the sweep).  Each instance keeps its own chunks, parameters,
+ * iteration counter, residual checks and stopping decision: its iterates do
+ * not depend on the other instances in the batch.  All problems must be
+ * uploaded on the current device, and the sum of their chunks must fit
+ * co-resident (create them with opf_problem_create_ex and a chunk count
+ * sized to the batch), else OPF_ERR_INVALID_ARG.  The batch borrows the
+ * problems (they must outlive it) and owns a small device and pinned-host
+ * buffer for the launch descriptors.                                        */
+typedef struct opf_batch opf_batch;
+int32_t opf_batch_create(opf_problem* const* problems, int32_t n, opf_batch** out);
+/* params: n_params == 1 (the same parameters for every instance) or n
+ * entries; every entry must have the same precision.  infos: n entries
+ * (may be NULL).  Returns OPF_OK when the call ran (per-instance outcomes in
+ * infos[i].status) or an error for the whole batch.                       */
+int32_t opf_batch_solve(opf_batch* b, const opf_params* params, int32_t n_params, void* stream, opf_info* infos);
+void opf_batch_destroy(opf_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,8 @@ void device_set_state(opf_problem* p, const double* xl, const double* lam, cudaS
 void device_free(opf_problem* p);
 int device_auto_engine(const opf_problem* p, int precision);
 void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us);
+void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos);
+void device_batch_free(opf_batch* B);
 void residuals_noalloc(const double* v, const double* z, const double* zp, const double* lam, long long n,
                        double rho, double eps_rel, double* out, cudaStream_t s);
 }  // namespace opf
@@ -298,6 +300,55 @@ void opf_destroy(opf_problem* p) {
     } catch (...) {
     }
     delete p;
+}
+
+int32_t opf_batch_create(opf_problem* const* problems, int32_t n, opf_batch** out) {
+    return guarded([&]() -> int32_t {
+        if (!out || !problems || n < 1) throw opf::Error(OPF_ERR_INVALID_ARG, "need at least one problem");
+        *out = nullptr;
+        int dev = -1;
+        for (int i = 0; i < n; ++i) {
+            if (!problems[i]) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem in batch");
+            if (!problems[i]->uploaded) throw opf::Error(OPF_ERR_STATE, "batch problem not uploaded");
+            if (i && problems[i]->device != dev) throw opf::Error(OPF_ERR_INVALID_ARG, "batch spans devices");
+            dev = problems[i]->device;
+            for (int j = 0; j < i; ++j)
+                if (problems[j] == problems[i]) throw opf::Error(OPF_ERR_INVALID_ARG, "problem listed twice");
+        }
+        opf_batch* b = new opf_batch();
+        b->probs.assign(problems, problems + n);
+        b->device = dev;
+        *out = b;
+        return OPF_OK;
+    });
+}
+
+int32_t opf_batch_solve(opf_batch* b, const opf_params* prm, int32_t n_params, void* stream, opf_info* infos) {
+    return guarded([&]() -> int32_t {
+        if (!b || !prm) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        const int n = (int)b->probs.size();
+        if (n_params != 1 && n_params != n) throw opf::Error(OPF_ERR_INVALID_ARG, "n_params must be 1 or the batch size");
+        for (int i = 0; i < n_params; ++i) {
+            const opf_params& q = prm[i];
+            if (!(q.rho > 0.0) || !std::isfinite(q.rho)) throw opf::Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
+            if (q.check_every < 1 || q.check_every > 4096) throw opf::Error(OPF_ERR_INVALID_ARG, "check_every out of [1, 4096]");
+            if (q.max_iter < 0 || q.criterion < 0 || q.criterion > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad max_iter or criterion");
+            if (q.precision != prm[0].precision || (q.precision != OPF_FP64 && q.precision != OPF_FP32))
+                throw opf::Error(OPF_ERR_INVALID_ARG, "batch precision must be FP64 or FP32 for every instance");
+            if (q.residual_form != OPF_RES_PAPER) throw opf::Error(OPF_ERR_INVALID_ARG, "unsupported residual form");
+        }
+        opf::device_batch_solve(b, prm, n_params, (cudaStream_t)stream, infos);
+        return OPF_OK;
+    });
+}
+
+void opf_batch_destroy(opf_batch* b) {
+    if (!b) return;
+    try {
+        opf::device_batch_free(b);
+    } catch (...) {
+    }
+    delete b;
 }
 
 }  // extern "C"

@@ -78,6 +78,15 @@ struct GraphEntry {
 
 }  // namespace opf
 
+struct opf_batch {
+    std::vector<opf_problem*> probs;
+    void* dev_buf = nullptr;          // views, CTA map, control read-back (cudaMallocAsync)
+    size_t dev_bytes = 0;
+    char* host_buf = nullptr;         // pinned staging of the same
+    size_t host_bytes = 0;
+    int device = -1;
+};
+
 struct opf_problem {
     opf::Model model;
     std::vector<opf::Operator> ops;

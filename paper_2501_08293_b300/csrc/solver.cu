@@ -314,8 +314,7 @@ __device__ bool wait_neighbours(const View<T>& v, const BlockInfo& bi, int t, un
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void chunk_global(const View<T>& v, const int b, unsigned char* smem_raw) {
     T* zs = reinterpret_cast<T*>(smem_raw);
     __shared__ T us[kXWarps][kMaxBigN];
     __shared__ double red[kXWarps][5];
@@ -323,7 +322,6 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
     __shared__ double tot[5];
     __shared__ int s_last, s_stop, s_ok;
     Ctl* ctl = v.ctl;
-    const int b = blockIdx.x;
     const BlockInfo bi = v.blocks[b];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it0 = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
@@ -409,6 +407,12 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    chunk_global(v, blockIdx.x, smem_raw);
+}
+
 // ----------------------------------------------- persistent, shared-memory
 // Per-launch shared-memory plan (byte offsets; every region 16-byte aligned).
 struct SmemPlan {
@@ -444,8 +448,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // the global ping-pong buffers each iteration; only copies held by another
 // chunk are read from them.
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32) persistent_smem_kernel(View<T> v, SmemPlan sp) {
-    extern __shared__ __align__(128) unsigned char sm[];
+__device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const SmemPlan& sp, unsigned char* sm) {
     T* sP = reinterpret_cast<T*>(sm + sp.P);
     T* xs = reinterpret_cast<T*>(sm + sp.xs);
     T* ls = reinterpret_cast<T*>(sm + sp.ls);
@@ -464,7 +467,6 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_smem_kernel(View<T> v
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_last, s_stop, s_ok;
     Ctl* ctl = v.ctl;
-    const int b = blockIdx.x;
     const BlockInfo bi = v.blocks[b];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it0 = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
@@ -669,6 +671,68 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_smem_kernel(View<T> v
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32) persistent_smem_kernel(View<T> v, SmemPlan sp) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    chunk_smem(v, blockIdx.x, sp, sm);
+}
+
+// ------------------------------------------------------------------ batch
+// Many problems in one cooperative launch: CTA i runs chunk map[i].chunk of
+// problem map[i].inst with that problem's own view, flags, control block and
+// ticket counter, so an instance's iterates and stopping decision do not
+// depend on the other instances in the launch.
+struct CtaMap {
+    int32_t inst, chunk;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32) batch_smem_kernel(const View<T>* views, const CtaMap* map, SmemPlan sp) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ View<T> sv;
+    const CtaMap m = map[blockIdx.x];
+    if (threadIdx.x == 0) sv = views[m.inst];
+    __syncthreads();
+    chunk_smem(sv, m.chunk, sp, sm);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32) batch_global_kernel(const View<T>* views, const CtaMap* map) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ View<T> sv;
+    const CtaMap m = map[blockIdx.x];
+    if (threadIdx.x == 0) sv = views[m.inst];
+    __syncthreads();
+    chunk_global(sv, m.chunk, smem_raw);
+}
+
+// One CTA per instance: objective c^T x in a fixed order, then the instance's
+// control block is copied to a contiguous array for one read-back.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_finish_kernel(const View<T>* views, Ctl* out) {
+    __shared__ double sh[256];
+    const View<T>& v = views[blockIdx.x];
+    double s = 0;
+    for (int i = threadIdx.x; i < v.ng; i += 256) s += v.cost[i] * (double)v.zg[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        v.ctl->objective = sh[0];
+        out[blockIdx.x] = *v.ctl;
+    }
+}
+
+// Zero every instance's CTA flags (one launch for the whole batch).
+template <typename T>
+__global__ void batch_clear_flags(const View<T>* views, int n) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+        for (int b = threadIdx.x; b < views[i].nblocks; b += blockDim.x) views[i].flags[b] = 0;
+}
+
 // ------------------------------------------------------------ misc kernels
 template <typename T>
 __global__ void init_kernel(View<T> v) {
@@ -841,9 +905,16 @@ GraphEntry& get_graph(opf_problem* p, int K) {
 template <typename T>
 size_t persistent_smem(const opf_problem* p) { return (size_t)std::max(1, p->pk.max_halo) * sizeof(T); }
 
+struct ChunkMax {
+    int mat = 0, loc = 0, halo = 0, copies = 0, big = 0;
+    void add(const Packed& k) {
+        mat = std::max(mat, k.max_mat); loc = std::max(loc, k.max_loc); halo = std::max(halo, k.max_halo);
+        copies = std::max(copies, k.max_copies); big = std::max(big, k.max_big);
+    }
+};
+
 template <typename T>
-SmemPlan smem_plan(const opf_problem* p) {
-    const Packed& k = p->pk;
+SmemPlan smem_plan_of(const ChunkMax& k) {
     SmemPlan sp;
     int off = 0;
     auto take = [&](size_t bytes) {
@@ -852,17 +923,25 @@ SmemPlan smem_plan(const opf_problem* p) {
         return o;
     };
     const size_t w = sizeof(T);
-    sp.P = take((size_t)k.max_mat * w + 16);
-    sp.xs = take((size_t)k.max_loc * w); sp.ls = take((size_t)k.max_loc * w);
-    sp.bb = take((size_t)k.max_loc * w); sp.mt = take((size_t)k.max_loc * 4);
-    sp.zs = take((size_t)k.max_halo * w); sp.hlo = take((size_t)k.max_halo * w); sp.hhi = take((size_t)k.max_halo * w);
-    sp.hik = take((size_t)k.max_halo * w); sp.hck = take((size_t)k.max_halo * w);
-    sp.hp = take((size_t)(k.max_halo + 1) * 4); sp.hc = take((size_t)std::max(1, k.max_copies) * 4);
-    sp.big = k.max_big;
-    sp.us = take((size_t)kXWarps * k.max_big * w);
+    sp.P = take((size_t)k.mat * w + 16);
+    sp.xs = take((size_t)k.loc * w); sp.ls = take((size_t)k.loc * w);
+    sp.bb = take((size_t)k.loc * w); sp.mt = take((size_t)k.loc * 4);
+    sp.zs = take((size_t)k.halo * w); sp.hlo = take((size_t)k.halo * w); sp.hhi = take((size_t)k.halo * w);
+    sp.hik = take((size_t)k.halo * w); sp.hck = take((size_t)k.halo * w);
+    sp.hp = take((size_t)(k.halo + 1) * 4); sp.hc = take((size_t)std::max(1, k.copies) * 4);
+    sp.big = k.big;
+    sp.us = take((size_t)kXWarps * k.big * w);
     sp.total = off;
     return sp;
 }
+
+template <typename T>
+SmemPlan smem_plan(const opf_problem* p) {
+    ChunkMax m;
+    m.add(p->pk);
+    return smem_plan_of<T>(m);
+}
+
 
 // Can every chunk's CTA be co-resident with `smem` dynamic bytes?
 template <typename KernelT>
@@ -1212,6 +1291,152 @@ void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_
     OPF_CUDA(cudaMemcpyAsync(p->ctl, save + 2 * nl * w + ng * w, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
     OPF_CUDA(cudaFreeAsync(save, s));
     OPF_CUDA(cudaStreamSynchronize(s));
+}
+
+namespace {
+
+// Control block for a solve: parameters from prm, iteration state from the
+// host mirror (kept current after every synchronizing call).
+Ctl solve_ctl(const opf_problem* p, const opf_params& prm, const Ctl& cur) {
+    Ctl c = cur;
+    c.rho = prm.rho; c.inv_rho = 1.0 / prm.rho;
+    c.eps_abs_prim = prm.eps_abs_prim; c.eps_abs_dual = prm.eps_abs_dual; c.eps_rel = prm.eps_rel;
+    c.criterion = prm.criterion; c.K = prm.check_every;
+    const long long mi = (long long)c.iter + prm.max_iter;
+    c.max_iter = (int32_t)(mi > INT32_MAX ? INT32_MAX : mi);
+    c.status = CTL_RUNNING; c.stop = 0;
+    c.arrive = 0; c.decided = 0; c.abort = 0; c.timeout_where = 0;
+    c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
+    return c;
+}
+
+int32_t status_of(const Ctl& r, const opf_params& prm) {
+    if (r.status == CTL_CONVERGED) return OPF_OK;
+    if (r.status == CTL_NUMERIC) return OPF_ERR_NUMERIC;
+    if (r.status == CTL_TIMEOUT) return OPF_ERR_TIMEOUT;
+    if (prm.criterion == OPF_CRIT_NEVER && r.status == CTL_MAXITER) return OPF_OK;
+    return OPF_NOT_CONVERGED;
+}
+
+template <typename T>
+void batch_run(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos) {
+    const int n = (int)B->probs.size();
+    const size_t ctl_off = 0;
+    const size_t views_off = ((size_t)n * sizeof(Ctl) + 255) & ~size_t(255);
+    int nctas = 0;
+    ChunkMax cm;
+    for (opf_problem* p : B->probs) {
+        nctas += p->pk.nblocks;
+        cm.add(p->pk);
+    }
+    const size_t map_off = views_off + (((size_t)n * sizeof(View<T>) + 255) & ~size_t(255));
+    const size_t bytes = map_off + (size_t)nctas * sizeof(CtaMap);
+    if (bytes > B->dev_bytes) {
+        if (B->dev_buf) OPF_CUDA(cudaFreeAsync(B->dev_buf, s));
+        B->dev_buf = nullptr;
+        OPF_CUDA(cudaMallocAsync(&B->dev_buf, bytes, s));
+        B->dev_bytes = bytes;
+    }
+    if (bytes > B->host_bytes) {
+        OPF_CUDA(cudaStreamSynchronize(s));
+        if (B->host_buf) cudaFreeHost(B->host_buf);
+        B->host_buf = nullptr;
+        OPF_CUDA(cudaMallocHost((void**)&B->host_buf, bytes));
+        B->host_bytes = bytes;
+    }
+    Ctl* hctl = reinterpret_cast<Ctl*>(B->host_buf + ctl_off);
+    View<T>* hviews = reinterpret_cast<View<T>*>(B->host_buf + views_off);
+    CtaMap* hmap = reinterpret_cast<CtaMap*>(B->host_buf + map_off);
+    const int prec = sizeof(T) == 8 ? OPF_FP64 : OPF_FP32;
+    // initial points / precision of each instance, then its control block
+    for (int i = 0; i < n; ++i) {
+        opf_problem* p = B->probs[i];
+        const opf_params& pr = prm[nprm == 1 ? 0 : i];
+        if (!pr.warm_start) {
+            enqueue_init<T>(p, s);
+            p->cur_prec = prec;
+        } else {
+            sync_state_to(p, prec, s);
+        }
+        OPF_CUDA(cudaMemcpyAsync(hctl + i, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    }
+    OPF_CUDA(cudaStreamSynchronize(s));
+    int c = 0;
+    for (int i = 0; i < n; ++i) {
+        opf_problem* p = B->probs[i];
+        hctl[i] = solve_ctl(p, prm[nprm == 1 ? 0 : i], hctl[i]);
+        hviews[i] = view_of<T>(p, prec_of<T>(p));
+        for (int b = 0; b < p->pk.nblocks; ++b) hmap[c++] = CtaMap{i, b};
+    }
+    for (int i = 0; i < n; ++i)
+        OPF_CUDA(cudaMemcpyAsync(B->probs[i]->ctl, hctl + i, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    char* d = static_cast<char*>(B->dev_buf);
+    OPF_CUDA(cudaMemcpyAsync(d + views_off, B->host_buf + views_off, bytes - views_off, cudaMemcpyHostToDevice, s));
+    const View<T>* dviews = reinterpret_cast<const View<T>*>(d + views_off);
+    const CtaMap* dmap = reinterpret_cast<const CtaMap*>(d + map_off);
+    Ctl* dctl = reinterpret_cast<Ctl*>(d + ctl_off);
+    batch_clear_flags<T><<<std::min(n, 1024), 256, 0, s>>>(dviews, n);
+    OPF_CUDA(cudaGetLastError());
+    SmemPlan sp = smem_plan_of<T>(cm);
+    const size_t gsmem = (size_t)std::max(1, cm.halo) * sizeof(T);
+    bool any_work = false;
+    for (int i = 0; i < n; ++i) any_work |= prm[nprm == 1 ? 0 : i].max_iter > 0;
+    if (any_work) {
+        if (coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas)) {
+            void* args[] = {&dviews, &dmap, &sp};
+            OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_smem_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
+                                                 args, (size_t)sp.total, s));
+        } else if (coop_fits(batch_global_kernel<T>, gsmem, nctas)) {
+            void* args[] = {&dviews, &dmap};
+            OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_global_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
+                                                 args, gsmem, s));
+        } else {
+            throw Error(OPF_ERR_INVALID_ARG, "batch: " + std::to_string(nctas) +
+                                                 " chunks do not fit co-resident; create the problems with fewer chunks");
+        }
+    }
+    batch_finish_kernel<T><<<n, 256, 0, s>>>(dviews, dctl);
+    OPF_CUDA(cudaGetLastError());
+    OPF_CUDA(cudaMemcpyAsync(hctl, dctl, (size_t)n * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    OPF_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i) {
+        opf_problem* p = B->probs[i];
+        *p->ctl_host = hctl[i];
+        p->cold = false;
+        const Ctl& r = hctl[i];
+        if (infos) {
+            opf_info& in = infos[i];
+            in.status = status_of(r, prm[nprm == 1 ? 0 : i]);
+            in.iters = r.iter;
+            in.first_rel_iter = r.first_rel;
+            in.pres = r.pres; in.dres = r.dres; in.eps_prim = r.eps_prim; in.eps_dual = r.eps_dual;
+            in.objective = r.objective;
+            in.seconds = 0;
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (hctl[i].status == CTL_TIMEOUT)
+            throw Error(OPF_ERR_TIMEOUT, "batch: instance " + std::to_string(i) + " hit a bounded-wait limit");
+}
+
+}  // namespace
+
+void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos) {
+    DeviceGuard g(B->device);
+    auto t0 = std::chrono::steady_clock::now();
+    if (prm[0].precision == OPF_FP64) batch_run<double>(B, prm, nprm, s, infos);
+    else batch_run<float>(B, prm, nprm, s, infos);
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (infos)
+        for (size_t i = 0; i < B->probs.size(); ++i) infos[i].seconds = sec;
+}
+
+void device_batch_free(opf_batch* B) {
+    DeviceGuard g(B->device);
+    if (B->dev_buf) cudaFree(B->dev_buf);
+    if (B->host_buf) cudaFreeHost(B->host_buf);
+    B->dev_buf = nullptr;
+    B->host_buf = nullptr;
 }
 
 void device_free(opf_problem* p) {

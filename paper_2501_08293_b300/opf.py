@@ -82,6 +82,9 @@ EXPORTS = {
     "opf_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
     "opf_residuals_noalloc": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "opf_destroy": (None, [_P]),
+    "opf_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "opf_batch_solve": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, C.POINTER(Info)]),
+    "opf_batch_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in EXPORTS.items():
     _fn = getattr(lib, _name)
@@ -247,6 +250,35 @@ class Problem:
             lib.opf_destroy(self._h)
             self._h = C.c_void_p()
         self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several uploaded problems solved in one cooperative launch."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        self._h = C.c_void_p()
+        _check(lib.opf_batch_create(arr, len(self.problems), C.byref(self._h)), "opf_batch_create")
+
+    def solve(self, params, stream=None):
+        """params: one Params for all instances or a list (one per instance)."""
+        plist = params if isinstance(params, (list, tuple)) else [params]
+        arr = (Params * len(plist))(*plist)
+        infos = (Info * len(self.problems))()
+        _check(lib.opf_batch_solve(self._h, arr, len(plist), _stream_handle(stream), infos), "opf_batch_solve")
+        return list(infos)
+
+    def close(self):
+        if self._h:
+            lib.opf_batch_destroy(self._h)
+            self._h = C.c_void_p()
 
     def __del__(self):
         try:

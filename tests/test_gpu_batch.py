@@ -1,0 +1,81 @@
+"""Batch dimension: several feeders of uneven size in one cooperative launch.
+Each instance keeps its own chunks, parameters, checks and stopping
+decision, so its result in the batch equals its result alone (same chunk
+layout, same engine kernel family) and matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2501_08293_b300 import feeders as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def opf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_08293_b300 import build
+    build.build()
+    from paper_2501_08293_b300 import opf as mod
+    return mod
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1.0))
+
+
+def feeders_mix():
+    return [F.feeder_13(1), F.feeder_123(1), F.feeder_tiny(6, 2), F.feeder_123(2), F.feeder_13(3),
+            F.feeder_8500(1, n_bus=1500)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_equals_alone(opf, prec):
+    fs = feeders_mix()
+    chunks = [1, 4, 1, 3, 2, 8]
+    rhos = [100.0, 10.0, 10.0, 1000.0, 100.0, 10.0]
+    params = [opf.default_params(rho=r, precision=prec, max_iter=3000 + 500 * i, check_every=50)
+              for i, r in enumerate(rhos)]
+    alone = []
+    for f, c, prm in zip(fs, chunks, params):
+        p = opf.Problem.from_feeder(f, chunks=c)
+        info = p.solve(prm)                       # single-instance persistent engine
+        alone.append((info, p.state()))
+        p.close()
+    probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, chunks)]
+    b = opf.Batch(probs)
+    infos = b.solve(params)
+    for i, (p, info) in enumerate(zip(probs, infos)):
+        ia, sa = alone[i]
+        assert info.iters == ia.iters and info.status == ia.status, i
+        sb = p.state()
+        for x, y in zip(sb, sa):
+            assert rel(x, y) <= 1e-12, (i, rel(x, y))
+        assert abs(info.pres - ia.pres) <= 1e-10 * max(ia.pres, 1e-12)
+    # a second batch solve, warm-started, continues every instance
+    more = [opf.default_params(rho=r, precision=prec, max_iter=100, check_every=50, warm_start=1,
+                               criterion=opf.CRIT_NEVER) for r in rhos]
+    infos2 = b.solve(more)
+    for i in range(len(fs)):
+        assert infos2[i].iters == infos[i].iters + 100
+    b.close()
+    for p in probs:
+        p.close()
+
+
+def test_batch_fp64_matches_oracle(opf):
+    from oracle import admm as OA, model as OM, precompute as OP
+    fs = [F.feeder_13(2), F.feeder_123(3), F.feeder_tiny(5, 1)]
+    probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, [1, 5, 1])]
+    b = opf.Batch(probs)
+    infos = b.solve(opf.default_params(criterion=opf.CRIT_NEVER, max_iter=250, check_every=25))
+    for f, p, info in zip(fs, probs, infos):
+        m = OM.build_feeder(f)
+        s = OA.ADMM(m, OP.precompute(m), 100.0)
+        for _ in range(250):
+            r = s.step()
+        xg, xl, lam = p.state()
+        assert rel(xg, s.x) <= 1e-9 and rel(xl, s.z) <= 1e-9 and rel(lam, s.lam) <= 1e-9
+        assert abs(info.pres - r.pres) <= 1e-9 * r.pres
+    b.close()
