@@ -124,7 +124,12 @@ enum { OPF_ENGINE_AUTO = 0, OPF_ENGINE_GRAPH = 1, OPF_ENGINE_HOSTLOOP = 2, OPF_E
  * PERSISTENT runs it as one cooperative kernel whose CTAs own feeder chunks
  * and wait only on neighbouring chunks (every wait bounded in time, see
  * opf_debug_config); AUTO picks PERSISTENT when the chunks fit co-resident
- * on the device, else GRAPH.                                                */
+ * on the device, else GRAPH.
+ * adaptive_rho 1 enables residual balancing, the acceleration the paper
+ * names in Section III-D: at every residual check that does not stop,
+ * rho *= rb_tau when pres > rb_mu * dres and rho /= rb_tau when dres >
+ * rb_mu * pres (duals are unscaled, so they are kept; the operators do not
+ * depend on rho).  The current rho is reported in opf_info.rho.            */
 typedef struct opf_params {
     double rho;
     double eps_abs_prim, eps_abs_dual, eps_rel;
@@ -135,7 +140,8 @@ typedef struct opf_params {
     int32_t residual_form;
     int32_t warm_start;
     int32_t engine;
-    int32_t _reserved;
+    int32_t adaptive_rho;
+    double rb_mu, rb_tau;
 } opf_params;
 
 /* Result of a solve.  iters counts all iterations since the last cold
@@ -145,10 +151,11 @@ typedef struct opf_info {
     int32_t status;
     int32_t iters;
     int32_t first_rel_iter;
-    int32_t _pad;
+    int32_t rho_changes;     /* residual-balancing updates of rho in this solve */
     double pres, dres, eps_prim, eps_dual;
     double objective;
     double seconds;
+    double rho;              /* rho at the end of the solve                     */
 } opf_info;
 
 /* Sizes of a built problem. */

@@ -36,7 +36,7 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):
         return LIB
-    cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17",
+    cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-fmad=false",
            "-Xcompiler", "-fPIC,-O3,-Wall", "-shared", "-cudart", "shared",
            "-I", INCLUDE, "-I", CSRC, "-o", LIB + ".tmp", *srcs]
     if ptxas_info:

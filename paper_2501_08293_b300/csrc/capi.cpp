@@ -97,6 +97,9 @@ void opf_params_default(opf_params* p) {
     p->residual_form = OPF_RES_PAPER;
     p->warm_start = 0;
     p->engine = OPF_ENGINE_AUTO;
+    p->adaptive_rho = 0;
+    p->rb_mu = 10.0;
+    p->rb_tau = 2.0;
 }
 
 int32_t opf_problem_create_ex(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
@@ -176,6 +179,8 @@ int32_t opf_admm_solve(opf_problem* p, const opf_params* prm, void* stream, opf_
         if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
         if (prm->residual_form != OPF_RES_PAPER) throw opf::Error(OPF_ERR_INVALID_ARG, "unsupported residual form");
         if (prm->engine < 0 || prm->engine > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad engine");
+        if (prm->adaptive_rho && !(prm->rb_mu > 1.0 && prm->rb_tau > 1.0))
+            throw opf::Error(OPF_ERR_INVALID_ARG, "residual balancing needs rb_mu > 1 and rb_tau > 1");
         return opf::device_solve(p, *prm, (cudaStream_t)stream, info);
     });
 }
@@ -336,6 +341,8 @@ int32_t opf_batch_solve(opf_batch* b, const opf_params* prm, int32_t n_params, v
             if (q.precision != prm[0].precision || (q.precision != OPF_FP64 && q.precision != OPF_FP32))
                 throw opf::Error(OPF_ERR_INVALID_ARG, "batch precision must be FP64 or FP32 for every instance");
             if (q.residual_form != OPF_RES_PAPER) throw opf::Error(OPF_ERR_INVALID_ARG, "unsupported residual form");
+            if (q.adaptive_rho && !(q.rb_mu > 1.0 && q.rb_tau > 1.0))
+                throw opf::Error(OPF_ERR_INVALID_ARG, "residual balancing needs rb_mu > 1 and rb_tau > 1");
         }
         opf::device_batch_solve(b, prm, n_params, (cudaStream_t)stream, infos);
         return OPF_OK;

@@ -66,12 +66,13 @@ struct Tile {
 // One CTA's share of a problem: a contiguous chunk of the component order
 // (a DFS over the feeder, so chunks are subtrees with few neighbours).
 struct BlockInfo {
-    int32_t tile0, tile1;   // tiles [tile0, tile1)
-    int32_t halo0, halo1;   // globals read by the chunk [halo0, halo1)
+    int32_t tile0, tile1;   // tiles [tile0, tile1); [tile0, tileb) are interior
+    int32_t halo0, halo1;   // globals read by the chunk [halo0, halo1); [halo0, halob) are interior
     int32_t nbr0, nbr1;     // neighbour CTAs (share a global) [nbr0, nbr1)
     int32_t loc0, loc1;     // locals [loc0, loc1)
     int32_t mat0, mat1;     // operator elements [mat0, mat1) of the chunk's tiles
     int32_t cp0, cp1;       // copy list entries of the chunk's halo [cp0, cp1)
+    int32_t tileb, halob;   // first boundary tile / halo entry
 };
 
 // Device-ordered problem, ready to upload.
@@ -101,6 +102,7 @@ struct Packed {
     int max_mat = 0;                     // largest chunk operator span (elements)
     int max_copies = 0;                  // largest chunk halo copy list
     int max_big = 0;                     // largest component with n > 32 (0: none)
+    int max_tiles = 0;                   // most tiles in one chunk
 };
 
 Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,

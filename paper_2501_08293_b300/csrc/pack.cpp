@@ -95,6 +95,13 @@ void validate(const Packed& K) {
         if (bi.loc1 - bi.loc0 > K.max_loc || bi.mat1 - bi.mat0 > K.max_mat || bi.cp1 - bi.cp0 > K.max_copies) fail("maxima");
         for (int q = bi.nbr0; q < bi.nbr1; ++q)
             if (K.nbrs[q] < 0 || K.nbrs[q] >= K.nblocks || K.nbrs[q] == b) fail("neighbour");
+        if (bi.tileb < bi.tile0 || bi.tileb > bi.tile1 || bi.halob < bi.halo0 || bi.halob > bi.halo1) fail("interior split");
+        for (int h = bi.halo0; h < bi.halob; ++h)
+            for (int q = K.hcp[h]; q < K.hcp[h + 1]; ++q)
+                if (K.hci[q] < 0) fail("interior halo entry with an outside copy");
+        for (int t = bi.tile0; t < bi.tileb; ++t)
+            for (int r = 0; r < K.tiles[t].L; ++r)
+                if ((K.meta[K.tiles[t].loc0 + r] & 0xFFFF) >= bi.halob - bi.halo0) fail("interior tile reads a boundary global");
         for (int t = bi.tile0; t < bi.tile1; ++t) {
             const Tile& tl = K.tiles[t];
             const int lanes = tl.L;
@@ -179,6 +186,21 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
     K.canon_of_dev.assign(K.nl, -1);
     K.meta.assign(K.nl, 0);
     std::vector<int> comp_block(K.ncomp, -1);
+    for (int b = 0; b < K.nblocks; ++b)
+        for (int q = chunk_start[b]; q < chunk_start[b + 1]; ++q) comp_block[order[q]] = b;
+    // a global is interior to a chunk when every copy is in that chunk
+    std::vector<int> gblock(K.ng, -1);
+    std::vector<char> gshared(K.ng, 0);
+    for (int s2 = 0; s2 < K.ncomp; ++s2)
+        for (int g : M.comps[s2].gvars) {
+            if (gblock[g] < 0) gblock[g] = comp_block[s2];
+            else if (gblock[g] != comp_block[s2]) gshared[g] = 1;
+        }
+    auto comp_boundary = [&](int s2) {
+        for (int g : M.comps[s2].gvars)
+            if (gshared[g]) return true;
+        return false;
+    };
     int loc = 0;
     int64_t mat = 0;
     for (int b = 0; b < K.nblocks; ++b) {
@@ -188,13 +210,22 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         mat = (mat + 3) & ~int64_t(3);
         bi.mat0 = (int32_t)mat;
         std::vector<int> comps(order.begin() + chunk_start[b], order.begin() + chunk_start[b + 1]);
-        std::stable_sort(comps.begin(), comps.end(),
-                         [&](int a, int c) { return M.comps[a].n() > M.comps[c].n(); });
-        for (int s : comps) comp_block[s] = b;
-        // first-fit-decreasing into warps
+        // interior components first, each group by decreasing n
+        std::stable_sort(comps.begin(), comps.end(), [&](int a, int c) {
+            const bool ba = comp_boundary(a), bc = comp_boundary(c);
+            if (ba != bc) return !ba;
+            return M.comps[a].n() > M.comps[c].n();
+        });
+        // first-fit-decreasing into warps, interior and boundary apart
         std::vector<std::vector<int>> warps;
         std::vector<int> lanes;
+        size_t first_boundary_warp = 0;
+        bool in_boundary = false;
         for (int s : comps) {
+            if (!in_boundary && comp_boundary(s)) {
+                in_boundary = true;
+                first_boundary_warp = warps.size();
+            }
             const int n = M.comps[s].n();
             if (n == 0) continue;
             if (n > 32) {
@@ -204,7 +235,7 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
                 continue;
             }
             bool placed = false;
-            for (size_t w = 0; w < warps.size(); ++w)
+            for (size_t w = in_boundary ? first_boundary_warp : 0; w < warps.size(); ++w)
                 if (lanes[w] >= 0 && lanes[w] + n <= 32) {
                     warps[w].push_back(s);
                     lanes[w] += n;
@@ -216,6 +247,8 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
                 lanes.push_back(n);
             }
         }
+        if (!in_boundary) first_boundary_warp = warps.size();
+        bi.tileb = bi.tile0 + (int)first_boundary_warp;
         for (size_t w = 0; w < warps.size(); ++w) {
             mat = (mat + 3) & ~int64_t(3);   // 32-byte aligned tile start (f64)
             if (mat > INT32_MAX) throw Error(OPF_ERR_INVALID_ARG, "problem too large");
@@ -262,6 +295,7 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         bi.tile1 = (int)K.tiles.size();
         bi.loc1 = loc;
         bi.mat1 = (int32_t)mat;
+        K.max_tiles = std::max(K.max_tiles, bi.tile1 - bi.tile0);
         K.max_loc = std::max(K.max_loc, bi.loc1 - bi.loc0);
         K.max_mat = std::max(K.max_mat, bi.mat1 - bi.mat0);
         K.blocks.push_back(bi);
@@ -319,14 +353,19 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
     for (int b = 0; b < K.nblocks; ++b) {
         BlockInfo& bi = K.blocks[b];
         bi.halo0 = (int)K.halo_gid.size();
-        for (int j = bi.loc0; j < bi.loc1; ++j) {
-            const int g = K.gidx[j];
-            if (hmark[g] != b) {
+        for (int pass = 0; pass < 2; ++pass) {           // interior globals, then boundary
+            if (pass == 1) bi.halob = (int)K.halo_gid.size();
+            for (int j = bi.loc0; j < bi.loc1; ++j) {
+                const int g = K.gidx[j];
+                if ((int)gshared[g] != pass || hmark[g] == b) continue;
                 hmark[g] = b;
                 hpos[g] = (int)K.halo_gid.size() - bi.halo0;
                 K.halo_gid.push_back(g);
                 K.halo_own.push_back(owner[g] == b ? 1 : 0);
             }
+        }
+        for (int j = bi.loc0; j < bi.loc1; ++j) {
+            const int g = K.gidx[j];
             if (hpos[g] > 0xFFFF) throw Error(OPF_ERR_INVALID_ARG, "chunk halo too large");
             K.meta[j] |= hpos[g];
         }

@@ -29,7 +29,10 @@ struct Ctl {
     int32_t decided;              // checks decided
     int32_t abort;                // a wait gave up: every CTA leaves
     int32_t skip_block;           // test hook: this CTA withholds its flag (-1: none)
-    int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait
+    int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait, 4 staging
+    int32_t adaptive;             // residual balancing on
+    int32_t rho_changes;
+    double rb_mu, rb_tau;
 };
 enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_MAXITER = 2, CTL_NUMERIC = 3, CTL_TIMEOUT = 4 };
 

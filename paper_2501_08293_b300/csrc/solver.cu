@@ -73,6 +73,41 @@ __device__ __forceinline__ double warp_sum(double a) {
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
+// The arithmetic of one iteration, written once with explicit fused
+// multiply-adds (the library is built with -fmad=false, so nothing else is
+// contracted): every engine and kernel computes bit-identical iterates.
+template <typename T>
+__device__ __forceinline__ T copy_term(T x, T l, T inv_rho) { return fma(-l, inv_rho, x); }            // x - l/rho
+template <typename T>
+__device__ __forceinline__ T global_from_sum(T s, T invk, T cik, T inv_rho, T lo, T hi) {
+    const T xh = fma(s, invk, -(cik * inv_rho));                                                          // s/k - c/(rho k)
+    return fmin(fmax(xh, lo), hi);
+}
+template <typename T>
+__device__ __forceinline__ T u_of(T v, T l, T inv_rho) { return fma(l, inv_rho, v); }                 // Bx + l/rho
+template <typename T>
+__device__ __forceinline__ T dual_of(T l, T rho, T v, T xn) { return fma(rho, v - xn, l); }            // l + rho (Bx - z)
+
+// Small-tile GEMV of one lane: y = sum_c P[c][r] u_c over the lane's
+// component, two interleaved partial sums (even / odd c) for latency.
+template <typename T>
+__device__ __forceinline__ T tile_gemv(const T* Pt, int L, int lane, int nmax, int n, int base, T u, bool act) {
+    T y0 = 0, y1 = 0;
+    int c = 0;
+#pragma unroll 2
+    for (; c + 1 < nmax; c += 2) {
+        const T u0 = __shfl_sync(0xffffffffu, u, (base + c) & 31);
+        const T u1 = __shfl_sync(0xffffffffu, u, (base + c + 1) & 31);
+        if (act && c < n) y0 = fma(Pt[c * L + lane], u0, y0);
+        if (act && c + 1 < n) y1 = fma(Pt[(c + 1) * L + lane], u1, y1);
+    }
+    if (c < nmax) {
+        const T u0 = __shfl_sync(0xffffffffu, u, (base + c) & 31);
+        if (act && c < n) y0 = fma(Pt[c * L + lane], u0, y0);
+    }
+    return y0 + y1;
+}
+
 // Eq. (global_sparse) for global g from the copies in (xr, lr).
 template <typename T, bool CG>
 __device__ __forceinline__ T global_value(const View<T>& v, int g, const T* xr, const T* lr, T inv_rho) {
@@ -80,11 +115,10 @@ __device__ __forceinline__ T global_value(const View<T>& v, int g, const T* xr, 
     T s = 0;
     for (int j = b; j < e; ++j) {
         const int l = v.gcol[j];
-        if (CG) s += ldcg(xr + l) - ldcg(lr + l) * inv_rho;
-        else s += xr[l] - lr[l] * inv_rho;
+        if (CG) s += copy_term(ldcg(xr + l), ldcg(lr + l), inv_rho);
+        else s += copy_term(xr[l], lr[l], inv_rho);
     }
-    const T xh = s * v.invk[g] - v.cik[g] * inv_rho;
-    return fmin(fmax(xh, v.lo[g]), v.hi[g]);
+    return global_from_sum(s, v.invk[g], v.cik[g], inv_rho, v.lo[g], v.hi[g]);
 }
 
 // Local update + dual update of one tile (Eq. closed_2, Eq. ADMM-3).
@@ -106,18 +140,12 @@ __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int
             vv = getv(j, m);
             lo = ldcg(lr + j);
             xo = ldcg(xr + j);
-            u = vv + lo * inv_rho;
+            u = u_of(vv, lo, inv_rho);
         }
-        const T* Pm = v.P + tl.mat0 + lane;
-        T y = 0;
-#pragma unroll 4
-        for (int c = 0; c < nmax; ++c) {
-            const T uc = __shfl_sync(0xffffffffu, u, (base + c) & 31);
-            if (act && c < n) y = fma(Pm[c * L], uc, y);
-        }
+        const T y = tile_gemv(v.P + tl.mat0, L, lane, nmax, n, base, u, act);
         if (act) {
             const T xn = y + v.bbar[j];
-            const T ln = lo + rho * (vv - xn);
+            const T ln = dual_of(lo, rho, vv, xn);
             xw[j] = xn;
             lw[j] = ln;
             if (want) {
@@ -130,7 +158,7 @@ __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int
         const int n = tl.nmax;
         for (int r = lane; r < n; r += 32) {
             const int j = tl.loc0 + r;
-            us[r] = getv(j, v.meta[j]) + ldcg(lr + j) * inv_rho;
+            us[r] = u_of(getv(j, v.meta[j]), ldcg(lr + j), inv_rho);
         }
         __syncwarp();
         const T* Pm = v.P + tl.mat0;
@@ -141,7 +169,7 @@ __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int
             const T vv = getv(j, v.meta[j]);
             const T lo = ldcg(lr + j), xo = ldcg(xr + j);
             const T xn = y + v.bbar[j];
-            const T ln = lo + rho * (vv - xn);
+            const T ln = dual_of(lo, rho, vv, xn);
             xw[j] = xn;
             lw[j] = ln;
             if (want) {
@@ -166,24 +194,6 @@ __device__ __forceinline__ void cta_partials(double* acc, double (*red)[5], doub
         for (int w = 0; w < kXWarps; ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
-}
-
-// Fixed-order sum of nparts partial records (8 doubles each) by one CTA of
-// kFinThreads threads; thread 0 gets the five sums in tot.
-__device__ __forceinline__ void sum_partials(const double* partials, int nparts, double (*sh)[kFinThreads],
-                                             double* tot, bool cg) {
-    double s[5] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nparts; b += kFinThreads)
-        for (int k = 0; k < 5; ++k) s[k] += cg ? __ldcg(partials + (size_t)b * 8 + k) : partials[(size_t)b * 8 + k];
-    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = s[k];
-    __syncthreads();
-    for (int w = kFinThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 5; ++k) tot[k] = sh[k][0];
 }
 
 // Fixed-order sum of nparts partial records by one CTA using only the
@@ -233,6 +243,16 @@ __device__ __forceinline__ int decide(Ctl* ctl, const double* s, int it) {
         ctl->status = CTL_MAXITER;
         return 1;
     }
+    if (ctl->adaptive) {                // residual balancing
+        double rho = ctl->rho;
+        if (pres > ctl->rb_mu * dres) rho *= ctl->rb_tau;
+        else if (dres > ctl->rb_mu * pres) rho /= ctl->rb_tau;
+        if (rho != ctl->rho) {
+            ctl->rho = rho;
+            ctl->inv_rho = 1.0 / rho;
+            ctl->rho_changes += 1;
+        }
+    }
     return 0;
 }
 
@@ -261,7 +281,9 @@ __global__ void __launch_bounds__(kXWarps * 32) x_kernel(View<T> v, int q) {
     const T* zg = v.zg;
     const int32_t* gidx = v.gidx;
     auto getv = [zg, gidx](int j, int) { return zg[gidx[j]]; };
-    for (int t = bi.tile0 + warp; t < bi.tile1; t += kXWarps)
+    for (int t = bi.tile0 + warp; t < bi.tileb; t += kXWarps)
+        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
+    for (int t = bi.tileb + warp; t < bi.tile1; t += kXWarps)
         tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
     if (!want) return;
     cta_partials(acc, red, v.partials + (size_t)blockIdx.x * 8);
@@ -272,9 +294,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(View<T> v, cudaGr
     Ctl* ctl = v.ctl;
     const int iter = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
     const int ndone = max(0, min(K, maxit - iter));
-    __shared__ double sh[5][kFinThreads];
+    __shared__ double red[kXWarps][5];
     __shared__ double tot[5];
-    if (ndone > 0) sum_partials(v.partials, v.nblocks, sh, tot, false);
+    static_assert(kFinThreads == kXWarps * 32, "finalize reduction layout");
+    if (ndone > 0) sum_partials_small(v.partials, v.nblocks, red, tot);
     if (threadIdx.x != 0) return;
     const int it = iter + ndone;
     ctl->iter = it;
@@ -318,14 +341,14 @@ __device__ __forceinline__ void chunk_global(const View<T>& v, const int b, unsi
     T* zs = reinterpret_cast<T*>(smem_raw);
     __shared__ T us[kXWarps][kMaxBigN];
     __shared__ double red[kXWarps][5];
-    __shared__ double sh[5][kFinThreads];
     __shared__ double tot[5];
     __shared__ int s_last, s_stop, s_ok;
+    __shared__ double s_rho;
     Ctl* ctl = v.ctl;
     const BlockInfo bi = v.blocks[b];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it0 = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
-    const T rho = (T)ctl->rho, inv_rho = (T)ctl->inv_rho;
+    T rho = (T)ctl->rho, inv_rho = (T)ctl->inv_rho;
     const unsigned long long tmo = ctl->timeout_ns;
     const bool withhold = (ctl->skip_block == b);
     int t = 0, checkno = 0;
@@ -348,7 +371,9 @@ __device__ __forceinline__ void chunk_global(const View<T>& v, const int b, unsi
         const bool check = ((t + 1) % K == 0) || nrem == 1;
         double acc[5] = {0, 0, 0, 0, 0};
         auto getv = [zs](int, int m) { return zs[m & 0xFFFF]; };
-        for (int q = bi.tile0 + warp; q < bi.tile1; q += kXWarps)
+        for (int q = bi.tile0 + warp; q < bi.tileb; q += kXWarps)
+            tile_update<T>(v, v.tiles[q], lane, rho, inv_rho, xr, lr, xw, lw, check, acc, us[warp], getv);
+        for (int q = bi.tileb + warp; q < bi.tile1; q += kXWarps)
             tile_update<T>(v, v.tiles[q], lane, rho, inv_rho, xr, lr, xw, lw, check, acc, us[warp], getv);
         __syncthreads();
         ++t;
@@ -366,7 +391,7 @@ __device__ __forceinline__ void chunk_global(const View<T>& v, const int b, unsi
             }
             __syncthreads();
             if (s_last) {
-                sum_partials(v.partials, v.nblocks, sh, tot, true);
+                sum_partials_small(v.partials, v.nblocks, red, tot);
                 if (threadIdx.x == 0) {
                     ctl->iter = it0 + t;
                     ctl->stop = decide(ctl, tot, it0 + t);
@@ -388,8 +413,11 @@ __device__ __forceinline__ void chunk_global(const View<T>& v, const int b, unsi
                 }
                 s_ok = ok;
                 s_stop = ok ? ld_acquire(&ctl->stop) : 1;
+                s_rho = __ldcg(&ctl->rho);
             }
             __syncthreads();
+            rho = (T)s_rho;
+            inv_rho = (T)(1.0 / s_rho);
             ++checkno;
             if (!s_ok) return;
             if (s_stop) done = true;
@@ -416,7 +444,7 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
 // ----------------------------------------------- persistent, shared-memory
 // Per-launch shared-memory plan (byte offsets; every region 16-byte aligned).
 struct SmemPlan {
-    int P, xs, ls, bb, mt, zs, hlo, hhi, hik, hck, hp, hc, us, big, total;
+    int P, xs, ls, bb, mt, zs, hlo, hhi, hik, hck, hp, hc, us, big, tl, total;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -462,15 +490,17 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     int* hp = reinterpret_cast<int*>(sm + sp.hp);
     int* hc = reinterpret_cast<int*>(sm + sp.hc);
     T* usw = reinterpret_cast<T*>(sm + sp.us);          // big-tile staging, sp.big per warp
+    Tile* stl = reinterpret_cast<Tile*>(sm + sp.tl);    // the chunk's tile descriptors
     __shared__ double red[kXWarps][5];
     __shared__ double tot[5];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_last, s_stop, s_ok;
+    __shared__ double s_rho;
     Ctl* ctl = v.ctl;
     const BlockInfo bi = v.blocks[b];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it0 = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
-    const T rho = (T)ctl->rho, inv_rho = (T)ctl->inv_rho;
+    T rho = (T)ctl->rho, inv_rho = (T)ctl->inv_rho;
     const unsigned long long tmo = ctl->timeout_ns;
     const bool withhold = (ctl->skip_block == b);
     const int nloc = bi.loc1 - bi.loc0, nh = bi.halo1 - bi.halo0, ncp = bi.cp1 - bi.cp0;
@@ -500,6 +530,8 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     }
     if (threadIdx.x == 0) hp[nh] = ncp;
     for (int q = threadIdx.x; q < ncp; q += blockDim.x) hc[q] = v.hci[bi.cp0 + q];
+    for (int q = threadIdx.x; q < bi.tile1 - bi.tile0; q += blockDim.x) stl[q] = v.tiles[bi.tile0 + q];
+    const int hb = bi.halob - bi.halo0;                // interior halo entries [0, hb)
     int ok = 1;
     if (pbytes) {
         const unsigned long long deadline = now_ns() + tmo;
@@ -521,30 +553,22 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
 
     int t = 0, checkno = 0;
     bool done = it0 >= maxit;
-    while (!done) {
-        if (t > 0 && !wait_neighbours(v, bi, t, tmo, &s_ok)) return;
-        const T* xr = (t & 1) ? v.xl2 : v.xl;
-        const T* lr = (t & 1) ? v.lam2 : v.lam;
-        T* xw = (t & 1) ? v.xl : v.xl2;
-        T* lw = (t & 1) ? v.lam : v.lam2;
-        // global update of the halo, Eq. (global_sparse), copies in CSR order
-        for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+    // global update of halo entries [h0, h1), Eq. (global_sparse), copies in CSR order
+    auto zphase = [&](int h0, int h1, const T* xr, const T* lr) {
+        for (int h = h0 + threadIdx.x; h < h1; h += blockDim.x) {
             T sum = 0;
             for (int q = hp[h]; q < hp[h + 1]; ++q) {
                 const int c = hc[q];
-                if (c >= 0) sum += xs[c] - ls[c] * inv_rho;
-                else sum += __ldcg(xr + ~c) - __ldcg(lr + ~c) * inv_rho;
+                if (c >= 0) sum += copy_term(xs[c], ls[c], inv_rho);
+                else sum += copy_term(__ldcg(xr + ~c), __ldcg(lr + ~c), inv_rho);
             }
-            const T xh = sum * hik[h] - hck[h] * inv_rho;
-            zs[h] = fmin(fmax(xh, hlo[h]), hhi[h]);
+            zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
         }
-        __syncthreads();
-        const int nrem = maxit - (it0 + t);
-        const bool check = ((t + 1) % K == 0) || nrem == 1;
-        double acc[5] = {0, 0, 0, 0, 0};
-        // local + dual updates, Eq. (closed_2) and Eq. (ADMM-3)
-        for (int q = bi.tile0 + warp; q < bi.tile1; q += kXWarps) {
-            const Tile tl = v.tiles[q];
+    };
+    // local + dual updates of tiles [q0, q1) (chunk-relative), Eq. (closed_2), Eq. (ADMM-3)
+    auto xphase = [&](int q0, int q1, T* xw, T* lw, bool check, double* acc) {
+        for (int q = q0 + warp; q < q1; q += kXWarps) {
+            const Tile tl = stl[q];
             const int jl0 = tl.loc0 - bi.loc0;
             const T* Pt = sP + (tl.mat0 - bi.mat0);
             if (!tl.big) {
@@ -560,17 +584,12 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                     vv = zs[m & 0xFFFF];
                     lo = ls[jl];
                     xo = xs[jl];
-                    u = vv + lo * inv_rho;
+                    u = u_of(vv, lo, inv_rho);
                 }
-                T y = 0;
-#pragma unroll 4
-                for (int c = 0; c < nmax; ++c) {
-                    const T uc = __shfl_sync(0xffffffffu, u, (base + c) & 31);
-                    if (act && c < n) y = fma(Pt[c * L + lane], uc, y);
-                }
+                const T y = tile_gemv(Pt, L, lane, nmax, n, base, u, act);
                 if (act) {
                     const T xn = y + bb[jl];
-                    const T ln = lo + rho * (vv - xn);
+                    const T ln = dual_of(lo, rho, vv, xn);
                     xs[jl] = xn;
                     ls[jl] = ln;
                     if (m & (1 << 30)) {
@@ -587,7 +606,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
             } else {
                 const int n = tl.nmax;
                 T* us = usw + warp * sp.big;
-                for (int r = lane; r < n; r += 32) us[r] = zs[mt[jl0 + r] & 0xFFFF] + ls[jl0 + r] * inv_rho;
+                for (int r = lane; r < n; r += 32) us[r] = u_of(zs[mt[jl0 + r] & 0xFFFF], ls[jl0 + r], inv_rho);
                 __syncwarp();
                 for (int r = lane; r < n; r += 32) {
                     T y = 0;
@@ -597,7 +616,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                     const T vv = zs[m & 0xFFFF];
                     const T lo = ls[jl], xo = xs[jl];
                     const T xn = y + bb[jl];
-                    const T ln = lo + rho * (vv - xn);
+                    const T ln = dual_of(lo, rho, vv, xn);
                     xs[jl] = xn;
                     ls[jl] = ln;
                     if (m & (1 << 30)) {
@@ -614,6 +633,25 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                 __syncwarp();
             }
         }
+    };
+    const int ntl = bi.tile1 - bi.tile0, ntb = bi.tileb - bi.tile0;
+    while (!done) {
+        const T* xr = (t & 1) ? v.xl2 : v.xl;
+        const T* lr = (t & 1) ? v.lam2 : v.lam;
+        T* xw = (t & 1) ? v.xl : v.xl2;
+        T* lw = (t & 1) ? v.lam : v.lam2;
+        const int nrem = maxit - (it0 + t);
+        const bool check = ((t + 1) % K == 0) || nrem == 1;
+        double acc[5] = {0, 0, 0, 0, 0};
+        // interior part: needs nothing from the neighbours
+        zphase(0, hb, xr, lr);
+        __syncthreads();
+        xphase(0, ntb, xw, lw, check, acc);
+        // boundary part, once every neighbour has published iteration t
+        if (t > 0 && !wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+        zphase(hb, nh, xr, lr);
+        __syncthreads();
+        xphase(ntb, ntl, xw, lw, check, acc);
         __syncthreads();
         ++t;
         if (threadIdx.x == 0 && !withhold) {
@@ -652,8 +690,11 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                 }
                 s_ok = okw;
                 s_stop = okw ? ld_acquire(&ctl->stop) : 1;
+                s_rho = __ldcg(&ctl->rho);
             }
             __syncthreads();
+            rho = (T)s_rho;
+            inv_rho = (T)(1.0 / s_rho);
             ++checkno;
             if (!s_ok) return;
             if (s_stop) done = true;
@@ -906,10 +947,10 @@ template <typename T>
 size_t persistent_smem(const opf_problem* p) { return (size_t)std::max(1, p->pk.max_halo) * sizeof(T); }
 
 struct ChunkMax {
-    int mat = 0, loc = 0, halo = 0, copies = 0, big = 0;
+    int mat = 0, loc = 0, halo = 0, copies = 0, big = 0, tiles = 0;
     void add(const Packed& k) {
         mat = std::max(mat, k.max_mat); loc = std::max(loc, k.max_loc); halo = std::max(halo, k.max_halo);
-        copies = std::max(copies, k.max_copies); big = std::max(big, k.max_big);
+        copies = std::max(copies, k.max_copies); big = std::max(big, k.max_big); tiles = std::max(tiles, k.max_tiles);
     }
 };
 
@@ -931,6 +972,7 @@ SmemPlan smem_plan_of(const ChunkMax& k) {
     sp.hp = take((size_t)(k.halo + 1) * 4); sp.hc = take((size_t)std::max(1, k.copies) * 4);
     sp.big = k.big;
     sp.us = take((size_t)kXWarps * k.big * w);
+    sp.tl = take((size_t)std::max(1, k.tiles) * sizeof(Tile));
     sp.total = off;
     return sp;
 }
@@ -1187,6 +1229,7 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
     c.status = CTL_RUNNING; c.stop = 0;
     c.arrive = 0; c.decided = 0; c.abort = 0; c.timeout_where = 0;
     c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
+    c.adaptive = prm.adaptive_rho; c.rb_mu = prm.rb_mu; c.rb_tau = prm.rb_tau; c.rho_changes = 0;
     *p->ctl_host = c;
     OPF_CUDA(cudaMemcpyAsync(p->ctl, p->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     if (prm.max_iter > 0) {
@@ -1208,6 +1251,8 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
         info->first_rel_iter = r.first_rel;
         info->pres = r.pres; info->dres = r.dres; info->eps_prim = r.eps_prim; info->eps_dual = r.eps_dual;
         info->objective = r.objective;
+        info->rho = r.rho;
+        info->rho_changes = r.rho_changes;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     if (st == OPF_ERR_TIMEOUT)
@@ -1307,6 +1352,7 @@ Ctl solve_ctl(const opf_problem* p, const opf_params& prm, const Ctl& cur) {
     c.status = CTL_RUNNING; c.stop = 0;
     c.arrive = 0; c.decided = 0; c.abort = 0; c.timeout_where = 0;
     c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
+    c.adaptive = prm.adaptive_rho; c.rb_mu = prm.rb_mu; c.rb_tau = prm.rb_tau; c.rho_changes = 0;
     return c;
 }
 
@@ -1411,6 +1457,8 @@ void batch_run(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, op
             in.first_rel_iter = r.first_rel;
             in.pres = r.pres; in.dres = r.dres; in.eps_prim = r.eps_prim; in.eps_dual = r.eps_dual;
             in.objective = r.objective;
+            in.rho = r.rho;
+            in.rho_changes = r.rho_changes;
             in.seconds = 0;
         }
     }

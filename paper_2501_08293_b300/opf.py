@@ -30,7 +30,8 @@ class Params(C.Structure):
     _fields_ = [("rho", C.c_double), ("eps_abs_prim", C.c_double), ("eps_abs_dual", C.c_double),
                 ("eps_rel", C.c_double), ("criterion", C.c_int32), ("max_iter", C.c_int32),
                 ("check_every", C.c_int32), ("precision", C.c_int32), ("residual_form", C.c_int32),
-                ("warm_start", C.c_int32), ("engine", C.c_int32), ("_reserved", C.c_int32)]
+                ("warm_start", C.c_int32), ("engine", C.c_int32), ("adaptive_rho", C.c_int32),
+                ("rb_mu", C.c_double), ("rb_tau", C.c_double)]
 
 
 class CreateOptions(C.Structure):
@@ -39,9 +40,9 @@ class CreateOptions(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("first_rel_iter", C.c_int32),
-                ("_pad", C.c_int32), ("pres", C.c_double), ("dres", C.c_double),
+                ("rho_changes", C.c_int32), ("pres", C.c_double), ("dres", C.c_double),
                 ("eps_prim", C.c_double), ("eps_dual", C.c_double), ("objective", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("rho", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("_")}
