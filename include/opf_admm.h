@@ -339,6 +339,55 @@ int32_t opf_batch_create(opf_problem* const* problems, int32_t n, opf_batch** ou
 int32_t opf_batch_solve(opf_batch* b, const opf_params* params, int32_t n_params, void* stream, opf_info* infos);
 void opf_batch_destroy(opf_batch* b);
 
+/* ----------------------------------------------------------------- serving
+ * Continuous batching: requests (feeders) are submitted at any time; each
+ * opf_server_step collects the round in flight, retires finished instances,
+ * admits queued requests in arrival order while a slot, the device memory
+ * budget and the co-resident chunk capacity allow (finished instances stay
+ * resident for warm starts and are evicted least recently used first), and
+ * launches the next round asynchronously: round_iters iterations of one
+ * batch launch over every active instance.  Host-side model building and
+ * precompute (in submit) and uploads (in step, on a side stream) overlap the
+ * round running on the device.  A request with warm_from = id of a finished
+ * resident request starts from that feeder's iterate for every local copy
+ * whose component and global variable are unchanged (a topology switch).
+ * Rounds are whole multiples of params.check_every and all engines compute
+ * bit-identical iterates, so a request's result does not depend on the mix.
+ * Not thread-safe across steps; submit may be called between steps.        */
+typedef struct opf_server opf_server;
+
+typedef struct opf_server_config {
+    int64_t device_budget_bytes;  /* resident instance arenas stay below this   */
+    int32_t max_active;           /* instances iterated per round                */
+    int32_t round_iters;          /* iterations per round, multiple of check_every */
+    int32_t max_chunks;           /* CTAs per round (0: 4 per SM)                */
+    int32_t _reserved[3];
+    opf_params params;            /* solve parameters of every request; max_iter
+                                     is each request's iteration budget          */
+} opf_server_config;
+
+typedef struct opf_server_stats {
+    int64_t submitted, admitted, completed, converged, warm_started, evicted, rounds, iterations;
+    int64_t resident_bytes;
+    int32_t active, pending;
+} opf_server_stats;
+
+void opf_server_config_default(opf_server_config* c);  /* FP32, rho 10, ABS 1e-4, 8 GiB */
+int32_t opf_server_create(const opf_server_config* cfg, opf_server** out);
+/* chunks <= 0: one chunk per 400 buses (1..64).  *id receives the request id. */
+int32_t opf_server_submit(opf_server* s, const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
+                          const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
+                          int32_t chunks, int64_t warm_from, int64_t* id);
+int32_t opf_server_step(opf_server* s, void* stream, int32_t* n_active, int32_t* n_pending);
+/* Finished requests since the last poll: ids[k], infos[k] (infos[k].seconds =
+ * latency from submit to the end of the round that finished it).          */
+int32_t opf_server_poll(opf_server* s, int64_t* ids, opf_info* infos, int32_t cap, int32_t* n);
+/* The resident problem of a finished request (borrowed; valid until it is
+ * evicted or the server is destroyed): use opf_get_solution / opf_get_state. */
+int32_t opf_server_problem(opf_server* s, int64_t id, opf_problem** p);
+int32_t opf_server_get_stats(opf_server* s, opf_server_stats* stats);
+void opf_server_destroy(opf_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,13 @@ void residuals_noalloc(const double* v, const double* z, const double* zp, const
 
 namespace {
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace opf {
+void set_last_error(const std::string& m) { g_last_error = m; }
+}  // namespace opf
+
+namespace {
 
 template <typename F>
 int32_t guarded(F&& f) {

@@ -88,6 +88,8 @@ struct opf_batch {
     char* host_buf = nullptr;         // pinned staging of the same
     size_t host_bytes = 0;
     int device = -1;
+    cudaEvent_t done = nullptr;       // end of the last launched batch
+    int n_launched = 0;
 };
 
 struct opf_problem {

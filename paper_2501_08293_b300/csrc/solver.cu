@@ -774,6 +774,19 @@ __global__ void batch_clear_flags(const View<T>* views, int n) {
         for (int b = threadIdx.x; b < views[i].nblocks; b += blockDim.x) views[i].flags[b] = 0;
 }
 
+// Warm start across a topology change: new local j takes the old iterate and
+// dual of local map[j] (same component, same position, same global
+// variable), or keeps its initial point when map[j] < 0.
+template <typename T>
+__global__ void warm_gather_kernel(const int32_t* __restrict__ map, const T* __restrict__ oxl, const T* __restrict__ olam,
+                                   T* __restrict__ nxl, T* __restrict__ nlam, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n && map[j] >= 0) {
+        nxl[j] = oxl[map[j]];
+        nlam[j] = olam[map[j]];
+    }
+}
+
 // ------------------------------------------------------------ misc kernels
 template <typename T>
 __global__ void init_kernel(View<T> v) {
@@ -1166,6 +1179,7 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     p->ctl = (Ctl*)(a + L.ctl);
     if (!p->ctl_host) OPF_CUDA(cudaMallocHost((void**)&p->ctl_host, sizeof(Ctl)));
     std::memset(p->ctl_host, 0, sizeof(Ctl));
+    p->ctl_host->first_rel = -1;                 // mirror of the state init_kernel leaves
 
     auto h2d = [&](void* dst, const void* src, size_t n) {
         if (n) OPF_CUDA(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s));
@@ -1364,8 +1378,12 @@ int32_t status_of(const Ctl& r, const opf_params& prm) {
     return OPF_NOT_CONVERGED;
 }
 
+// Enqueue a batch solve on `s` without waiting: initial points, control
+// blocks built from each problem's host mirror, flags cleared, one
+// cooperative launch, objectives and a single read-back of all control
+// blocks into pinned memory; B->done is recorded at the end.
 template <typename T>
-void batch_run(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos) {
+void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s) {
     const int n = (int)B->probs.size();
     const size_t ctl_off = 0;
     const size_t views_off = ((size_t)n * sizeof(Ctl) + 255) & ~size_t(255);
@@ -1390,29 +1408,29 @@ void batch_run(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, op
         OPF_CUDA(cudaMallocHost((void**)&B->host_buf, bytes));
         B->host_bytes = bytes;
     }
+    if (!B->done) OPF_CUDA(cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming));
     Ctl* hctl = reinterpret_cast<Ctl*>(B->host_buf + ctl_off);
     View<T>* hviews = reinterpret_cast<View<T>*>(B->host_buf + views_off);
     CtaMap* hmap = reinterpret_cast<CtaMap*>(B->host_buf + map_off);
     const int prec = sizeof(T) == 8 ? OPF_FP64 : OPF_FP32;
-    // initial points / precision of each instance, then its control block
+    int c = 0;
+    bool any_work = false;
     for (int i = 0; i < n; ++i) {
         opf_problem* p = B->probs[i];
         const opf_params& pr = prm[nprm == 1 ? 0 : i];
+        Ctl cur = *p->ctl_host;
         if (!pr.warm_start) {
             enqueue_init<T>(p, s);
             p->cur_prec = prec;
+            cur.iter = 0; cur.first_rel = -1; cur.checks = 0;
+            cur.pres = cur.dres = cur.eps_prim = cur.eps_dual = NAN;
         } else {
             sync_state_to(p, prec, s);
         }
-        OPF_CUDA(cudaMemcpyAsync(hctl + i, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-    }
-    OPF_CUDA(cudaStreamSynchronize(s));
-    int c = 0;
-    for (int i = 0; i < n; ++i) {
-        opf_problem* p = B->probs[i];
-        hctl[i] = solve_ctl(p, prm[nprm == 1 ? 0 : i], hctl[i]);
+        hctl[i] = solve_ctl(p, pr, cur);
         hviews[i] = view_of<T>(p, prec_of<T>(p));
         for (int b = 0; b < p->pk.nblocks; ++b) hmap[c++] = CtaMap{i, b};
+        any_work |= pr.max_iter > 0;
     }
     for (int i = 0; i < n; ++i)
         OPF_CUDA(cudaMemcpyAsync(B->probs[i]->ctl, hctl + i, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -1425,8 +1443,6 @@ void batch_run(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, op
     OPF_CUDA(cudaGetLastError());
     SmemPlan sp = smem_plan_of<T>(cm);
     const size_t gsmem = (size_t)std::max(1, cm.halo) * sizeof(T);
-    bool any_work = false;
-    for (int i = 0; i < n; ++i) any_work |= prm[nprm == 1 ? 0 : i].max_iter > 0;
     if (any_work) {
         if (coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas)) {
             void* args[] = {&dviews, &dmap, &sp};
@@ -1444,7 +1460,18 @@ void batch_run(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, op
     batch_finish_kernel<T><<<n, 256, 0, s>>>(dviews, dctl);
     OPF_CUDA(cudaGetLastError());
     OPF_CUDA(cudaMemcpyAsync(hctl, dctl, (size_t)n * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-    OPF_CUDA(cudaStreamSynchronize(s));
+    OPF_CUDA(cudaEventRecord(B->done, s));
+    B->n_launched = n;
+}
+
+}  // namespace
+
+// Wait for the batch launched last and publish each instance's outcome.
+void device_batch_collect(opf_batch* B, const opf_params* prm, int nprm, opf_info* infos) {
+    DeviceGuard g(B->device);
+    OPF_CUDA(cudaEventSynchronize(B->done));
+    const int n = B->n_launched;
+    const Ctl* hctl = reinterpret_cast<const Ctl*>(B->host_buf);
     for (int i = 0; i < n; ++i) {
         opf_problem* p = B->probs[i];
         *p->ctl_host = hctl[i];
@@ -1467,13 +1494,20 @@ void batch_run(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, op
             throw Error(OPF_ERR_TIMEOUT, "batch: instance " + std::to_string(i) + " hit a bounded-wait limit");
 }
 
+void device_batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s) {
+    DeviceGuard g(B->device);
+    if (prm[0].precision == OPF_FP64) batch_launch<double>(B, prm, nprm, s);
+    else batch_launch<float>(B, prm, nprm, s);
+}
+
+namespace {
 }  // namespace
 
 void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos) {
     DeviceGuard g(B->device);
     auto t0 = std::chrono::steady_clock::now();
-    if (prm[0].precision == OPF_FP64) batch_run<double>(B, prm, nprm, s, infos);
-    else batch_run<float>(B, prm, nprm, s, infos);
+    device_batch_launch(B, prm, nprm, s);
+    device_batch_collect(B, prm, nprm, infos);
     const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (infos)
         for (size_t i = 0; i < B->probs.size(); ++i) infos[i].seconds = sec;
@@ -1481,10 +1515,44 @@ void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStrea
 
 void device_batch_free(opf_batch* B) {
     DeviceGuard g(B->device);
+    if (B->done) cudaEventDestroy(B->done);
+    B->done = nullptr;
     if (B->dev_buf) cudaFree(B->dev_buf);
     if (B->host_buf) cudaFreeHost(B->host_buf);
     B->dev_buf = nullptr;
     B->host_buf = nullptr;
+}
+
+// Copy the old problem's iterate into the new one where the local copies
+// correspond (map built by the caller, device order of the new problem, old
+// device indices).  Both problems on the same device; runs on `s`.
+void device_warm_transfer(opf_problem* dst, const opf_problem* src, const std::vector<int32_t>& map, cudaStream_t s) {
+    DeviceGuard g(dst->device);
+    const int prec = src->cur_prec;
+    const int n = dst->pk.nl;
+    if ((int)map.size() != n) throw Error(OPF_ERR_INVALID_ARG, "warm map size");
+    int32_t* dmap = nullptr;
+    OPF_CUDA(cudaMallocAsync((void**)&dmap, sizeof(int32_t) * std::max(1, n), s));
+    OPF_CUDA(cudaMemcpyAsync(dmap, map.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    // the new problem starts from its initial point in the old one's precision
+    if (prec == OPF_FP64) enqueue_init<double>(dst, s);
+    else enqueue_init<float>(dst, s);
+    const DevPrec& sd = prec == OPF_FP64 ? src->d64 : src->d32;
+    const DevPrec& dd = prec == OPF_FP64 ? dst->d64 : dst->d32;
+    if (n > 0) {
+        if (prec == OPF_FP64)
+            warm_gather_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(dmap, (const double*)sd.xl, (const double*)sd.lam,
+                                                                      (double*)dd.xl, (double*)dd.lam, n);
+        else
+            warm_gather_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(dmap, (const float*)sd.xl, (const float*)sd.lam,
+                                                                     (float*)dd.xl, (float*)dd.lam, n);
+        OPF_CUDA(cudaGetLastError());
+    }
+    OPF_CUDA(cudaFreeAsync(dmap, s));
+    dst->cur_prec = prec;
+    dst->cold = false;
+    Ctl& m = *dst->ctl_host;
+    m.iter = 0; m.first_rel = -1; m.checks = 0;
 }
 
 void device_free(opf_problem* p) {

@@ -390,6 +390,51 @@ def feeder_batch(n: int, seed: int, lo: int = 100, hi: int = 2500) -> list[Feede
     return out
 
 
+def reconfigure(f: Feeder, rng) -> Feeder:
+    """A topology switch that keeps the feeder radial and connected: close
+    one open tie line and open an in-service line on the loop it closes.
+    Returns a copy; if the feeder has no open tie, a closed tree switch is
+    opened and closed again elsewhere is not attempted (the copy is equal)."""
+    g = f.copy()
+    ties = [e for e in range(len(g.lines)) if g.lines["in_service"][e] == 0]
+    if not ties:
+        return g
+    tie = int(ties[rng.integers(0, len(ties))])
+    a, b = int(g.lines["from_bus"][tie]), int(g.lines["to_bus"][tie])
+    # parent pointers of the current spanning tree (BFS from the root)
+    adj = [[] for _ in range(g.n_bus)]
+    for e in range(len(g.lines)):
+        if g.lines["in_service"][e]:
+            u, v = int(g.lines["from_bus"][e]), int(g.lines["to_bus"][e])
+            adj[u].append((v, e)); adj[v].append((u, e))
+    par = [(-1, -1)] * g.n_bus
+    seen = [False] * g.n_bus
+    seen[0] = True
+    queue = [0]
+    for u in queue:
+        for v, e in adj[u]:
+            if not seen[v]:
+                seen[v] = True
+                par[v] = (u, e)
+                queue.append(v)
+    def path(u):
+        out = []
+        while u != 0:
+            out.append(par[u][1]); u = par[u][0]
+        return out
+    pa, pb = path(a), path(b)
+    common = set(pa) & set(pb)
+    loop = [e for e in pa + pb if e not in common]
+    # open a line on the loop whose phases match the tie's (keeps every bus fed)
+    cand = [e for e in loop if int(g.lines["phases"][e]) == int(g.lines["phases"][tie])]
+    if not cand:
+        return g
+    off = int(cand[rng.integers(0, len(cand))])
+    g.lines["in_service"][tie] = 1
+    g.lines["in_service"][off] = 0
+    return g
+
+
 CONFIG_FEEDERS = {
     "13": feeder_13,
     "123": feeder_123,

@@ -57,6 +57,20 @@ class Dims(C.Structure):
                 ("max_chunk_copies", C.c_int32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("device_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("round_iters", C.c_int32),
+                ("max_chunks", C.c_int32), ("_reserved", C.c_int32 * 3), ("params", Params)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "admitted", "completed", "converged", "warm_started",
+                                         "evicted", "rounds", "iterations", "resident_bytes")] + \
+               [("active", C.c_int32), ("pending", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int32)
@@ -86,6 +100,15 @@ EXPORTS = {
     "opf_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "opf_batch_solve": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, C.POINTER(Info)]),
     "opf_batch_destroy": (None, [_P]),
+    "opf_server_config_default": (None, [C.POINTER(ServerConfig)]),
+    "opf_server_create": (C.c_int32, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
+    "opf_server_submit": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32,
+                                      C.c_int32, C.c_int64, C.POINTER(C.c_int64)]),
+    "opf_server_step": (C.c_int32, [_P, _P, _I, _I]),
+    "opf_server_poll": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(Info), C.c_int32, _I]),
+    "opf_server_problem": (C.c_int32, [_P, C.c_int64, C.POINTER(C.c_void_p)]),
+    "opf_server_get_stats": (C.c_int32, [_P, C.POINTER(ServerStats)]),
+    "opf_server_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in EXPORTS.items():
     _fn = getattr(lib, _name)
@@ -171,6 +194,19 @@ class Problem:
     def from_feeder(cls, f, **kw) -> "Problem":
         return cls(f.buses, f.lines, f.gens, f.loads, **kw)
 
+    @classmethod
+    def borrowed(cls, handle, n_bus, n_line, n_gen, n_load) -> "Problem":
+        """Non-owning view of a handle owned elsewhere (e.g. a server)."""
+        p = cls.__new__(cls)
+        p._h = C.c_void_p(handle)
+        p._arrays = []
+        p.dims = Dims()
+        _check(lib.opf_get_dims(p._h, C.byref(p.dims)), "opf_get_dims")
+        p.n_bus, p.n_line, p.n_gen, p.n_load = n_bus, n_line, n_gen, n_load
+        p._arena = None
+        p._borrowed = True
+        return p
+
     def upload(self, device=None, stream=None):
         import torch
         if not torch.cuda.is_available():
@@ -247,9 +283,9 @@ class Problem:
         return out
 
     def close(self):
-        if self._h:
+        if self._h and not getattr(self, "_borrowed", False):
             lib.opf_destroy(self._h)
-            self._h = C.c_void_p()
+        self._h = C.c_void_p()
         self._arena = None
 
     def __del__(self):
@@ -279,6 +315,69 @@ class Batch:
     def close(self):
         if self._h:
             lib.opf_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_server_config(**kw) -> ServerConfig:
+    c = ServerConfig()
+    lib.opf_server_config_default(C.byref(c))
+    for k, v in kw.items():
+        if k in ("device_budget_bytes", "max_active", "round_iters", "max_chunks"):
+            setattr(c, k, v)
+        else:
+            setattr(c.params, k, v)
+    return c
+
+
+class Server:
+    """Continuous-batching OPF server (opf_server_*)."""
+
+    def __init__(self, config: ServerConfig | None = None, **kw):
+        cfg = config if config is not None else default_server_config(**kw)
+        self._h = C.c_void_p()
+        _check(lib.opf_server_create(C.byref(cfg), C.byref(self._h)), "opf_server_create")
+        self._shapes = {}
+
+    def submit(self, f, warm_from: int = -1, chunks: int = 0) -> int:
+        arrs = [np.ascontiguousarray(a) for a in (f.buses, f.lines, f.gens, f.loads)]
+        rid = C.c_int64()
+        _check(lib.opf_server_submit(self._h, arrs[0].ctypes.data, len(arrs[0]), arrs[1].ctypes.data, len(arrs[1]),
+                                     arrs[2].ctypes.data, len(arrs[2]), arrs[3].ctypes.data, len(arrs[3]),
+                                     int(chunks), int(warm_from), C.byref(rid)), "opf_server_submit")
+        self._shapes[rid.value] = tuple(len(a) for a in arrs)
+        return rid.value
+
+    def step(self, stream=None):
+        na, npend = C.c_int32(), C.c_int32()
+        _check(lib.opf_server_step(self._h, _stream_handle(stream), C.byref(na), C.byref(npend)), "opf_server_step")
+        return na.value, npend.value
+
+    def poll(self, cap: int = 1024):
+        ids = (C.c_int64 * cap)()
+        infos = (Info * cap)()
+        n = C.c_int32()
+        _check(lib.opf_server_poll(self._h, ids, infos, cap, C.byref(n)), "opf_server_poll")
+        return [(ids[k], infos[k]) for k in range(n.value)]
+
+    def problem(self, rid: int) -> Problem:
+        h = C.c_void_p()
+        _check(lib.opf_server_problem(self._h, int(rid), C.byref(h)), "opf_server_problem")
+        return Problem.borrowed(h.value, *self._shapes[rid])
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib.opf_server_get_stats(self._h, C.byref(st)), "opf_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib.opf_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):
