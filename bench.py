@@ -10,6 +10,8 @@ timed solve, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
     python bench.py --impl reference   # the CPU oracle on the same workload
+    python bench.py --workload batch   # 256 feeders (100-2500 buses) in one launch
+    python bench.py --workload serve   # Poisson stream of requests, continuous batching
 """
 from __future__ import annotations
 
@@ -33,7 +35,7 @@ WORKLOAD = "synthetic 8500-class feeder (11,932 nodes, 1200 loads, 200 PV), rho=
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
@@ -44,7 +46,24 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="8500", choices=["8500", "batch", "serve"])
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--batch-iters", type=int, default=2000)
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=100.0, help="request arrivals per second")
+    ap.add_argument("--serve-max-bus", type=int, default=2500)
+    ap.add_argument("--serve-budget-iters", type=int, default=200000)
+    ap.add_argument("--profile-solve", type=int, default=0,
+                    help="only run one solve of this many iterations (a small case for ncu captures)")
     return ap.parse_args()
+
+
+def golden_lp():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "lp_objectives.json")) as fh:
+            return {k: v["objective"] for k, v in json.load(fh)["feeders"].items()}
+    except Exception:
+        return {}
 
 
 # ------------------------------------------------------------------ helpers
@@ -301,6 +320,25 @@ def run_ours(args):
                 "seconds_per_step": sum(e2e_times) / len(e2e_times)},
         "gpu_launches": launches,
     }
+    # precision: FP32 sweeps vs the FP64 GPU path on the 123-bus configuration
+    # and the objective of each result against the LP optimum (HiGHS, stored)
+    lp = golden_lp()
+    prec_rep = {"objective_rel_err_vs_lp": (abs(infos[-1]["objective"] - lp["8500"]) / abs(lp["8500"])
+                                            if "8500" in lp else None)}
+    f123 = F.feeder_123(1)
+    p123 = opf.Problem.from_feeder(f123)
+    res = {}
+    for nm, pc in (("fp64", opf.FP64), ("fp32", opf.FP32)):
+        inf = p123.solve(opf.default_params(rho=args.rho, precision=pc, max_iter=args.max_iter, check_every=50))
+        res[nm] = inf.as_dict()
+    p123.close()
+    prec_rep["123bus"] = {
+        "fp64": {k: res["fp64"][k] for k in ("status", "iters", "pres", "dres", "objective")},
+        "fp32": {k: res["fp32"][k] for k in ("status", "iters", "pres", "dres", "objective")},
+        "fp32_vs_fp64_objective_rel": abs(res["fp32"]["objective"] - res["fp64"]["objective"]) / abs(res["fp64"]["objective"]),
+        "fp64_vs_lp_objective_rel": (abs(res["fp64"]["objective"] - lp["123"]) / abs(lp["123"]) if "123" in lp else None),
+    }
+    out["precision"] = prec_rep
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, n, dt = cpu_oracle_rate(f, args.rho, args.cpu_seconds)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -313,9 +351,158 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """256 feeders of uneven size, each with its own switch state and load
+    draw, iterated in one cooperative launch; one step = batch-iters
+    iterations of every feeder; value = feeder-iterations per second."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+    rng = np.random.default_rng(args.seed)
+    fs = [F.reconfigure(f, rng) for f in F.feeder_batch(args.batch, args.seed)]
+    prec = opf.FP64 if args.precision == "fp64" else opf.FP32
+    probs = [opf.Problem.from_feeder(f, chunks=max(1, (f.n_bus + 599) // 600)) for f in fs]
+    bt = opf.Batch(probs)
+    prm = opf.default_params(rho=args.rho, precision=prec, criterion=opf.CRIT_NEVER, max_iter=args.batch_iters,
+                             check_every=50)
+    for _ in range(args.warmup):
+        bt.solve(prm)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.solve(prm)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    tot = sum(times)
+    w = 8 if prec == opf.FP64 else 4
+    bytes_iter = sum(w * p.dims.sum_n2 + p.dims.n_local * (8 * w + 8) + p.dims.n_global * (5 * w + 4) for p in probs)
+    iters = args.steps * args.batch_iters * len(probs)
+    peaks, kind = measured_peaks()
+    achieved = bytes_iter * args.steps * args.batch_iters / tot / 1e9
+    # to tolerance (capped): solves per second of the whole batch
+    tt = opf.default_params(rho=args.rho, precision=prec, max_iter=args.serve_budget_iters, check_every=50)
+    t0 = time.perf_counter()
+    infos = bt.solve(tt)
+    tsol = time.perf_counter() - t0
+    conv = sum(1 for i in infos if i.status == opf.OK)
+    print(json.dumps({
+        "metric": "batched feeder ADMM iterations/s (256 feeders, one launch)", "value": iters / tot,
+        "unit": "feeder-iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == opf.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": f"{len(fs)} synthetic feeders, n_bus ~ U[100, 2500], random switch state and loads",
+                   "rho": args.rho, "iters_per_step": args.batch_iters, "ctas": sum(p.dims.n_blocks for p in probs),
+                   "buses": int(sum(f.n_bus for f in fs)), "l2": "flushed before each step; data > L2"},
+        "roofline": {"kernel": "batch persistent kernel", "bound": "hbm", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": None, "peak_kind": kind, "bytes_per_batch_iter": bytes_iter},
+        "to_tolerance": {"budget_iters": args.serve_budget_iters, "converged": conv, "of": len(infos),
+                         "seconds": tsol, "solves_per_s": conv / tsol,
+                         "iters_max": max(i.iters for i in infos)},
+        "clocks": clk.summary(), "gpu_launches": 4 * (args.steps + args.warmup),
+    }))
+
+
+def run_serve(args):
+    """Poisson stream of requests (sizes log-uniform, 30 % topology switches
+    of a resident feeder warm-started from its last iterate), continuous
+    batching; reports solves/s and p50/p99 latency."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+    rng = np.random.default_rng(args.seed)
+    prec = opf.FP64 if args.precision == "fp64" else opf.FP32
+    srv = opf.Server(precision=prec, rho=args.rho, max_iter=args.serve_budget_iters, check_every=50,
+                     round_iters=1000, max_active=256)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=args.requests))
+    sizes = np.exp(rng.uniform(np.log(13), np.log(args.serve_max_bus), size=args.requests)).astype(int)
+    done_feeders = []            # (request id, feeder) finished and possibly resident
+    kind = {}
+    t0 = time.perf_counter()
+    nxt = 0
+    results = {}
+    warm_n = 0
+    while len(results) < args.requests:
+        now = time.perf_counter() - t0
+        while nxt < args.requests and arrivals[nxt] <= now:
+            if done_feeders and rng.random() < 0.3:
+                rid0, f0 = done_feeders[int(rng.integers(0, len(done_feeders)))]
+                g = F.reconfigure(f0, rng)
+                rid = srv.submit(g, warm_from=rid0)
+                kind[rid] = ("warm", g)
+                warm_n += 1
+            else:
+                nb = int(max(13, sizes[nxt]))
+                g = F.make_feeder(nb, int(rng.integers(1 << 30)), n_loads=max(1, nb // 8),
+                                  load_sampler=lambda r: r.lognormal(-4.0, 1.0), n_pv=max(1, nb // 60),
+                                  n_switches=4, line_mix=(0.6, 0.15, 0.25), v_ll_kv=12.47, lateral_mean=5.0)
+                rid = srv.submit(g)
+                kind[rid] = ("cold", g)
+            nxt += 1
+        srv.step()
+        for rid, info in srv.poll():
+            results[rid] = info
+            done_feeders.append((rid, kind[rid][1]))
+    wall = time.perf_counter() - t0
+    lat = np.array([results[r].seconds for r in results])
+    conv = sum(1 for r in results if results[r].status == opf.OK)
+    st = srv.stats()
+    srv.close()
+    print(json.dumps({
+        "metric": "served OPF solves/s (continuous batching)", "value": len(results) / wall, "unit": "solves/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == opf.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, n_bus log-uniform [13, {args.serve_max_bus}], "
+                               f"30% topology switches warm-started, ABS 1e-4, budget {args.serve_budget_iters} iterations",
+                   "rho": args.rho},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean())},
+        "converged": conv, "warm_requests": warm_n, "wall_s": wall, "server": st,
+    }))
+
+
+def run_profile_solve(args):
+    """One fixed-length solve of the 8500-class feeder (no timing, no output
+    beyond a status line): the small case used for ncu captures."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+    prec = opf.FP64 if args.precision == "fp64" else opf.FP32
+    engine = {"auto": opf.ENGINE_AUTO, "graph": opf.ENGINE_GRAPH, "persistent": opf.ENGINE_PERSISTENT,
+              "hostloop": opf.ENGINE_HOSTLOOP}[args.engine]
+    p = opf.Problem.from_feeder(F.feeder_8500(args.seed))
+    info = p.solve(opf.default_params(rho=args.rho, precision=prec, criterion=opf.CRIT_NEVER,
+                                      max_iter=args.profile_solve, check_every=args.check_every, engine=engine))
+    print("profile solve", info.iters, info.pres, info.dres)
+    p.close()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile_solve:
+        run_profile_solve(a)
+    elif a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_ours(a)

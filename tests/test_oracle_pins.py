@@ -471,3 +471,14 @@ def test_rank_deficient_component_uses_row_reduction():
     U, S, Vt = np.linalg.svd(bus1.A)
     N = Vt[2:].T
     np.testing.assert_allclose(-pre.Abar[1], N @ N.T, atol=1e-12)
+
+
+def test_golden_lp_objectives_reproduce():
+    """tests/golden/lp_objectives.json (written by make_lp_objectives.py,
+    oracle only) matches a fresh HiGHS solve on the small feeders."""
+    import json, os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "lp_objectives.json")) as fh:
+        g = json.load(fh)["feeders"]
+    for name, f in (("13", F.feeder_13(1)), ("123", F.feeder_123(1))):
+        r = OL.solve_lp(OM.build_feeder(f))
+        assert r.status == 0 and abs(r.fun - g[name]["objective"]) <= 1e-9 * abs(r.fun)
