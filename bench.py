@@ -238,15 +238,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    tot = sum(times)
-    iters_all = float(iters)
-    if world > 1:
-        t = torch.tensor([tot], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-        it = torch.tensor([float(iters)], device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        iters_all = float(it.item())
+    from paper_2501_08293_b300.replicas import aggregate
+    tot, iters_all = aggregate(sum(times), iters, device="cuda")
     value = iters_all / tot
     ms_per_step = 1e3 * tot / args.steps
 
@@ -365,7 +358,12 @@ def run_batch(args):
     rng = np.random.default_rng(args.seed)
     fs = [F.reconfigure(f, rng) for f in F.feeder_batch(args.batch, args.seed)]
     prec = opf.FP64 if args.precision == "fp64" else opf.FP32
-    probs = [opf.Problem.from_feeder(f, chunks=max(1, (f.n_bus + 599) // 600)) for f in fs]
+    # each feeder's chunk count in proportion to its size, all co-resident
+    cap = opf.batch_capacity(prec)
+    tot_bus = sum(f.n_bus for f in fs)
+    spare = max(0, cap - len(fs))
+    chunks = [1 + int(spare * f.n_bus / tot_bus) for f in fs]
+    probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, chunks)]
     bt = opf.Batch(probs)
     prm = opf.default_params(rho=args.rho, precision=prec, criterion=opf.CRIT_NEVER, max_iter=args.batch_iters,
                              check_every=50)

@@ -274,6 +274,15 @@ int32_t opf_get_solution(const opf_problem* p, double* w, double* pg, double* qg
  * cudaMallocAsync on `stream` and freed before returning).                 */
 int32_t opf_profile_kernels(opf_problem* p, const opf_params* params, int32_t reps, void* stream, double* us);
 
+/* Per-iteration time of each phase of the shared-memory persistent kernel,
+ * in microseconds, measured on the device (globaltimer, thread 0 of each
+ * CTA): out[0..3] = mean over CTAs of {interior halo + tile updates, wait
+ * for the neighbours, boundary halo + tile updates, flag release + residual
+ * check}; out[4..7] = the maximum over CTAs.  Runs `iters` iterations from
+ * the initial point (the problem is left at that iterate); needs the
+ * shared-memory kernel to fit (else OPF_ERR_INVALID_ARG).                  */
+int32_t opf_profile_persistent(opf_problem* p, const opf_params* params, int32_t iters, void* stream, double* out);
+
 /* Engine that OPF_ENGINE_AUTO selects for this problem and precision on the
  * problem's device (OPF_ENGINE_PERSISTENT or OPF_ENGINE_GRAPH).            */
 int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine);
@@ -338,6 +347,9 @@ int32_t opf_batch_create(opf_problem* const* problems, int32_t n, opf_batch** ou
  * infos[i].status) or an error for the whole batch.                       */
 int32_t opf_batch_solve(opf_batch* b, const opf_params* params, int32_t n_params, void* stream, opf_info* infos);
 void opf_batch_destroy(opf_batch* b);
+/* Chunks (CTAs) that one batch launch can hold co-resident on the current
+ * device: the sum of the problems' chunk counts must not exceed it.        */
+int32_t opf_batch_capacity(int32_t precision, int32_t* max_chunks);
 
 /* ----------------------------------------------------------------- serving
  * Continuous batching: requests (feeders) are submitted at any time; each
@@ -360,7 +372,8 @@ typedef struct opf_server_config {
     int64_t device_budget_bytes;  /* resident instance arenas stay below this   */
     int32_t max_active;           /* instances iterated per round                */
     int32_t round_iters;          /* iterations per round, multiple of check_every */
-    int32_t max_chunks;           /* CTAs per round (0: 4 per SM)                */
+    int32_t max_chunks;           /* CTAs per round (0: the device's batch capacity,
+                                     opf_batch_capacity)                         */
     int32_t _reserved[3];
     opf_params params;            /* solve parameters of every request; max_iter
                                      is each request's iteration budget          */

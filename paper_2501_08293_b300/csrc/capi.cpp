@@ -20,7 +20,9 @@ void device_free(opf_problem* p);
 int device_auto_engine(const opf_problem* p, int precision);
 void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us);
 void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos);
+void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters, cudaStream_t s, double* out);
 void device_batch_free(opf_batch* B);
+int device_batch_capacity(int precision);
 void residuals_noalloc(const double* v, const double* z, const double* zp, const double* lam, long long n,
                        double rho, double eps_rel, double* out, cudaStream_t s);
 }  // namespace opf
@@ -259,6 +261,18 @@ int32_t opf_profile_kernels(opf_problem* p, const opf_params* prm, int32_t reps,
     });
 }
 
+int32_t opf_profile_persistent(opf_problem* p, const opf_params* prm, int32_t iters, void* stream, double* out) {
+    return guarded([&]() -> int32_t {
+        if (!p || !prm || !out) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "profile before upload");
+        if (iters < 1) throw opf::Error(OPF_ERR_INVALID_ARG, "iters must be >= 1");
+        if (!(prm->rho > 0.0) || (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) || prm->check_every < 1)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
+        opf::device_profile_persistent(p, *prm, iters, (cudaStream_t)stream, out);
+        return OPF_OK;
+    });
+}
+
 int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine) {
     return guarded([&]() -> int32_t {
         if (!p || !engine) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
@@ -352,6 +366,15 @@ int32_t opf_batch_solve(opf_batch* b, const opf_params* prm, int32_t n_params, v
                 throw opf::Error(OPF_ERR_INVALID_ARG, "residual balancing needs rb_mu > 1 and rb_tau > 1");
         }
         opf::device_batch_solve(b, prm, n_params, (cudaStream_t)stream, infos);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_batch_capacity(int32_t precision, int32_t* max_chunks) {
+    return guarded([&]() -> int32_t {
+        if (!max_chunks) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (precision != OPF_FP64 && precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
+        *max_chunks = opf::device_batch_capacity(precision);
         return OPF_OK;
     });
 }

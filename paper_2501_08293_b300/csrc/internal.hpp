@@ -52,9 +52,14 @@ struct Operator {
     std::vector<double> bbar;   // n
 };
 
+// Warps per CTA of the local-update kernels; the packer balances tiles over
+// this many warps (a tile at chunk position q is run by warp q % kTileWarps).
+constexpr int kTileWarps = 8;
+
 // Work item of the local-update kernel: one warp.  Small tiles hold whole
 // components (sizes n_g <= 32, sum n_g = L <= 32 lanes, nmax = max n_g);
-// a big tile holds one component with n > 32 (flag big = 1).
+// a big tile holds one component with n > 32 (flag big = 1); L = 0 marks an
+// empty padding tile.
 struct Tile {
     int32_t loc0;   // first local (device order)
     int32_t mat0;   // first operator element

@@ -108,7 +108,8 @@ void validate(const Packed& K) {
             const int64_t span = tl.big ? (int64_t)tl.L * tl.L : (int64_t)tl.nmax * tl.L;
             if (tl.loc0 < bi.loc0 || tl.loc0 + lanes > bi.loc1) fail("tile locals");
             if (tl.mat0 < bi.mat0 || tl.mat0 + span > bi.mat1 || (tl.mat0 & 3)) fail("tile operators");
-            if (!tl.big && (lanes < 1 || lanes > 32 || tl.nmax < 1 || tl.nmax > 32)) fail("small tile shape");
+            if (!tl.big && lanes == 0 && tl.nmax != 0) fail("padding tile shape");
+            if (!tl.big && lanes != 0 && (lanes < 1 || lanes > 32 || tl.nmax < 1 || tl.nmax > 32)) fail("small tile shape");
             if (tl.big && (tl.nmax != tl.L || tl.L <= 32 || tl.L > 255)) fail("big tile shape");
             for (int r = 0; r < lanes; ++r) {
                 const int j = tl.loc0 + r;
@@ -248,8 +249,50 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
             }
         }
         if (!in_boundary) first_boundary_warp = warps.size();
-        bi.tileb = bi.tile0 + (int)first_boundary_warp;
-        for (size_t w = 0; w < warps.size(); ++w) {
+        // balance each range (interior, boundary) over the CTA's warps:
+        // longest tile first to the least loaded warp, then lay the tiles out
+        // so that position q of the range is run by warp q % kTileWarps
+        // (empty padding tiles where a warp has fewer tiles)
+        auto tile_cost = [&](size_t w) {
+            if (lanes[w] < 0) {
+                const int n = M.comps[warps[w][0]].n();
+                return (int64_t)n * ((n + 31) / 32) + 16;
+            }
+            int nmax = 0;
+            for (int s2 : warps[w]) nmax = std::max(nmax, M.comps[s2].n());
+            return (int64_t)nmax + 8;
+        };
+        std::vector<long> layout;              // indices into warps, -1 = padding
+        for (int range = 0; range < 2; ++range) {
+            const size_t r0 = range == 0 ? 0 : first_boundary_warp;
+            const size_t r1 = range == 0 ? first_boundary_warp : warps.size();
+            if (range == 1) bi.tileb = bi.tile0 + (int)layout.size();
+            std::vector<size_t> idx;
+            for (size_t w = r0; w < r1; ++w) idx.push_back(w);
+            std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) { return tile_cost(a) > tile_cost(c); });
+            std::vector<std::vector<size_t>> per(kTileWarps);
+            std::vector<int64_t> load(kTileWarps, 0);
+            for (size_t w : idx) {
+                int best = 0;
+                for (int k = 1; k < kTileWarps; ++k)
+                    if (load[k] < load[best]) best = k;
+                per[best].push_back(w);
+                load[best] += tile_cost(w);
+            }
+            size_t rows = 0;
+            for (auto& v2 : per) rows = std::max(rows, v2.size());
+            for (size_t k = 0; k < rows; ++k)
+                for (int w = 0; w < kTileWarps; ++w) layout.push_back(k < per[w].size() ? (long)per[w][k] : -1L);
+            while (!layout.empty() && layout.back() < 0 && (int)layout.size() > bi.tileb - bi.tile0) layout.pop_back();
+        }
+        for (long lw : layout) {
+            if (lw < 0) {                          // padding tile: no lanes, no operator
+                Tile t;
+                t.loc0 = bi.loc0; t.mat0 = bi.mat0; t.L = 0; t.nmax = 0; t.big = 0;
+                K.tiles.push_back(t);
+                continue;
+            }
+            const size_t w = (size_t)lw;
             mat = (mat + 3) & ~int64_t(3);   // 32-byte aligned tile start (f64)
             if (mat > INT32_MAX) throw Error(OPF_ERR_INVALID_ARG, "problem too large");
             Tile t;

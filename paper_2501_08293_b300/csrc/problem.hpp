@@ -30,6 +30,7 @@ struct Ctl {
     int32_t abort;                // a wait gave up: every CTA leaves
     int32_t skip_block;           // test hook: this CTA withholds its flag (-1: none)
     int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait, 4 staging
+    int32_t profile_phases;       // persistent kernel: accumulate per-phase time
     int32_t adaptive;             // residual balancing on
     int32_t rho_changes;
     double rb_mu, rb_tau;
@@ -64,6 +65,7 @@ struct View {
     const T* P;
     const double* cost;
     double* partials;
+    unsigned long long* phase;        // per CTA: interior, wait, boundary, release+check (ns)
     Ctl* ctl;
     int32_t ng, nl, nblocks;
 };
@@ -121,6 +123,7 @@ struct opf_problem {
     int32_t* flags = nullptr;
     double* cost = nullptr;
     double* partials = nullptr;
+    unsigned long long* phase = nullptr;
     opf::Ctl* ctl = nullptr;
     opf::Ctl* ctl_host = nullptr;       // pinned mirror
     int cur_prec = 0;                   // precision holding the current state
@@ -128,5 +131,6 @@ struct opf_problem {
     unsigned long long timeout_ns = 2000000000ull;   // bounded waits (persistent engine)
     int skip_block = -1;                              // test hook
     int force_variant = 0;                            // persistent kernel: 0 auto, 1 global, 2 shared
+    int profile_phases = 0;
     std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision, K)
 };

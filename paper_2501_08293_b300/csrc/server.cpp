@@ -277,12 +277,13 @@ int32_t opf_server_create(const opf_server_config* cfg, opf_server** out) {
             throw opf::Error(OPF_ERR_INVALID_ARG, "round_iters must be a multiple of params.check_every");
         opf_server* S = new opf_server();
         S->cfg = *cfg;
-        if (S->cfg.max_chunks <= 0) {
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            S->cfg.max_chunks = std::max(1, sms * 4);
+        int32_t cap = 0;
+        const int32_t st = opf_batch_capacity(cfg->params.precision, &cap);
+        if (st != OPF_OK) {
+            delete S;
+            throw opf::Error(st, "server: device capacity query failed");
         }
+        if (S->cfg.max_chunks <= 0 || S->cfg.max_chunks > cap) S->cfg.max_chunks = cap;
         cudaGetDevice(&S->device);
         S->batch.device = S->device;
         cudaError_t e = cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking);

@@ -46,7 +46,7 @@ namespace opf {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                   \
     } while (0)
 
-constexpr int kXWarps = 8;          // warps per CTA of x_kernel / persistent_kernel
+constexpr int kXWarps = kTileWarps;  // warps per CTA of x_kernel / persistent kernels
 constexpr int kZThreads = 256;
 constexpr int kFinThreads = 256;
 constexpr int kMaxBigN = 256;
@@ -557,10 +557,26 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     auto zphase = [&](int h0, int h1, const T* xr, const T* lr) {
         for (int h = h0 + threadIdx.x; h < h1; h += blockDim.x) {
             T sum = 0;
-            for (int q = hp[h]; q < hp[h + 1]; ++q) {
-                const int c = hc[q];
-                if (c >= 0) sum += copy_term(xs[c], ls[c], inv_rho);
-                else sum += copy_term(__ldcg(xr + ~c), __ldcg(lr + ~c), inv_rho);
+            const int q0 = hp[h], q1 = hp[h + 1];
+            if (q1 - q0 <= 8) {
+                // issue every copy's loads first, then add in CSR order
+                T xv[8], lv[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (q0 + k < q1) {
+                        const int c = hc[q0 + k];
+                        if (c >= 0) { xv[k] = xs[c]; lv[k] = ls[c]; }
+                        else { xv[k] = __ldcg(xr + ~c); lv[k] = __ldcg(lr + ~c); }
+                    }
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (q0 + k < q1) sum += copy_term(xv[k], lv[k], inv_rho);
+            } else {
+                for (int q = q0; q < q1; ++q) {
+                    const int c = hc[q];
+                    if (c >= 0) sum += copy_term(xs[c], ls[c], inv_rho);
+                    else sum += copy_term(__ldcg(xr + ~c), __ldcg(lr + ~c), inv_rho);
+                }
             }
             zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
         }
@@ -635,6 +651,15 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         }
     };
     const int ntl = bi.tile1 - bi.tile0, ntb = bi.tileb - bi.tile0;
+    const bool prof = ctl->profile_phases != 0 && threadIdx.x == 0;
+    unsigned long long ph[4] = {0, 0, 0, 0}, tp = prof ? now_ns() : 0;
+    auto mark = [&](int k) {
+        if (prof) {
+            const unsigned long long tn = now_ns();
+            ph[k] += tn - tp;
+            tp = tn;
+        }
+    };
     while (!done) {
         const T* xr = (t & 1) ? v.xl2 : v.xl;
         const T* lr = (t & 1) ? v.lam2 : v.lam;
@@ -647,12 +672,15 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         zphase(0, hb, xr, lr);
         __syncthreads();
         xphase(0, ntb, xw, lw, check, acc);
+        mark(0);
         // boundary part, once every neighbour has published iteration t
         if (t > 0 && !wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+        mark(1);
         zphase(hb, nh, xr, lr);
         __syncthreads();
         xphase(ntb, ntl, xw, lw, check, acc);
         __syncthreads();
+        mark(2);
         ++t;
         if (threadIdx.x == 0 && !withhold) {
             __threadfence();
@@ -700,7 +728,10 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
             if (s_stop) done = true;
         }
         if (it0 + t >= maxit) done = true;
+        mark(3);
     }
+    if (prof)
+        for (int k = 0; k < 4; ++k) v.phase[(size_t)b * 4 + k] = ph[k];
     // epilogue: owners publish the last global update; once every neighbour
     // has finished, the chunk's iterate goes back to the primary buffers
     for (int h = threadIdx.x; h < nh; h += blockDim.x)
@@ -728,7 +759,7 @@ struct CtaMap {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32) batch_smem_kernel(const View<T>* views, const CtaMap* map, SmemPlan sp) {
+__global__ void __launch_bounds__(kXWarps * 32, 3) batch_smem_kernel(const View<T>* views, const CtaMap* map, SmemPlan sp) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ View<T> sv;
     const CtaMap m = map[blockIdx.x];
@@ -738,7 +769,7 @@ __global__ void __launch_bounds__(kXWarps * 32) batch_smem_kernel(const View<T>*
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32) batch_global_kernel(const View<T>* views, const CtaMap* map) {
+__global__ void __launch_bounds__(kXWarps * 32, 4) batch_global_kernel(const View<T>* views, const CtaMap* map) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ View<T> sv;
     const CtaMap m = map[blockIdx.x];
@@ -840,7 +871,7 @@ struct Arena {
 
 struct Layout {
     size_t lo, hi, invk, cik, zg, lo32, hi32, invk32, cik32, zg32;
-    size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, ctl;
+    size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, phase, ctl;
     size_t xl, lam, xl2, lam2, bbar, xl0, xl32, lam32, xl2_32, lam2_32, bbar32, xl0_32, P64, P32;
     size_t total;
 };
@@ -862,6 +893,7 @@ Layout layout_of(const opf_problem* p) {
     L.flags = a.take<int32_t>(k.nblocks);
     L.cost = a.take<double>(k.ng);
     L.partials = a.take<double>((size_t)k.nblocks * 8); L.ctl = a.take<Ctl>(1);
+    L.phase = a.take<unsigned long long>((size_t)k.nblocks * 4);
     L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.xl2 = a.take<double>(k.nl); L.lam2 = a.take<double>(k.nl);
     L.bbar = a.take<double>(k.nl); L.xl0 = a.take<double>(k.nl);
     L.xl32 = a.take<float>(k.nl); L.lam32 = a.take<float>(k.nl); L.xl2_32 = a.take<float>(k.nl); L.lam2_32 = a.take<float>(k.nl);
@@ -881,7 +913,7 @@ View<T> view_of(const opf_problem* p, const DevPrec& d) {
     v.bbar = (const T*)d.bbar; v.xl0 = (const T*)d.xl0; v.gidx = p->gidx; v.meta = p->meta;
     v.tiles = p->tiles; v.blocks = p->blocks; v.halo_gid = p->halo_gid; v.halo_own = p->halo_own;
     v.nbrs = p->nbrs; v.hcp = p->hcp; v.hci = p->hci; v.flags = p->flags;
-    v.P = (const T*)d.P; v.cost = p->cost; v.partials = p->partials; v.ctl = p->ctl;
+    v.P = (const T*)d.P; v.cost = p->cost; v.partials = p->partials; v.phase = p->phase; v.ctl = p->ctl;
     v.ng = p->pk.ng; v.nl = p->pk.nl; v.nblocks = p->pk.nblocks;
     return v;
 }
@@ -1176,6 +1208,7 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     p->nbrs = (int32_t*)(a + L.nbrs); p->flags = (int32_t*)(a + L.flags);
     p->hcp = (int32_t*)(a + L.hcp); p->hci = (int32_t*)(a + L.hci);
     p->cost = (double*)(a + L.cost); p->partials = (double*)(a + L.partials);
+    p->phase = (unsigned long long*)(a + L.phase);
     p->ctl = (Ctl*)(a + L.ctl);
     if (!p->ctl_host) OPF_CUDA(cudaMallocHost((void**)&p->ctl_host, sizeof(Ctl)));
     std::memset(p->ctl_host, 0, sizeof(Ctl));
@@ -1244,6 +1277,7 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
     c.arrive = 0; c.decided = 0; c.abort = 0; c.timeout_where = 0;
     c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
     c.adaptive = prm.adaptive_rho; c.rb_mu = prm.rb_mu; c.rb_tau = prm.rb_tau; c.rho_changes = 0;
+    c.profile_phases = p->profile_phases;
     *p->ctl_host = c;
     OPF_CUDA(cudaMemcpyAsync(p->ctl, p->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     if (prm.max_iter > 0) {
@@ -1513,6 +1547,20 @@ void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStrea
         for (size_t i = 0; i < B->probs.size(); ++i) infos[i].seconds = sec;
 }
 
+// Co-resident CTAs a batch launch can use on the current device (the
+// global-memory kernel with its smallest shared-memory footprint).
+int device_batch_capacity(int precision) {
+    int dev = 0, sms = 0, per_sm = 0;
+    OPF_CUDA(cudaGetDevice(&dev));
+    OPF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = 4096;
+    if (precision == OPF_FP64)
+        OPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_global_kernel<double>, kXWarps * 32, smem));
+    else
+        OPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_global_kernel<float>, kXWarps * 32, smem));
+    return per_sm * sms;
+}
+
 void device_batch_free(opf_batch* B) {
     DeviceGuard g(B->device);
     if (B->done) cudaEventDestroy(B->done);
@@ -1553,6 +1601,44 @@ void device_warm_transfer(opf_problem* dst, const opf_problem* src, const std::v
     dst->cold = false;
     Ctl& m = *dst->ctl_host;
     m.iter = 0; m.first_rel = -1; m.checks = 0;
+}
+
+// Per-iteration time of each phase of the shared-memory persistent kernel,
+// mean and max over CTAs: a solve of `iters` iterations from the initial
+// point with the phase counters on.
+void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters, cudaStream_t s, double* out) {
+    DeviceGuard g(p->device);
+    opf_params q = prm;
+    q.warm_start = 0;
+    q.criterion = OPF_CRIT_NEVER;
+    q.max_iter = iters;
+    q.engine = OPF_ENGINE_PERSISTENT;
+    const int saved = p->force_variant;
+    p->force_variant = 2;
+    p->profile_phases = 1;
+    try {
+        device_solve(p, q, s, nullptr);
+    } catch (...) {
+        p->force_variant = saved;
+        p->profile_phases = 0;
+        throw;
+    }
+    p->force_variant = saved;
+    p->profile_phases = 0;
+    const int nb = p->pk.nblocks;
+    std::vector<unsigned long long> h((size_t)nb * 4);
+    OPF_CUDA(cudaMemcpyAsync(h.data(), p->phase, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    OPF_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < 4; ++k) {
+        double sum = 0, mx = 0;
+        for (int b = 0; b < nb; ++b) {
+            const double us = 1e-3 * (double)h[(size_t)b * 4 + k] / iters;
+            sum += us;
+            mx = std::max(mx, us);
+        }
+        out[k] = sum / nb;
+        out[4 + k] = mx;
+    }
 }
 
 void device_free(opf_problem* p) {

@@ -95,11 +95,13 @@ EXPORTS = {
     "opf_profile_kernels": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
     "opf_debug_config": (C.c_int32, [_P, C.c_int64, C.c_int32, C.c_int32]),
     "opf_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
+    "opf_profile_persistent": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
     "opf_residuals_noalloc": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "opf_destroy": (None, [_P]),
     "opf_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "opf_batch_solve": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, C.POINTER(Info)]),
     "opf_batch_destroy": (None, [_P]),
+    "opf_batch_capacity": (C.c_int32, [C.c_int32, _I]),
     "opf_server_config_default": (None, [C.POINTER(ServerConfig)]),
     "opf_server_create": (C.c_int32, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
     "opf_server_submit": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32,
@@ -236,6 +238,15 @@ class Problem:
                "opf_profile_kernels")
         return dict(z=us[0], x=us[1], x_partials=us[2], finalize=us[3])
 
+    def profile_persistent(self, params: Params | None = None, iters: int = 2000, stream=None) -> dict:
+        """Per-iteration microseconds of each persistent-kernel phase (mean, max over CTAs)."""
+        p = params if params is not None else default_params()
+        out = np.zeros(8)
+        _check(lib.opf_profile_persistent(self._h, C.byref(p), int(iters), _stream_handle(stream), _dp(out)),
+               "opf_profile_persistent")
+        names = ("interior", "wait", "boundary", "release_check")
+        return {"mean": dict(zip(names, out[:4])), "max": dict(zip(names, out[4:]))}
+
     def persistent_ok(self, params: Params) -> bool:
         e = C.c_int32()
         _check(lib.opf_engine_for(self._h, params.precision, C.byref(e)), "opf_engine_for")
@@ -293,6 +304,13 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def batch_capacity(precision: int = FP32) -> int:
+    """Co-resident chunks (CTAs) a batch launch can hold on the current device."""
+    n = C.c_int32()
+    _check(lib.opf_batch_capacity(int(precision), C.byref(n)), "opf_batch_capacity")
+    return n.value
 
 
 class Batch:

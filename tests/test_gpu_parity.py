@@ -279,3 +279,29 @@ def test_residual_balancing_matches_oracle(opf):
         xg, xl, lam = p.state()
         assert rel(xg, s.x) <= TOL and rel(xl, s.z) <= TOL and rel(lam, s.lam) <= TOL
         p.close()
+
+
+def test_persistent_phase_profile(opf):
+    """opf_profile_persistent: per-phase times are positive, the phases add
+    up to about the event-timed iteration, and the iterate it leaves is the
+    ordinary 300-iteration iterate (profiling does not change the arithmetic)."""
+    import torch
+    f = F.feeder_123(1)
+    p = opf.Problem.from_feeder(f)
+    prm = opf.default_params(precision=1, rho=10.0, check_every=50)
+    prof = p.profile_persistent(prm, iters=300)
+    a = p.state()
+    assert all(v >= 0 for v in prof["mean"].values()) and prof["mean"]["interior"] > 0
+    q = opf.Problem.from_feeder(f)
+    q.solve(opf.default_params(precision=1, rho=10.0, check_every=50, criterion=opf.CRIT_NEVER, max_iter=300,
+                               engine=opf.ENGINE_PERSISTENT))
+    for x, y in zip(a, q.state()):
+        assert np.array_equal(x, y)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    q.solve(opf.default_params(precision=1, rho=10.0, check_every=50, criterion=opf.CRIT_NEVER, max_iter=300,
+                               engine=opf.ENGINE_PERSISTENT))
+    e1.record(); e1.synchronize()
+    per_iter = e0.elapsed_time(e1) * 1e3 / 300
+    assert 0.3 * per_iter <= sum(prof["mean"].values()) <= 1.5 * per_iter
+    p.close(); q.close()
