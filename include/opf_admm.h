@@ -330,15 +330,28 @@ int32_t opf_get_operator(const opf_problem* p, int32_t s, double* P, double* bba
 void opf_destroy(opf_problem* p);
 
 /* ------------------------------------------------------------------ batch
- * Many feeders solved together in one cooperative launch (the batch
- * dimension of the sweep).  Each instance keeps its own chunks, parameters,
- * iteration counter, residual checks and stopping decision: its iterates do
- * not depend on the other instances in the batch.  All problems must be
- * uploaded on the current device, and the sum of their chunks must fit
- * co-resident (create them with opf_problem_create_ex and a chunk count
- * sized to the batch), else OPF_ERR_INVALID_ARG.  The batch borrows the
- * problems (they must outlive it) and owns a small device and pinned-host
- * buffer for the launch descriptors.                                        */
+ * Many feeders solved together (the batch dimension of the sweep).  Each
+ * instance keeps its own chunks, parameters, iteration counter, residual
+ * checks and stopping decision: its iterates do not depend on the other
+ * instances in the batch, and are bit-identical to a solve of that problem
+ * alone.  params[0].engine picks the engine for the whole batch:
+ *   OPF_ENGINE_PERSISTENT  one cooperative launch over every instance's
+ *                          chunks; the sum of the chunks must fit
+ *                          co-resident (opf_batch_capacity; create the
+ *                          problems with opf_problem_create_ex and a chunk
+ *                          count sized to the batch), else
+ *                          OPF_ERR_INVALID_ARG;
+ *   OPF_ENGINE_GRAPH       (HOSTLOOP maps here) a CUDA graph whose while
+ *                          node runs one global-update launch and one
+ *                          local-update launch per iteration over all
+ *                          instances, and the per-instance checks every
+ *                          check_every iterations, until every instance has
+ *                          stopped; any number of chunks; every entry must
+ *                          have the same check_every;
+ *   OPF_ENGINE_AUTO        persistent when the chunks fit, else graph.
+ * All problems must be uploaded on the current device.  The batch borrows
+ * the problems (they must outlive it) and owns a small device and
+ * pinned-host buffer for the launch descriptors, plus the cached graph.    */
 typedef struct opf_batch opf_batch;
 int32_t opf_batch_create(opf_problem* const* problems, int32_t n, opf_batch** out);
 /* params: n_params == 1 (the same parameters for every instance) or n

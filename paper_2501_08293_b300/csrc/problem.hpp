@@ -92,6 +92,11 @@ struct opf_batch {
     int device = -1;
     cudaEvent_t done = nullptr;       // end of the last launched batch
     int n_launched = 0;
+    // batched graph engine: cached while-node graph and what it was built for
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_buf = nullptr;
+    int g_n = 0, g_nz = 0, g_nx = 0, g_K = 0, g_prec = -1;
 };
 
 struct opf_problem {

@@ -108,6 +108,26 @@ __device__ __forceinline__ T tile_gemv(const T* Pt, int L, int lane, int nmax, i
     return y0 + y1;
 }
 
+// tile_gemv with u taken from a shared-memory copy of the warp's u values
+// (ub[lane] = u of that lane): the loads are independent of the
+// accumulation, so they pipeline; same predicates, same accumulation order
+// (even c into y0, odd c into y1), hence bit-identical results.
+template <typename T>
+__device__ __forceinline__ T tile_gemv_smem(const T* Pt, int L, int lane, int nmax, int n, int base, const T* ub, bool act) {
+    T y0 = 0, y1 = 0;
+    const T* ul = ub + base;
+    int c = 0;
+#pragma unroll 4
+    for (; c + 1 < nmax; c += 2) {
+        const T p0 = Pt[c * L + lane], p1 = Pt[(c + 1) * L + lane];
+        const T u0 = ul[c], u1 = ul[c + 1];
+        if (act && c < n) y0 = fma(p0, u0, y0);
+        if (act && c + 1 < n) y1 = fma(p1, u1, y1);
+    }
+    if (c < nmax && act && c < n) y0 = fma(Pt[c * L + lane], ul[c], y0);
+    return y0 + y1;
+}
+
 // Eq. (global_sparse) for global g from the copies in (xr, lr).
 template <typename T, bool CG>
 __device__ __forceinline__ T global_value(const View<T>& v, int g, const T* xr, const T* lr, T inv_rho) {
@@ -266,8 +286,9 @@ __global__ void __launch_bounds__(kZThreads) z_kernel(View<T> v, int q) {
     v.zg[i] = global_value<T, false>(v, i, v.xl, v.lam, (T)ctl->inv_rho);
 }
 
+// Local + dual update of chunk b for iteration offset q of a graph body.
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32) x_kernel(View<T> v, int q) {
+__device__ __forceinline__ void x_chunk(const View<T>& v, const int b, const int q) {
     const Ctl* ctl = v.ctl;
     const int iter = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
     if (iter + q >= maxit) return;
@@ -276,7 +297,7 @@ __global__ void __launch_bounds__(kXWarps * 32) x_kernel(View<T> v, int q) {
     __shared__ T us[kXWarps][kMaxBigN];
     __shared__ double red[kXWarps][5];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const BlockInfo bi = v.blocks[blockIdx.x];
+    const BlockInfo bi = v.blocks[b];
     double acc[5] = {0, 0, 0, 0, 0};
     const T* zg = v.zg;
     const int32_t* gidx = v.gidx;
@@ -286,11 +307,18 @@ __global__ void __launch_bounds__(kXWarps * 32) x_kernel(View<T> v, int q) {
     for (int t = bi.tileb + warp; t < bi.tile1; t += kXWarps)
         tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
     if (!want) return;
-    cta_partials(acc, red, v.partials + (size_t)blockIdx.x * 8);
+    cta_partials(acc, red, v.partials + (size_t)b * 8);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFinThreads) finalize_kernel(View<T> v, cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(kXWarps * 32) x_kernel(View<T> v, int q) {
+    x_chunk(v, blockIdx.x, q);
+}
+
+// Residual check after a graph body (fixed-order sum, Eq. termination);
+// returns the stop decision to thread 0.
+template <typename T>
+__device__ __forceinline__ int finalize_body(const View<T>& v) {
     Ctl* ctl = v.ctl;
     const int iter = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
     const int ndone = max(0, min(K, maxit - iter));
@@ -298,7 +326,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(View<T> v, cudaGr
     __shared__ double tot[5];
     static_assert(kFinThreads == kXWarps * 32, "finalize reduction layout");
     if (ndone > 0) sum_partials_small(v.partials, v.nblocks, red, tot);
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0) return 0;
     const int it = iter + ndone;
     ctl->iter = it;
     int stop = 0;
@@ -308,7 +336,13 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(View<T> v, cudaGr
         stop = 1;
     }
     ctl->stop = stop;
-    if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+    return stop;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(View<T> v, cudaGraphConditionalHandle h, int use_cond) {
+    const int stop = finalize_body(v);
+    if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
 // ------------------------------------------------------------- persistent
@@ -493,6 +527,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     Tile* stl = reinterpret_cast<Tile*>(sm + sp.tl);    // the chunk's tile descriptors
     __shared__ double red[kXWarps][5];
     __shared__ double tot[5];
+    __shared__ T ubuf[kXWarps][33];                     // a tile's u values, per warp
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_last, s_stop, s_ok;
     __shared__ double s_rho;
@@ -602,7 +637,10 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                     xo = xs[jl];
                     u = u_of(vv, lo, inv_rho);
                 }
-                const T y = tile_gemv(Pt, L, lane, nmax, n, base, u, act);
+                ubuf[warp][lane] = u;
+                __syncwarp();
+                const T y = tile_gemv_smem(Pt, L, lane, nmax, n, base, ubuf[warp], act);
+                __syncwarp();
                 if (act) {
                     const T xn = y + bb[jl];
                     const T ln = dual_of(lo, rho, vv, xn);
@@ -776,6 +814,49 @@ __global__ void __launch_bounds__(kXWarps * 32, 4) batch_global_kernel(const Vie
     if (threadIdx.x == 0) sv = views[m.inst];
     __syncthreads();
     chunk_global(sv, m.chunk, smem_raw);
+}
+
+// Batched graph engine: the graph engine's kernels over many instances.
+// Global update: CTA -> (instance, first global); local update: CTA ->
+// (instance, chunk); one finalize CTA per instance.  Instances that have
+// stopped skip their work; the body repeats while any instance runs.
+struct ZMap {
+    int32_t inst, g0;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) zb_kernel(const View<T>* views, const ZMap* zmap, int q) {
+    const ZMap m = zmap[blockIdx.x];
+    const View<T>& v = views[m.inst];
+    const Ctl* ctl = v.ctl;
+    if (ctl->stop || ctl->iter + q >= ctl->max_iter) return;
+    const int i = m.g0 + threadIdx.x;
+    if (i >= v.ng) return;
+    v.zg[i] = global_value<T, false>(v, i, v.xl, v.lam, (T)ctl->inv_rho);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32) xb_kernel(const View<T>* views, const CtaMap* map, int q) {
+    __shared__ View<T> sv;
+    const CtaMap m = map[blockIdx.x];
+    if (threadIdx.x == 0) sv = views[m.inst];
+    __syncthreads();
+    if (sv.ctl->stop) return;
+    x_chunk(sv, m.chunk, q);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFinThreads) finb_kernel(const View<T>* views, int* running) {
+    const View<T>& v = views[blockIdx.x];
+    const int stopped = v.ctl->stop;
+    __syncthreads();                  // every thread has read stop before thread 0 may write it
+    if (stopped) return;
+    const int stop = finalize_body(v);
+    if (threadIdx.x == 0 && stop) atomicSub(running, 1);
+}
+
+__global__ void batch_cond_kernel(const int* running, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, *running > 0 ? 1u : 0u);
 }
 
 // One CTA per instance: objective c^T x in a fixed order, then the instance's
@@ -1412,23 +1493,65 @@ int32_t status_of(const Ctl& r, const opf_params& prm) {
     return OPF_NOT_CONVERGED;
 }
 
+// The batched graph engine's graph: a while node whose body runs K
+// iterations of every instance (global then local update, one launch each
+// over all instances), the per-instance checks, and sets the condition to
+// "some instance still runs".
+template <typename T>
+GraphEntry build_batch_graph(const View<T>* dviews, const CtaMap* dmap, const ZMap* dzmap, int* drun, int n, int nz,
+                             int nx, int K) {
+    GraphEntry g;
+    OPF_CUDA(cudaGraphCreate(&g.graph, 0));
+    cudaGraphConditionalHandle h;
+    OPF_CUDA(cudaGraphConditionalHandleCreate(&h, g.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = cudaGraphNodeParams{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    OPF_CUDA(cudaGraphAddNode(&cnode, g.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    OPF_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < K; ++q) {
+        zb_kernel<T><<<nz, kZThreads, 0, cs>>>(dviews, dzmap, q);
+        xb_kernel<T><<<nx, kXWarps * 32, 0, cs>>>(dviews, dmap, q);
+    }
+    finb_kernel<T><<<n, kFinThreads, 0, cs>>>(dviews, drun);
+    batch_cond_kernel<<<1, 1, 0, cs>>>(drun, h);
+    const cudaError_t le = cudaGetLastError();
+    cudaGraph_t captured;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (le != cudaSuccess || ee != cudaSuccess)
+        throw Error(OPF_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ee));
+    OPF_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    return g;
+}
+
 // Enqueue a batch solve on `s` without waiting: initial points, control
-// blocks built from each problem's host mirror, flags cleared, one
-// cooperative launch, objectives and a single read-back of all control
-// blocks into pinned memory; B->done is recorded at the end.
+// blocks built from each problem's host mirror, flags cleared, the
+// iterations (one cooperative persistent launch, or the batched graph
+// engine's while-node graph), objectives and a single read-back of all
+// control blocks into pinned memory; B->done is recorded at the end.
 template <typename T>
 void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s) {
     const int n = (int)B->probs.size();
     const size_t ctl_off = 0;
     const size_t views_off = ((size_t)n * sizeof(Ctl) + 255) & ~size_t(255);
-    int nctas = 0;
+    int nctas = 0, nz = 0;
     ChunkMax cm;
     for (opf_problem* p : B->probs) {
         nctas += p->pk.nblocks;
+        nz += (p->pk.ng + kZThreads - 1) / kZThreads;
         cm.add(p->pk);
     }
     const size_t map_off = views_off + (((size_t)n * sizeof(View<T>) + 255) & ~size_t(255));
-    const size_t bytes = map_off + (size_t)nctas * sizeof(CtaMap);
+    const size_t zmap_off = map_off + (((size_t)nctas * sizeof(CtaMap) + 255) & ~size_t(255));
+    const size_t run_off = zmap_off + (((size_t)std::max(1, nz) * sizeof(ZMap) + 255) & ~size_t(255));
+    const size_t bytes = run_off + 256;
     if (bytes > B->dev_bytes) {
         if (B->dev_buf) OPF_CUDA(cudaFreeAsync(B->dev_buf, s));
         B->dev_buf = nullptr;
@@ -1446,9 +1569,18 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     Ctl* hctl = reinterpret_cast<Ctl*>(B->host_buf + ctl_off);
     View<T>* hviews = reinterpret_cast<View<T>*>(B->host_buf + views_off);
     CtaMap* hmap = reinterpret_cast<CtaMap*>(B->host_buf + map_off);
+    ZMap* hzmap = reinterpret_cast<ZMap*>(B->host_buf + zmap_off);
+    int* hrun = reinterpret_cast<int*>(B->host_buf + run_off);
+    SmemPlan sp = smem_plan_of<T>(cm);
+    const size_t gsmem = (size_t)std::max(1, cm.halo) * sizeof(T);
+    int engine = prm[0].engine;
+    if (engine == OPF_ENGINE_HOSTLOOP) engine = OPF_ENGINE_GRAPH;
+    if (engine == OPF_ENGINE_AUTO)
+        engine = (coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas) ||
+                  coop_fits(batch_global_kernel<T>, gsmem, nctas)) ? OPF_ENGINE_PERSISTENT : OPF_ENGINE_GRAPH;
     const int prec = sizeof(T) == 8 ? OPF_FP64 : OPF_FP32;
-    int c = 0;
-    bool any_work = false;
+    int c = 0, cz = 0, running = 0;
+    bool same_K = true;
     for (int i = 0; i < n; ++i) {
         opf_problem* p = B->probs[i];
         const opf_params& pr = prm[nprm == 1 ? 0 : i];
@@ -1462,22 +1594,28 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
             sync_state_to(p, prec, s);
         }
         hctl[i] = solve_ctl(p, pr, cur);
+        if (pr.max_iter > 0) ++running;
+        else if (engine == OPF_ENGINE_GRAPH) hctl[i].stop = 1;   // nothing to do: skipped by the graph body
         hviews[i] = view_of<T>(p, prec_of<T>(p));
         for (int b = 0; b < p->pk.nblocks; ++b) hmap[c++] = CtaMap{i, b};
-        any_work |= pr.max_iter > 0;
+        for (int g0 = 0; g0 < p->pk.ng; g0 += kZThreads) hzmap[cz++] = ZMap{i, g0};
+        same_K &= pr.check_every == prm[0].check_every;
     }
+    *hrun = running;
     for (int i = 0; i < n; ++i)
         OPF_CUDA(cudaMemcpyAsync(B->probs[i]->ctl, hctl + i, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     char* d = static_cast<char*>(B->dev_buf);
     OPF_CUDA(cudaMemcpyAsync(d + views_off, B->host_buf + views_off, bytes - views_off, cudaMemcpyHostToDevice, s));
     const View<T>* dviews = reinterpret_cast<const View<T>*>(d + views_off);
     const CtaMap* dmap = reinterpret_cast<const CtaMap*>(d + map_off);
+    const ZMap* dzmap = reinterpret_cast<const ZMap*>(d + zmap_off);
+    int* drun = reinterpret_cast<int*>(d + run_off);
     Ctl* dctl = reinterpret_cast<Ctl*>(d + ctl_off);
     batch_clear_flags<T><<<std::min(n, 1024), 256, 0, s>>>(dviews, n);
     OPF_CUDA(cudaGetLastError());
-    SmemPlan sp = smem_plan_of<T>(cm);
-    const size_t gsmem = (size_t)std::max(1, cm.halo) * sizeof(T);
-    if (any_work) {
+    if (engine == OPF_ENGINE_GRAPH && !same_K)
+        throw Error(OPF_ERR_INVALID_ARG, "batch graph engine: every instance needs the same check_every");
+    if (running > 0 && engine == OPF_ENGINE_PERSISTENT) {
         if (coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas)) {
             void* args[] = {&dviews, &dmap, &sp};
             OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_smem_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
@@ -1488,8 +1626,23 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
                                                  args, gsmem, s));
         } else {
             throw Error(OPF_ERR_INVALID_ARG, "batch: " + std::to_string(nctas) +
-                                                 " chunks do not fit co-resident; create the problems with fewer chunks");
+                                                 " chunks do not fit co-resident; create the problems with fewer"
+                                                 " chunks or use the graph engine");
         }
+    } else if (running > 0) {
+        const int K = prm[0].check_every;
+        if (!B->gexec || B->g_buf != B->dev_buf || B->g_n != n || B->g_nz != nz || B->g_nx != nctas || B->g_K != K ||
+            B->g_prec != prec) {
+            if (B->gexec) cudaGraphExecDestroy(B->gexec);
+            if (B->graph) cudaGraphDestroy(B->graph);
+            B->gexec = nullptr;
+            B->graph = nullptr;
+            GraphEntry ge = build_batch_graph<T>(dviews, dmap, dzmap, drun, n, nz, nctas, K);
+            B->graph = ge.graph;
+            B->gexec = ge.exec;
+            B->g_buf = B->dev_buf; B->g_n = n; B->g_nz = nz; B->g_nx = nctas; B->g_K = K; B->g_prec = prec;
+        }
+        OPF_CUDA(cudaGraphLaunch(B->gexec, s));
     }
     batch_finish_kernel<T><<<n, 256, 0, s>>>(dviews, dctl);
     OPF_CUDA(cudaGetLastError());
@@ -1563,6 +1716,10 @@ int device_batch_capacity(int precision) {
 
 void device_batch_free(opf_batch* B) {
     DeviceGuard g(B->device);
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->gexec = nullptr;
+    B->graph = nullptr;
     if (B->done) cudaEventDestroy(B->done);
     B->done = nullptr;
     if (B->dev_buf) cudaFree(B->dev_buf);

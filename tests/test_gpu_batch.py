@@ -1,7 +1,9 @@
-"""Batch dimension: several feeders of uneven size in one cooperative launch.
-Each instance keeps its own chunks, parameters, checks and stopping
-decision, so its result in the batch is bit-identical to its result alone
-(same chunk layout) and matches the FP64 oracle."""
+"""Batch dimension: several feeders of uneven size solved together, in one
+cooperative launch (persistent engine) or in one while-node graph over all
+instances (batched graph engine).  Each instance keeps its own chunks,
+parameters, checks and stopping decision, so its result in the batch is
+bit-identical to its result alone (same chunk layout) and matches the FP64
+oracle."""
 import numpy as np
 import pytest
 
@@ -30,17 +32,20 @@ def feeders_mix():
             F.feeder_8500(1, n_bus=1500)]
 
 
+@pytest.mark.parametrize("engine", ["auto", "graph"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_batch_equals_alone(opf, prec):
+def test_batch_equals_alone(opf, prec, engine):
+    eng = opf.ENGINE_AUTO if engine == "auto" else opf.ENGINE_GRAPH
     fs = feeders_mix()
     chunks = [1, 4, 1, 3, 2, 8]
     rhos = [100.0, 10.0, 10.0, 1000.0, 100.0, 10.0]
-    params = [opf.default_params(rho=r, precision=prec, max_iter=3000 + 500 * i, check_every=50)
+    params = [opf.default_params(rho=r, precision=prec, max_iter=3000 + 500 * i, check_every=50, engine=eng)
               for i, r in enumerate(rhos)]
     alone = []
     for f, c, prm in zip(fs, chunks, params):
         p = opf.Problem.from_feeder(f, chunks=c)
-        info = p.solve(prm)                       # single-instance persistent engine
+        info = p.solve(opf.default_params(rho=prm.rho, precision=prec, max_iter=prm.max_iter,
+                                          check_every=50))   # alone, default engine
         alone.append((info, p.state()))
         p.close()
     probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, chunks)]
@@ -55,7 +60,7 @@ def test_batch_equals_alone(opf, prec):
         assert info.pres == ia.pres and info.dres == ia.dres
     # a second batch solve, warm-started, continues every instance
     more = [opf.default_params(rho=r, precision=prec, max_iter=100, check_every=50, warm_start=1,
-                               criterion=opf.CRIT_NEVER) for r in rhos]
+                               criterion=opf.CRIT_NEVER, engine=eng) for r in rhos]
     infos2 = b.solve(more)
     for i in range(len(fs)):
         assert infos2[i].iters == infos[i].iters + 100
@@ -79,3 +84,31 @@ def test_batch_fp64_matches_oracle(opf):
         assert rel(xg, s.x) <= 1e-9 and rel(xl, s.z) <= 1e-9 and rel(lam, s.lam) <= 1e-9
         assert abs(info.pres - r.pres) <= 1e-9 * r.pres
     b.close()
+
+
+def test_batch_graph_engine_many_chunks(opf):
+    """More chunks than fit co-resident: the persistent engine refuses, the
+    graph engine runs, and each instance equals its graph-engine solve alone."""
+    cap = opf.batch_capacity(opf.FP32)
+    fs = [F.feeder_8500(s, n_bus=1500) for s in (1, 2, 3)]
+    chunks = cap // 2 + 1
+    prm = opf.default_params(rho=10.0, precision=opf.FP32, max_iter=600, check_every=50, engine=opf.ENGINE_GRAPH)
+    alone = []
+    for f in fs:
+        p = opf.Problem.from_feeder(f, chunks=chunks)
+        alone.append((p.solve(prm), p.state()))
+        p.close()
+    probs = [opf.Problem.from_feeder(f, chunks=chunks) for f in fs]
+    b = opf.Batch(probs)
+    with pytest.raises(RuntimeError):
+        b.solve(opf.default_params(rho=10.0, precision=opf.FP32, max_iter=600, check_every=50,
+                                   engine=opf.ENGINE_PERSISTENT))
+    infos = b.solve(prm)
+    for i, p in enumerate(probs):
+        ia, sa = alone[i]
+        assert infos[i].iters == ia.iters and infos[i].status == ia.status
+        for x, y in zip(p.state(), sa):
+            assert np.array_equal(x, y), (i, rel(x, y))
+    b.close()
+    for p in probs:
+        p.close()
