@@ -276,8 +276,10 @@ int32_t opf_profile_kernels(opf_problem* p, const opf_params* params, int32_t re
 
 /* Per-iteration time of each phase of the shared-memory persistent kernel,
  * in microseconds, measured on the device (globaltimer, thread 0 of each
- * CTA): out[0..3] = mean over CTAs of {interior halo + tile updates, wait
- * for the neighbours, boundary halo + tile updates, flag release + residual
+ * CTA): out[0..3] = mean over CTAs of {global update of the interior halo
+ * entries, global update of the boundary entries including the wait for
+ * the neighbours' terms and the CTA barrier, local update of the boundary
+ * tiles, local update of the interior tiles + CTA barrier + residual
  * check}; out[4..7] = the maximum over CTAs.  Runs `iters` iterations from
  * the initial point (the problem is left at that iterate); needs the
  * shared-memory kernel to fit (else OPF_ERR_INVALID_ARG).                  */

@@ -105,7 +105,7 @@ void validate(const Packed& K) {
         for (int t = bi.tile0; t < bi.tile1; ++t) {
             const Tile& tl = K.tiles[t];
             const int lanes = tl.L;
-            const int64_t span = tl.big ? (int64_t)tl.L * tl.L : (int64_t)tl.nmax * tl.L;
+            const int64_t span = tl.big ? (int64_t)tl.L * tl.L : (int64_t)((tl.nmax + 3) / 4) * 4 * tl.L;
             if (tl.loc0 < bi.loc0 || tl.loc0 + lanes > bi.loc1) fail("tile locals");
             if (tl.mat0 < bi.mat0 || tl.mat0 + span > bi.mat1 || (tl.mat0 & 3)) fail("tile operators");
             if (!tl.big && lanes == 0 && tl.nmax != 0) fail("padding tile shape");
@@ -316,7 +316,10 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
                 int nmax = 0;
                 for (int s : warps[w]) nmax = std::max(nmax, M.comps[s].n());
                 t.L = (int16_t)L; t.nmax = (int16_t)nmax; t.big = 0;
-                K.P.resize((size_t)mat + (size_t)nmax * L, 0.0);
+                // columns in groups of four, lane-interleaved: column c of
+                // lane r at ((c / 4) * L + r) * 4 + c % 4, zero beyond n
+                const int nq = (nmax + 3) / 4;
+                K.P.resize((size_t)mat + (size_t)nq * 4 * L, 0.0);
                 int base = 0;
                 for (int s : warps[w]) {
                     const int n = M.comps[s].n();
@@ -326,11 +329,11 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
                         K.canon_of_dev[loc + lane] = (int32_t)(cptr[s] + r);
                         K.meta[loc + lane] = (n << 16) | (base << 24);
                         for (int c = 0; c < n; ++c)
-                            K.P[(size_t)mat + (size_t)c * L + lane] = ops[s].P[(size_t)c * n + r];
+                            K.P[(size_t)mat + ((size_t)(c / 4) * L + lane) * 4 + c % 4] = ops[s].P[(size_t)c * n + r];
                     }
                     base += n;
                 }
-                mat += (int64_t)nmax * L;
+                mat += (int64_t)nq * 4 * L;
                 loc += L;
             }
             K.tiles.push_back(t);

@@ -66,6 +66,7 @@ struct View {
     const double* cost;
     double* partials;
     unsigned long long* phase;        // per CTA: interior, wait, boundary, release+check (ns)
+    unsigned long long* mbox;         // tagged boundary values, 2 slots x nl x (1 f32 | 2 f64) words
     Ctl* ctl;
     int32_t ng, nl, nblocks;
 };
@@ -129,6 +130,7 @@ struct opf_problem {
     double* cost = nullptr;
     double* partials = nullptr;
     unsigned long long* phase = nullptr;
+    unsigned long long* mbox = nullptr;
     opf::Ctl* ctl = nullptr;
     opf::Ctl* ctl_host = nullptr;       // pinned mirror
     int cur_prec = 0;                   // precision holding the current state

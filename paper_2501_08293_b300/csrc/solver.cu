@@ -28,6 +28,14 @@
 //               ticket counter elects the last CTA to finalize the residuals.
 //               Every wait is bounded in time: on expiry the CTA records
 //               where, sets OPF_ERR_TIMEOUT and all CTAs leave.
+//               The shared-memory variant exchanges boundary values without
+//               flags or fences: a CTA publishes, for each of its copies that
+//               other chunks read, the term x_j - lambda_j / rho together
+//               with the iteration number in one 64-bit word (two for FP64:
+//               each half of the double with the tag) into a two-slot
+//               mailbox; a reader polls exactly the words it needs until the
+//               tags match.  A single-copy-atomic word carries its own
+//               validity, so no release / acquire ordering is involved.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -60,10 +68,80 @@ __device__ __forceinline__ int ld_acquire(const int32_t* p) {
 __device__ __forceinline__ void st_release(int32_t* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Tagged mailbox of boundary terms: slot s, device local j.  A word holds
+// the value bits in its low half and the tag (iteration + 1, never 0 after
+// the launch clears the mailbox) in its high half; an FP64 value takes two
+// words, one per 32-bit half, each with the tag.
+template <typename T>
+struct Mail;
+template <>
+struct Mail<float> {
+    static constexpr int kWords = 1;
+    static __device__ __forceinline__ void put(unsigned long long* mb, int nl, int slot, int j, float w, unsigned tag) {
+        st_relaxed64(mb + (size_t)slot * nl + j, ((unsigned long long)tag << 32) | __float_as_uint(w));
+    }
+    static __device__ __forceinline__ bool get(const unsigned long long* mb, int nl, int slot, int j, unsigned tag,
+                                               float& w) {
+        const unsigned long long v = ld_relaxed64(mb + (size_t)slot * nl + j);
+        w = __uint_as_float((unsigned)v);
+        return (unsigned)(v >> 32) == tag;
+    }
+};
+template <>
+struct Mail<double> {
+    static constexpr int kWords = 2;
+    static __device__ __forceinline__ void put(unsigned long long* mb, int nl, int slot, int j, double w, unsigned tag) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+        unsigned long long* q = mb + ((size_t)slot * nl + j) * 2;
+        const unsigned long long t = (unsigned long long)tag << 32;
+        st_relaxed64(q, t | (b & 0xFFFFFFFFull));
+        st_relaxed64(q + 1, t | (b >> 32));
+    }
+    static __device__ __forceinline__ bool get(const unsigned long long* mb, int nl, int slot, int j, unsigned tag,
+                                               double& w) {
+        const unsigned long long* q = mb + ((size_t)slot * nl + j) * 2;
+        const unsigned long long a = ld_relaxed64(q), c = ld_relaxed64(q + 1);
+        w = __longlong_as_double((long long)(((c & 0xFFFFFFFFull) << 32) | (a & 0xFFFFFFFFull)));
+        return (unsigned)(a >> 32) == tag && (unsigned)(c >> 32) == tag;
+    }
+};
+
 __device__ __forceinline__ unsigned long long now_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Bounded poll of one mailbox entry until its tag matches; false once the
+// deadline passed (the CTA then raises the abort flag and records `where`)
+// or another CTA aborted.
+template <typename T>
+__device__ __forceinline__ bool mail_poll(const unsigned long long* mb, int nl, int slot, int j, unsigned tag, T& w,
+                                          Ctl* ctl, unsigned long long tmo, int where) {
+    unsigned spins = 0;
+    unsigned long long deadline = 0;
+    while (!Mail<T>::get(mb, nl, slot, j, tag, w)) {
+        if ((++spins & 31u) == 0) {
+            if (ld_acquire(&ctl->abort)) return false;
+            const unsigned long long tn = now_ns();
+            if (deadline == 0) {
+                deadline = tn + tmo;
+            } else if (tn > deadline) {
+                if (atomicCAS(&ctl->abort, 0, 1) == 0) { ctl->status = CTL_TIMEOUT; ctl->timeout_where = where; }
+                return false;
+            }
+        }
+    }
+    return true;
 }
 __device__ __forceinline__ double warp_sum(double a) {
 #pragma unroll
@@ -88,43 +166,73 @@ __device__ __forceinline__ T u_of(T v, T l, T inv_rho) { return fma(l, inv_rho, 
 template <typename T>
 __device__ __forceinline__ T dual_of(T l, T rho, T v, T xn) { return fma(rho, v - xn, l); }            // l + rho (Bx - z)
 
-// Small-tile GEMV of one lane: y = sum_c P[c][r] u_c over the lane's
-// component, two interleaved partial sums (even / odd c) for latency.
+// Operator columns 4q .. 4q+3 of one lane (quad layout of pack.cpp: column c
+// of lane r at ((c / 4) * L + r) * 4 + c % 4): one 16-byte load for FP32,
+// two for FP64.
+__device__ __forceinline__ void load_quad(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load_quad(const double* p, double (&o)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+// y0 = fma(a0, b0, y0), y1 = fma(a1, b1, y1): one packed FP32 instruction on
+// sm_100+ (two independent round-to-nearest fmas, so the same bits as two
+// scalar fmas); two fmas for FP64.
+__device__ __forceinline__ void fma_pair(float& y0, float& y1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(y0), "+f"(y1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fma_pair(double& y0, double& y1, double a0, double a1, double b0, double b1) {
+    y0 = fma(a0, b0, y0);
+    y1 = fma(a1, b1, y1);
+}
+
+// Small-tile GEMV of one lane, y = sum_c P[c][r] u_(base + c), with u
+// broadcast by warp shuffles: even columns accumulate into y0, odd ones into
+// y1 (the order of every engine).  Columns past the lane's component are
+// zero in the packed operator, so they add exact zeros and need no test.
+// Inactive lanes (act false) read lane 0's operator and discard y.
 template <typename T>
-__device__ __forceinline__ T tile_gemv(const T* Pt, int L, int lane, int nmax, int n, int base, T u, bool act) {
+__device__ __forceinline__ T tile_gemv(const T* Pt, int L, int lane, int nmax, int base, T u, bool act) {
     T y0 = 0, y1 = 0;
-    int c = 0;
-#pragma unroll 2
-    for (; c + 1 < nmax; c += 2) {
-        const T u0 = __shfl_sync(0xffffffffu, u, (base + c) & 31);
-        const T u1 = __shfl_sync(0xffffffffu, u, (base + c + 1) & 31);
-        if (act && c < n) y0 = fma(Pt[c * L + lane], u0, y0);
-        if (act && c + 1 < n) y1 = fma(Pt[(c + 1) * L + lane], u1, y1);
-    }
-    if (c < nmax) {
-        const T u0 = __shfl_sync(0xffffffffu, u, (base + c) & 31);
-        if (act && c < n) y0 = fma(Pt[c * L + lane], u0, y0);
+    const int r = act ? lane : 0;
+    const int nq = (nmax + 3) >> 2;
+    for (int q = 0; q < nq; ++q) {
+        T p[4];
+        load_quad(Pt + (q * L + r) * 4, p);
+        const int c = base + 4 * q;
+        const T u0 = __shfl_sync(0xffffffffu, u, c & 31), u1 = __shfl_sync(0xffffffffu, u, (c + 1) & 31);
+        const T u2 = __shfl_sync(0xffffffffu, u, (c + 2) & 31), u3 = __shfl_sync(0xffffffffu, u, (c + 3) & 31);
+        fma_pair(y0, y1, p[0], p[1], u0, u1);
+        fma_pair(y0, y1, p[2], p[3], u2, u3);
     }
     return y0 + y1;
 }
 
-// tile_gemv with u taken from a shared-memory copy of the warp's u values
-// (ub[lane] = u of that lane): the loads are independent of the
-// accumulation, so they pipeline; same predicates, same accumulation order
-// (even c into y0, odd c into y1), hence bit-identical results.
+// The same GEMV with u from shared memory: ub is the lane's 16-byte-aligned
+// view of the warp's u values, ub[4q + j] = u_(base + 4q + j) (zero past the
+// tile), so each group of four columns is two vector loads and two packed
+// fmas.  Same accumulation order as tile_gemv, hence the same bits.
+constexpr int kUrow = 68;     // shifted u row: 64 entries + 4 of padding (bank spread)
 template <typename T>
-__device__ __forceinline__ T tile_gemv_smem(const T* Pt, int L, int lane, int nmax, int n, int base, const T* ub, bool act) {
+__device__ __forceinline__ T tile_gemv_sh(const T* Pt, int L, int r, int nq, const T* ub) {
     T y0 = 0, y1 = 0;
-    const T* ul = ub + base;
-    int c = 0;
 #pragma unroll 4
-    for (; c + 1 < nmax; c += 2) {
-        const T p0 = Pt[c * L + lane], p1 = Pt[(c + 1) * L + lane];
-        const T u0 = ul[c], u1 = ul[c + 1];
-        if (act && c < n) y0 = fma(p0, u0, y0);
-        if (act && c + 1 < n) y1 = fma(p1, u1, y1);
+    for (int q = 0; q < nq; ++q) {
+        T p[4], w[4];
+        load_quad(Pt + (q * L + r) * 4, p);
+        load_quad(ub + 4 * q, w);
+        fma_pair(y0, y1, p[0], p[1], w[0], w[1]);
+        fma_pair(y0, y1, p[2], p[3], w[2], w[3]);
     }
-    if (c < nmax && act && c < n) y0 = fma(Pt[c * L + lane], ul[c], y0);
     return y0 + y1;
 }
 
@@ -151,18 +259,17 @@ __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int
         const int L = tl.L, nmax = tl.nmax;
         const bool act = lane < L;
         const int j = tl.loc0 + lane;
-        int n = 0, base = 0;
+        int base = 0;
         T vv = 0, lo = 0, xo = 0, u = 0;
         if (act) {
             const int m = v.meta[j];
-            n = (m >> 16) & 0xFF;
             base = (m >> 24) & 0x1F;
             vv = getv(j, m);
             lo = ldcg(lr + j);
             xo = ldcg(xr + j);
             u = u_of(vv, lo, inv_rho);
         }
-        const T y = tile_gemv(v.P + tl.mat0, L, lane, nmax, n, base, u, act);
+        const T y = tile_gemv(v.P + tl.mat0, L, lane, nmax, base, u, act);
         if (act) {
             const T xn = y + v.bbar[j];
             const T ln = dual_of(lo, rho, vv, xn);
@@ -302,9 +409,12 @@ __device__ __forceinline__ void x_chunk(const View<T>& v, const int b, const int
     const T* zg = v.zg;
     const int32_t* gidx = v.gidx;
     auto getv = [zg, gidx](int j, int) { return zg[gidx[j]]; };
-    for (int t = bi.tile0 + warp; t < bi.tileb; t += kXWarps)
-        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
+    // boundary tiles first, then interior ones: the order of every engine
+    // (the persistent kernel publishes boundary values early), so the
+    // residual partial sums agree bit for bit
     for (int t = bi.tileb + warp; t < bi.tile1; t += kXWarps)
+        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
+    for (int t = bi.tile0 + warp; t < bi.tileb; t += kXWarps)
         tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
     if (!want) return;
     cta_partials(acc, red, v.partials + (size_t)b * 8);
@@ -405,16 +515,13 @@ __device__ __forceinline__ void chunk_global(const View<T>& v, const int b, unsi
         const bool check = ((t + 1) % K == 0) || nrem == 1;
         double acc[5] = {0, 0, 0, 0, 0};
         auto getv = [zs](int, int m) { return zs[m & 0xFFFF]; };
-        for (int q = bi.tile0 + warp; q < bi.tileb; q += kXWarps)
-            tile_update<T>(v, v.tiles[q], lane, rho, inv_rho, xr, lr, xw, lw, check, acc, us[warp], getv);
         for (int q = bi.tileb + warp; q < bi.tile1; q += kXWarps)
+            tile_update<T>(v, v.tiles[q], lane, rho, inv_rho, xr, lr, xw, lw, check, acc, us[warp], getv);
+        for (int q = bi.tile0 + warp; q < bi.tileb; q += kXWarps)
             tile_update<T>(v, v.tiles[q], lane, rho, inv_rho, xr, lr, xw, lw, check, acc, us[warp], getv);
         __syncthreads();
         ++t;
-        if (threadIdx.x == 0 && !withhold) {
-            __threadfence();
-            st_release(v.flags + b, t);
-        }
+        if (threadIdx.x == 0 && !withhold) st_release(v.flags + b, t);   // release: cumulative over the CTA barrier
         if (check) {
             cta_partials(acc, red, v.partials + (size_t)b * 8);
             __syncthreads();
@@ -478,7 +585,7 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
 // ----------------------------------------------- persistent, shared-memory
 // Per-launch shared-memory plan (byte offsets; every region 16-byte aligned).
 struct SmemPlan {
-    int P, xs, ls, bb, mt, zs, hlo, hhi, hik, hck, hp, hc, us, big, tl, total;
+    int P, xs, ls, ws, bb, mt, zs, hlo, hhi, hik, hck, hp, hc, us, big, tl, ush, total;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -525,9 +632,14 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     int* hc = reinterpret_cast<int*>(sm + sp.hc);
     T* usw = reinterpret_cast<T*>(sm + sp.us);          // big-tile staging, sp.big per warp
     Tile* stl = reinterpret_cast<Tile*>(sm + sp.tl);    // the chunk's tile descriptors
+    constexpr bool kF32 = sizeof(T) == 4;
+    T* ws = reinterpret_cast<T*>(sm + sp.ws);           // per local: x_j - lambda_j / rho (FP32)
+    // (FP32) per warp four shifted copies of a tile's u values, row k
+    // holding u_(i + k) at i (zero for i + k >= 32), so that every lane
+    // reads its operands u_(base + c) with 16-byte-aligned vector loads
+    T* ush = reinterpret_cast<T*>(sm + sp.ush);
     __shared__ double red[kXWarps][5];
     __shared__ double tot[5];
-    __shared__ T ubuf[kXWarps][33];                     // a tile's u values, per warp
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_last, s_stop, s_ok;
     __shared__ double s_rho;
@@ -538,11 +650,14 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     T rho = (T)ctl->rho, inv_rho = (T)ctl->inv_rho;
     const unsigned long long tmo = ctl->timeout_ns;
     const bool withhold = (ctl->skip_block == b);
+    const bool adaptive = ctl->adaptive != 0;
     const int nloc = bi.loc1 - bi.loc0, nh = bi.halo1 - bi.halo0, ncp = bi.cp1 - bi.cp0;
 
     // ---- prologue: operators by TMA bulk copies, the rest by plain loads
     const unsigned pbytes = (unsigned)(((size_t)(bi.mat1 - bi.mat0) * sizeof(T) + 15) & ~size_t(15));
     if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    if constexpr (kF32)
+        for (int i = threadIdx.x; i < kXWarps * 4 * kUrow; i += blockDim.x) ush[i] = 0;
     __syncthreads();
     if (threadIdx.x == 0 && pbytes) {
         mbar_expect_tx(&mbar, pbytes);
@@ -555,6 +670,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
         xs[j] = v.xl[bi.loc0 + j];
         ls[j] = v.lam[bi.loc0 + j];
+        if constexpr (kF32) ws[j] = copy_term(xs[j], ls[j], inv_rho);
         bb[j] = v.bbar[bi.loc0 + j];
         mt[j] = v.meta[bi.loc0 + j];
     }
@@ -588,36 +704,53 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
 
     int t = 0, checkno = 0;
     bool done = it0 >= maxit;
-    // global update of halo entries [h0, h1), Eq. (global_sparse), copies in CSR order
-    auto zphase = [&](int h0, int h1, const T* xr, const T* lr) {
-        for (int h = h0 + threadIdx.x; h < h1; h += blockDim.x) {
+    // global update of halo entries [h0, h1), Eq. (global_sparse), copies in
+    // CSR order.  Copies of other chunks: at t == 0 the initial iterate from
+    // the primary buffers, later the neighbour's term of iteration t - 1
+    // from mailbox slot (t - 1) & 1, polled until its tag is t (bounded).
+    const unsigned long long* mb = v.mbox;
+    const int nlg = v.nl;
+    auto zphase = [&](int h0, int h1, int t, bool& ok) {
+        const int slot = (t - 1) & 1;
+        const unsigned tag = (unsigned)t;
+        for (int h = h0 + threadIdx.x; h < h1 && ok; h += blockDim.x) {
             T sum = 0;
             const int q0 = hp[h], q1 = hp[h + 1];
-            if (q1 - q0 <= 8) {
+            for (int qb = q0; qb < q1 && ok; qb += 8) {
                 // issue every copy's loads first, then add in CSR order
-                T xv[8], lv[8];
+                T w[8];
+                unsigned miss = 0;
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (q0 + k < q1) {
-                        const int c = hc[q0 + k];
-                        if (c >= 0) { xv[k] = xs[c]; lv[k] = ls[c]; }
-                        else { xv[k] = __ldcg(xr + ~c); lv[k] = __ldcg(lr + ~c); }
+                for (int k = 0; k < 8; ++k) {
+                    w[k] = 0;
+                    if (qb + k < q1) {
+                        const int c = hc[qb + k];
+                        if (c >= 0) {
+                            if constexpr (kF32) w[k] = ws[c];
+                            else w[k] = copy_term(xs[c], ls[c], inv_rho);
+                        }
+                        else if (t == 0) w[k] = copy_term(__ldcg(v.xl + ~c), __ldcg(v.lam + ~c), inv_rho);
+                        else if (!Mail<T>::get(mb, nlg, slot, ~c, tag, w[k])) miss |= 1u << k;
                     }
+                }
+                if (miss) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (((miss >> k) & 1u) && ok) ok = mail_poll(mb, nlg, slot, ~hc[qb + k], tag, w[k], ctl, tmo, 1);
+                }
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
-                    if (q0 + k < q1) sum += copy_term(xv[k], lv[k], inv_rho);
-            } else {
-                for (int q = q0; q < q1; ++q) {
-                    const int c = hc[q];
-                    if (c >= 0) sum += copy_term(xs[c], ls[c], inv_rho);
-                    else sum += copy_term(__ldcg(xr + ~c), __ldcg(lr + ~c), inv_rho);
-                }
+                    if (qb + k < q1) sum += w[k];
             }
-            zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
+            if (ok) zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
         }
     };
+    // publish the terms of this chunk's exported copies for iteration t
+    auto publish = [&](int jl, T w, int t) {
+        if (!withhold) Mail<T>::put(v.mbox, nlg, t & 1, bi.loc0 + jl, w, (unsigned)(t + 1));
+    };
     // local + dual updates of tiles [q0, q1) (chunk-relative), Eq. (closed_2), Eq. (ADMM-3)
-    auto xphase = [&](int q0, int q1, T* xw, T* lw, bool check, double* acc) {
+    auto xphase = [&](int q0, int q1, int t, bool pub, bool check, double* acc) {
         for (int q = q0 + warp; q < q1; q += kXWarps) {
             const Tile tl = stl[q];
             const int jl0 = tl.loc0 - bi.loc0;
@@ -626,30 +759,36 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                 const int L = tl.L, nmax = tl.nmax;
                 const bool act = lane < L;
                 const int jl = jl0 + lane;
-                int n = 0, base = 0, m = 0;
+                int base = 0, m = 0;
                 T vv = 0, lo = 0, xo = 0, u = 0;
                 if (act) {
                     m = mt[jl];
-                    n = (m >> 16) & 0xFF;
                     base = (m >> 24) & 0x1F;
                     vv = zs[m & 0xFFFF];
                     lo = ls[jl];
                     xo = xs[jl];
                     u = u_of(vv, lo, inv_rho);
                 }
-                ubuf[warp][lane] = u;
-                __syncwarp();
-                const T y = tile_gemv_smem(Pt, L, lane, nmax, n, base, ubuf[warp], act);
-                __syncwarp();
+                T y;
+                if constexpr (kF32) {
+                    T* uw = ush + warp * 4 * kUrow;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (lane >= k) uw[k * kUrow + lane - k] = u;
+                    __syncwarp();
+                    y = tile_gemv_sh(Pt, L, act ? lane : 0, (nmax + 3) >> 2, uw + (base & 3) * kUrow + (base & ~3));
+                    __syncwarp();
+                } else {
+                    y = tile_gemv(Pt, L, lane, nmax, base, u, act);
+                }
                 if (act) {
                     const T xn = y + bb[jl];
                     const T ln = dual_of(lo, rho, vv, xn);
+                    const T wn = copy_term(xn, ln, inv_rho);
                     xs[jl] = xn;
                     ls[jl] = ln;
-                    if (m & (1 << 30)) {
-                        xw[bi.loc0 + jl] = xn;
-                        lw[bi.loc0 + jl] = ln;
-                    }
+                    if constexpr (kF32) ws[jl] = wn;
+                    if (pub && (m & (1 << 30))) publish(jl, wn, t);
                     if (check) {
                         const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
                         acc[0] += pr * pr; acc[1] += dz * dz;
@@ -671,12 +810,11 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                     const T lo = ls[jl], xo = xs[jl];
                     const T xn = y + bb[jl];
                     const T ln = dual_of(lo, rho, vv, xn);
+                    const T wn = copy_term(xn, ln, inv_rho);
                     xs[jl] = xn;
                     ls[jl] = ln;
-                    if (m & (1 << 30)) {
-                        xw[bi.loc0 + jl] = xn;
-                        lw[bi.loc0 + jl] = ln;
-                    }
+                    if constexpr (kF32) ws[jl] = wn;
+                    if (pub && (m & (1 << 30))) publish(jl, wn, t);
                     if (check) {
                         const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
                         acc[0] += pr * pr; acc[1] += dz * dz;
@@ -699,31 +837,26 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         }
     };
     while (!done) {
-        const T* xr = (t & 1) ? v.xl2 : v.xl;
-        const T* lr = (t & 1) ? v.lam2 : v.lam;
-        T* xw = (t & 1) ? v.xl : v.xl2;
-        T* lw = (t & 1) ? v.lam : v.lam2;
         const int nrem = maxit - (it0 + t);
         const bool check = ((t + 1) % K == 0) || nrem == 1;
+        // with residual balancing rho may change at a check: publish after it
+        const bool defer = check && adaptive;
         double acc[5] = {0, 0, 0, 0, 0};
-        // interior part: needs nothing from the neighbours
-        zphase(0, hb, xr, lr);
-        __syncthreads();
-        xphase(0, ntb, xw, lw, check, acc);
+        bool okz = true;
+        // global update: interior halo entries (copies all in this chunk),
+        // then boundary ones (the neighbours' terms of iteration t - 1)
+        zphase(0, hb, t, okz);
         mark(0);
-        // boundary part, once every neighbour has published iteration t
-        if (t > 0 && !wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+        zphase(hb, nh, t, okz);
+        if (!__syncthreads_and(okz)) return;
         mark(1);
-        zphase(hb, nh, xr, lr);
-        __syncthreads();
-        xphase(ntb, ntl, xw, lw, check, acc);
-        __syncthreads();
+        // local update: boundary tiles first so that their terms reach the
+        // neighbours while the interior tiles are computed
+        xphase(ntb, ntl, t, !defer, check, acc);
         mark(2);
+        xphase(0, ntb, t, !defer, check, acc);
+        __syncthreads();
         ++t;
-        if (threadIdx.x == 0 && !withhold) {
-            __threadfence();
-            st_release(v.flags + b, t);
-        }
         if (check) {
             cta_partials(acc, red, v.partials + (size_t)b * 8);
             __syncthreads();
@@ -764,17 +897,34 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
             ++checkno;
             if (!s_ok) return;
             if (s_stop) done = true;
+            if (defer) {    // rho may have changed: terms with the new rho, then publish
+                for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
+                    const T wn = copy_term(xs[j], ls[j], inv_rho);
+                    if constexpr (kF32) ws[j] = wn;
+                    if (mt[j] & (1 << 30)) publish(j, wn, t - 1);
+                }
+                __syncthreads();
+            }
         }
         if (it0 + t >= maxit) done = true;
         mark(3);
     }
     if (prof)
         for (int k = 0; k < 4; ++k) v.phase[(size_t)b * 4 + k] = ph[k];
-    // epilogue: owners publish the last global update; once every neighbour
-    // has finished, the chunk's iterate goes back to the primary buffers
+    // epilogue: owners publish the last global update, the chunk's iterate
+    // goes back to the primary buffers.  Neighbours read those buffers only
+    // at t == 0; after a one-iteration launch, wait until every neighbour
+    // has published iteration 0 (which it does after reading them).
     for (int h = threadIdx.x; h < nh; h += blockDim.x)
         if (v.halo_own[bi.halo0 + h]) v.zg[v.halo_gid[bi.halo0 + h]] = zs[h];
-    if (!wait_neighbours(v, bi, t, tmo, &s_ok)) return;
+    if (t == 1) {
+        bool okz = true;
+        for (int q = threadIdx.x; q < ncp && okz; q += blockDim.x) {
+            T w;
+            if (hc[q] < 0) okz = mail_poll(mb, nlg, 0, ~hc[q], 1u, w, ctl, tmo, 3);
+        }
+        if (!__syncthreads_and(okz)) return;
+    }
     for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
         v.xl[bi.loc0 + j] = xs[j];
         v.lam[bi.loc0 + j] = ls[j];
@@ -782,7 +932,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32) persistent_smem_kernel(View<T> v, SmemPlan sp) {
+__global__ void __launch_bounds__(kXWarps * 32, 2) persistent_smem_kernel(View<T> v, SmemPlan sp) {
     extern __shared__ __align__(128) unsigned char sm[];
     chunk_smem(v, blockIdx.x, sp, sm);
 }
@@ -879,11 +1029,17 @@ __global__ void __launch_bounds__(256) batch_finish_kernel(const View<T>* views,
     }
 }
 
-// Zero every instance's CTA flags (one launch for the whole batch).
+// Zero every instance's CTA flags and, for the shared-memory persistent
+// kernel, its boundary mailbox (one launch for the whole batch).
 template <typename T>
-__global__ void batch_clear_flags(const View<T>* views, int n) {
-    for (int i = blockIdx.x; i < n; i += gridDim.x)
+__global__ void batch_clear_flags(const View<T>* views, int n, int mailbox) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
         for (int b = threadIdx.x; b < views[i].nblocks; b += blockDim.x) views[i].flags[b] = 0;
+        if (mailbox) {
+            const size_t words = (size_t)views[i].nl * 2 * Mail<T>::kWords;
+            for (size_t j = threadIdx.x; j < words; j += blockDim.x) views[i].mbox[j] = 0;
+        }
+    }
 }
 
 // Warm start across a topology change: new local j takes the old iterate and
@@ -952,7 +1108,7 @@ struct Arena {
 
 struct Layout {
     size_t lo, hi, invk, cik, zg, lo32, hi32, invk32, cik32, zg32;
-    size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, phase, ctl;
+    size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, phase, ctl, mbox;
     size_t xl, lam, xl2, lam2, bbar, xl0, xl32, lam32, xl2_32, lam2_32, bbar32, xl0_32, P64, P32;
     size_t total;
 };
@@ -975,6 +1131,7 @@ Layout layout_of(const opf_problem* p) {
     L.cost = a.take<double>(k.ng);
     L.partials = a.take<double>((size_t)k.nblocks * 8); L.ctl = a.take<Ctl>(1);
     L.phase = a.take<unsigned long long>((size_t)k.nblocks * 4);
+    L.mbox = a.take<unsigned long long>((size_t)k.nl * 4);     // 2 slots x 2 words (f64)
     L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.xl2 = a.take<double>(k.nl); L.lam2 = a.take<double>(k.nl);
     L.bbar = a.take<double>(k.nl); L.xl0 = a.take<double>(k.nl);
     L.xl32 = a.take<float>(k.nl); L.lam32 = a.take<float>(k.nl); L.xl2_32 = a.take<float>(k.nl); L.lam2_32 = a.take<float>(k.nl);
@@ -995,6 +1152,7 @@ View<T> view_of(const opf_problem* p, const DevPrec& d) {
     v.tiles = p->tiles; v.blocks = p->blocks; v.halo_gid = p->halo_gid; v.halo_own = p->halo_own;
     v.nbrs = p->nbrs; v.hcp = p->hcp; v.hci = p->hci; v.flags = p->flags;
     v.P = (const T*)d.P; v.cost = p->cost; v.partials = p->partials; v.phase = p->phase; v.ctl = p->ctl;
+    v.mbox = p->mbox;
     v.ng = p->pk.ng; v.nl = p->pk.nl; v.nblocks = p->pk.nblocks;
     return v;
 }
@@ -1091,7 +1249,11 @@ SmemPlan smem_plan_of(const ChunkMax& k) {
     };
     const size_t w = sizeof(T);
     sp.P = take((size_t)k.mat * w + 16);
-    sp.xs = take((size_t)k.loc * w); sp.ls = take((size_t)k.loc * w);
+    // FP32 keeps x - lambda / rho per local and the shifted u rows; FP64
+    // (bound by FP64 fma throughput) recomputes the former and shuffles u,
+    // which keeps two of its CTAs within one SM's shared memory
+    const bool f32 = w == 4;
+    sp.xs = take((size_t)k.loc * w); sp.ls = take((size_t)k.loc * w); sp.ws = take(f32 ? (size_t)k.loc * w : 0);
     sp.bb = take((size_t)k.loc * w); sp.mt = take((size_t)k.loc * 4);
     sp.zs = take((size_t)k.halo * w); sp.hlo = take((size_t)k.halo * w); sp.hhi = take((size_t)k.halo * w);
     sp.hik = take((size_t)k.halo * w); sp.hck = take((size_t)k.halo * w);
@@ -1099,6 +1261,7 @@ SmemPlan smem_plan_of(const ChunkMax& k) {
     sp.big = k.big;
     sp.us = take((size_t)kXWarps * k.big * w);
     sp.tl = take((size_t)std::max(1, k.tiles) * sizeof(Tile));
+    sp.ush = take(f32 ? (size_t)kXWarps * 4 * kUrow * w : 0);
     sp.total = off;
     return sp;
 }
@@ -1150,6 +1313,7 @@ void launch_persistent(opf_problem* p, cudaStream_t s) {
     OPF_CUDA(cudaMemsetAsync(p->flags, 0, sizeof(int32_t) * p->pk.nblocks, s));
     const int variant = persistent_variant<T>(p);
     if (variant == 2) {
+        OPF_CUDA(cudaMemsetAsync(p->mbox, 0, (size_t)p->pk.nl * 2 * Mail<T>::kWords * sizeof(unsigned long long), s));
         SmemPlan sp = smem_plan<T>(p);
         void* args[] = {&v, &sp};
         OPF_CUDA(cudaLaunchCooperativeKernel((const void*)persistent_smem_kernel<T>, dim3(p->pk.nblocks),
@@ -1290,6 +1454,7 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     p->hcp = (int32_t*)(a + L.hcp); p->hci = (int32_t*)(a + L.hci);
     p->cost = (double*)(a + L.cost); p->partials = (double*)(a + L.partials);
     p->phase = (unsigned long long*)(a + L.phase);
+    p->mbox = (unsigned long long*)(a + L.mbox);
     p->ctl = (Ctl*)(a + L.ctl);
     if (!p->ctl_host) OPF_CUDA(cudaMallocHost((void**)&p->ctl_host, sizeof(Ctl)));
     std::memset(p->ctl_host, 0, sizeof(Ctl));
@@ -1578,9 +1743,12 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     if (engine == OPF_ENGINE_AUTO)
         engine = (coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas) ||
                   coop_fits(batch_global_kernel<T>, gsmem, nctas)) ? OPF_ENGINE_PERSISTENT : OPF_ENGINE_GRAPH;
+    if (engine == OPF_ENGINE_GRAPH)
+        for (int i = 0; i < nprm; ++i)
+            if (prm[i].check_every != prm[0].check_every)
+                throw Error(OPF_ERR_INVALID_ARG, "batch graph engine: every instance needs the same check_every");
     const int prec = sizeof(T) == 8 ? OPF_FP64 : OPF_FP32;
     int c = 0, cz = 0, running = 0;
-    bool same_K = true;
     for (int i = 0; i < n; ++i) {
         opf_problem* p = B->probs[i];
         const opf_params& pr = prm[nprm == 1 ? 0 : i];
@@ -1599,7 +1767,6 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
         hviews[i] = view_of<T>(p, prec_of<T>(p));
         for (int b = 0; b < p->pk.nblocks; ++b) hmap[c++] = CtaMap{i, b};
         for (int g0 = 0; g0 < p->pk.ng; g0 += kZThreads) hzmap[cz++] = ZMap{i, g0};
-        same_K &= pr.check_every == prm[0].check_every;
     }
     *hrun = running;
     for (int i = 0; i < n; ++i)
@@ -1611,12 +1778,11 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     const ZMap* dzmap = reinterpret_cast<const ZMap*>(d + zmap_off);
     int* drun = reinterpret_cast<int*>(d + run_off);
     Ctl* dctl = reinterpret_cast<Ctl*>(d + ctl_off);
-    batch_clear_flags<T><<<std::min(n, 1024), 256, 0, s>>>(dviews, n);
+    const bool smem_var = engine == OPF_ENGINE_PERSISTENT && coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas);
+    batch_clear_flags<T><<<std::min(n, 1024), 256, 0, s>>>(dviews, n, smem_var ? 1 : 0);
     OPF_CUDA(cudaGetLastError());
-    if (engine == OPF_ENGINE_GRAPH && !same_K)
-        throw Error(OPF_ERR_INVALID_ARG, "batch graph engine: every instance needs the same check_every");
     if (running > 0 && engine == OPF_ENGINE_PERSISTENT) {
-        if (coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas)) {
+        if (smem_var) {
             void* args[] = {&dviews, &dmap, &sp};
             OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_smem_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
                                                  args, (size_t)sp.total, s));

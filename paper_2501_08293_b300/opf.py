@@ -244,7 +244,7 @@ class Problem:
         out = np.zeros(8)
         _check(lib.opf_profile_persistent(self._h, C.byref(p), int(iters), _stream_handle(stream), _dp(out)),
                "opf_profile_persistent")
-        names = ("interior", "wait", "boundary", "release_check")
+        names = ("global_interior", "global_boundary_wait", "local_boundary", "local_interior_check")
         return {"mean": dict(zip(names, out[:4])), "max": dict(zip(names, out[4:]))}
 
     def persistent_ok(self, params: Params) -> bool:

@@ -291,7 +291,7 @@ def test_persistent_phase_profile(opf):
     prm = opf.default_params(precision=1, rho=10.0, check_every=50)
     prof = p.profile_persistent(prm, iters=300)
     a = p.state()
-    assert all(v >= 0 for v in prof["mean"].values()) and prof["mean"]["interior"] > 0
+    assert all(v >= 0 for v in prof["mean"].values()) and prof["mean"]["local_interior_check"] > 0
     q = opf.Problem.from_feeder(f)
     q.solve(opf.default_params(precision=1, rho=10.0, check_every=50, criterion=opf.CRIT_NEVER, max_iter=300,
                                engine=opf.ENGINE_PERSISTENT))
