@@ -285,6 +285,21 @@ int32_t opf_profile_kernels(opf_problem* p, const opf_params* params, int32_t re
  * shared-memory kernel to fit (else OPF_ERR_INVALID_ARG).                  */
 int32_t opf_profile_persistent(opf_problem* p, const opf_params* params, int32_t iters, void* stream, double* out);
 
+/* The same measurement per CTA: per_cta[4*b + k] = microseconds per
+ * iteration of phase k (order as above) in chunk b, n_blocks * 4 entries.  */
+int32_t opf_profile_persistent_ctas(opf_problem* p, const opf_params* params, int32_t iters, void* stream,
+                                    double* per_cta);
+
+/* Layout statistics of each chunk (host data, no device needed), for
+ * choosing the chunk count: out[OPF_CHUNK_STATS * b + k] with k =
+ * 0 tiles (without padding), 1 interior tiles, 2 operator column groups of
+ * four over the chunk's tiles, 3 the largest per-warp sum of (column groups
+ * + 2) over the chunk's warps, 4 halo entries, 5 boundary halo entries,
+ * 6 copies in the halo lists, 7 copies held by other chunks, 8 neighbour
+ * chunks, 9 locals.  The paper has no counterpart.                        */
+#define OPF_CHUNK_STATS 10
+int32_t opf_chunk_stats(const opf_problem* p, int32_t* out);
+
 /* Engine that OPF_ENGINE_AUTO selects for this problem and precision on the
  * problem's device (OPF_ENGINE_PERSISTENT or OPF_ENGINE_GRAPH).            */
 int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine);

@@ -3,6 +3,7 @@
 // message retrievable with opf_last_error() on the same thread.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -20,7 +21,8 @@ void device_free(opf_problem* p);
 int device_auto_engine(const opf_problem* p, int precision);
 void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us);
 void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos);
-void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters, cudaStream_t s, double* out);
+void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters, cudaStream_t s, double* out,
+                               double* per_cta);
 void device_batch_free(opf_batch* B);
 int device_batch_capacity(int precision);
 void residuals_noalloc(const double* v, const double* z, const double* zp, const double* lam, long long n,
@@ -268,7 +270,50 @@ int32_t opf_profile_persistent(opf_problem* p, const opf_params* prm, int32_t it
         if (iters < 1) throw opf::Error(OPF_ERR_INVALID_ARG, "iters must be >= 1");
         if (!(prm->rho > 0.0) || (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) || prm->check_every < 1)
             throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
-        opf::device_profile_persistent(p, *prm, iters, (cudaStream_t)stream, out);
+        opf::device_profile_persistent(p, *prm, iters, (cudaStream_t)stream, out, nullptr);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_profile_persistent_ctas(opf_problem* p, const opf_params* prm, int32_t iters, void* stream,
+                                    double* per_cta) {
+    return guarded([&]() -> int32_t {
+        if (!p || !prm || !per_cta) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "profile before upload");
+        if (iters < 1) throw opf::Error(OPF_ERR_INVALID_ARG, "iters must be >= 1");
+        if (!(prm->rho > 0.0) || (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) || prm->check_every < 1)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
+        double agg[8];
+        opf::device_profile_persistent(p, *prm, iters, (cudaStream_t)stream, agg, per_cta);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_chunk_stats(const opf_problem* p, int32_t* out) {
+    return guarded([&]() -> int32_t {
+        if (!p || !out) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        const opf::Packed& k = p->pk;
+        for (int b = 0; b < k.nblocks; ++b) {
+            const opf::BlockInfo& bi = k.blocks[b];
+            int32_t* o = out + (size_t)OPF_CHUNK_STATS * b;
+            int tiles = 0, itiles = 0, quads = 0;
+            std::vector<int> wq(opf::kTileWarps, 0);
+            for (int q = bi.tile0; q < bi.tile1; ++q) {
+                const opf::Tile& t = k.tiles[q];
+                if (!t.big && t.L == 0) continue;
+                const int nq = t.big ? t.L * ((t.L + 3) / 4) / 32 + 1 : (t.nmax + 3) / 4;
+                ++tiles;
+                itiles += q < bi.tileb;
+                quads += nq;
+                wq[(q - (q < bi.tileb ? bi.tile0 : bi.tileb)) % opf::kTileWarps] += nq + 2;
+            }
+            int ext = 0;
+            for (int q = bi.cp0; q < bi.cp1; ++q) ext += k.hci[q] < 0;
+            o[0] = tiles; o[1] = itiles; o[2] = quads;
+            o[3] = *std::max_element(wq.begin(), wq.end());
+            o[4] = bi.halo1 - bi.halo0; o[5] = bi.halo1 - bi.halob;
+            o[6] = bi.cp1 - bi.cp0; o[7] = ext; o[8] = bi.nbr1 - bi.nbr0; o[9] = bi.loc1 - bi.loc0;
+        }
         return OPF_OK;
     });
 }

@@ -86,6 +86,14 @@ struct Mail;
 template <>
 struct Mail<float> {
     static constexpr int kWords = 1;
+    static __device__ __forceinline__ void fetch(const unsigned long long* mb, int nl, int slot, int j,
+                                                 unsigned long long* r) {
+        r[0] = ld_relaxed64(mb + (size_t)slot * nl + j);
+    }
+    static __device__ __forceinline__ bool decode(const unsigned long long* r, unsigned tag, float& w) {
+        w = __uint_as_float((unsigned)r[0]);
+        return (unsigned)(r[0] >> 32) == tag;
+    }
     static __device__ __forceinline__ void put(unsigned long long* mb, int nl, int slot, int j, float w, unsigned tag) {
         st_relaxed64(mb + (size_t)slot * nl + j, ((unsigned long long)tag << 32) | __float_as_uint(w));
     }
@@ -99,6 +107,16 @@ struct Mail<float> {
 template <>
 struct Mail<double> {
     static constexpr int kWords = 2;
+    static __device__ __forceinline__ void fetch(const unsigned long long* mb, int nl, int slot, int j,
+                                                 unsigned long long* r) {
+        const unsigned long long* q = mb + ((size_t)slot * nl + j) * 2;
+        r[0] = ld_relaxed64(q);
+        r[1] = ld_relaxed64(q + 1);
+    }
+    static __device__ __forceinline__ bool decode(const unsigned long long* r, unsigned tag, double& w) {
+        w = __longlong_as_double((long long)(((r[1] & 0xFFFFFFFFull) << 32) | (r[0] & 0xFFFFFFFFull)));
+        return (unsigned)(r[0] >> 32) == tag && (unsigned)(r[1] >> 32) == tag;
+    }
     static __device__ __forceinline__ void put(unsigned long long* mb, int nl, int slot, int j, double w, unsigned tag) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(w);
         unsigned long long* q = mb + ((size_t)slot * nl + j) * 2;
@@ -710,12 +728,28 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     // from mailbox slot (t - 1) & 1, polled until its tag is t (bounded).
     const unsigned long long* mb = v.mbox;
     const int nlg = v.nl;
+    // Mailbox words of the first boundary entry of each thread, loaded at
+    // the start of an iteration so that their latency overlaps the
+    // interior global update (kPre copies; raw words, tags checked later).
+    constexpr int kW = Mail<T>::kWords;
+    constexpr int kPre = 8 / kW;
+    unsigned long long raw[8];
+    auto prefetch = [&](int t) {
+        const int h = hb + threadIdx.x;
+        if (t == 0 || h >= nh) return;
+        const int q0 = hp[h], n = min(hp[h + 1] - q0, kPre);
+#pragma unroll
+        for (int k = 0; k < kPre; ++k)
+            if (k < n && hc[q0 + k] < 0) Mail<T>::fetch(mb, nlg, (t - 1) & 1, ~hc[q0 + k], raw + k * kW);
+    };
     auto zphase = [&](int h0, int h1, int t, bool& ok) {
         const int slot = (t - 1) & 1;
         const unsigned tag = (unsigned)t;
         for (int h = h0 + threadIdx.x; h < h1 && ok; h += blockDim.x) {
             T sum = 0;
             const int q0 = hp[h], q1 = hp[h + 1];
+            // the prefetched words cover this thread's first boundary entry
+            const bool pre = h0 == hb && h == hb + (int)threadIdx.x && t > 0;
             for (int qb = q0; qb < q1 && ok; qb += 8) {
                 // issue every copy's loads first, then add in CSR order
                 T w[8];
@@ -728,9 +762,13 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                         if (c >= 0) {
                             if constexpr (kF32) w[k] = ws[c];
                             else w[k] = copy_term(xs[c], ls[c], inv_rho);
+                        } else if (t == 0) {
+                            w[k] = copy_term(__ldcg(v.xl + ~c), __ldcg(v.lam + ~c), inv_rho);
+                        } else if (k < kPre && pre && qb == q0) {
+                            if (!Mail<T>::decode(raw + k * kW, tag, w[k])) miss |= 1u << k;
+                        } else if (!Mail<T>::get(mb, nlg, slot, ~c, tag, w[k])) {
+                            miss |= 1u << k;
                         }
-                        else if (t == 0) w[k] = copy_term(__ldcg(v.xl + ~c), __ldcg(v.lam + ~c), inv_rho);
-                        else if (!Mail<T>::get(mb, nlg, slot, ~c, tag, w[k])) miss |= 1u << k;
                     }
                 }
                 if (miss) {
@@ -827,12 +865,17 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         }
     };
     const int ntl = bi.tile1 - bi.tile0, ntb = bi.tileb - bi.tile0;
+    // phase marks in SM cycles (cheap), scaled to ns by the globaltimer over
+    // the whole loop
     const bool prof = ctl->profile_phases != 0 && threadIdx.x == 0;
-    unsigned long long ph[4] = {0, 0, 0, 0}, tp = prof ? now_ns() : 0;
+    unsigned long long ph[4] = {0, 0, 0, 0};
+    long long tp = prof ? clock64() : 0;
+    const long long c_start = tp;
+    const unsigned long long g_start = prof ? now_ns() : 0;
     auto mark = [&](int k) {
         if (prof) {
-            const unsigned long long tn = now_ns();
-            ph[k] += tn - tp;
+            const long long tn = clock64();
+            ph[k] += (unsigned long long)(tn - tp);
             tp = tn;
         }
     };
@@ -845,6 +888,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         bool okz = true;
         // global update: interior halo entries (copies all in this chunk),
         // then boundary ones (the neighbours' terms of iteration t - 1)
+        prefetch(t);
         zphase(0, hb, t, okz);
         mark(0);
         zphase(hb, nh, t, okz);
@@ -909,8 +953,10 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         if (it0 + t >= maxit) done = true;
         mark(3);
     }
-    if (prof)
-        for (int k = 0; k < 4; ++k) v.phase[(size_t)b * 4 + k] = ph[k];
+    if (prof) {
+        const double scale = (double)(now_ns() - g_start) / (double)max(1ll, clock64() - c_start);
+        for (int k = 0; k < 4; ++k) v.phase[(size_t)b * 4 + k] = (unsigned long long)((double)ph[k] * scale);
+    }
     // epilogue: owners publish the last global update, the chunk's iterate
     // goes back to the primary buffers.  Neighbours read those buffers only
     // at t == 0; after a one-iteration launch, wait until every neighbour
@@ -1929,7 +1975,8 @@ void device_warm_transfer(opf_problem* dst, const opf_problem* src, const std::v
 // Per-iteration time of each phase of the shared-memory persistent kernel,
 // mean and max over CTAs: a solve of `iters` iterations from the initial
 // point with the phase counters on.
-void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters, cudaStream_t s, double* out) {
+void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters, cudaStream_t s, double* out,
+                               double* per_cta) {
     DeviceGuard g(p->device);
     opf_params q = prm;
     q.warm_start = 0;
@@ -1956,6 +2003,7 @@ void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters,
         double sum = 0, mx = 0;
         for (int b = 0; b < nb; ++b) {
             const double us = 1e-3 * (double)h[(size_t)b * 4 + k] / iters;
+            if (per_cta) per_cta[(size_t)b * 4 + k] = us;
             sum += us;
             mx = std::max(mx, us);
         }

@@ -96,6 +96,8 @@ EXPORTS = {
     "opf_debug_config": (C.c_int32, [_P, C.c_int64, C.c_int32, C.c_int32]),
     "opf_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
     "opf_profile_persistent": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
+    "opf_profile_persistent_ctas": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
+    "opf_chunk_stats": (C.c_int32, [_P, _I]),
     "opf_residuals_noalloc": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "opf_destroy": (None, [_P]),
     "opf_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
@@ -246,6 +248,23 @@ class Problem:
                "opf_profile_persistent")
         names = ("global_interior", "global_boundary_wait", "local_boundary", "local_interior_check")
         return {"mean": dict(zip(names, out[:4])), "max": dict(zip(names, out[4:]))}
+
+    def profile_persistent_ctas(self, params: Params | None = None, iters: int = 2000, stream=None) -> np.ndarray:
+        """Per-CTA microseconds per iteration of each phase, shape (n_blocks, 4)."""
+        p = params if params is not None else default_params()
+        out = np.zeros((self.dims.n_blocks, 4))
+        _check(lib.opf_profile_persistent_ctas(self._h, C.byref(p), int(iters), _stream_handle(stream), _dp(out)),
+               "opf_profile_persistent_ctas")
+        return out
+
+    CHUNK_STATS = ("tiles", "interior_tiles", "quads", "max_warp_quads", "halo", "boundary_halo", "copies",
+                   "external_copies", "neighbours", "locals")
+
+    def chunk_stats(self) -> dict:
+        """Per-chunk layout statistics (opf_chunk_stats), one array per name."""
+        out = np.zeros((self.dims.n_blocks, len(self.CHUNK_STATS)), dtype=np.int32)
+        _check(lib.opf_chunk_stats(self._h, out.ctypes.data_as(_I)), "opf_chunk_stats")
+        return {k: out[:, i].copy() for i, k in enumerate(self.CHUNK_STATS)}
 
     def persistent_ok(self, params: Params) -> bool:
         e = C.c_int32()
