@@ -253,25 +253,30 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         // longest tile first to the least loaded warp, then lay the tiles out
         // so that position q of the range is run by warp q % kTileWarps
         // (empty padding tiles where a warp has fewer tiles)
+        // tile cost in units of one group of four operator columns (two
+        // vector loads and two packed fmas per lane), plus the per-tile work
         auto tile_cost = [&](size_t w) {
             if (lanes[w] < 0) {
                 const int n = M.comps[warps[w][0]].n();
-                return (int64_t)n * ((n + 31) / 32) + 16;
+                return (int64_t)(n * ((n + 31) / 32) + 3) / 4 + 6;
             }
             int nmax = 0;
             for (int s2 : warps[w]) nmax = std::max(nmax, M.comps[s2].n());
-            return (int64_t)nmax + 8;
+            return (int64_t)(nmax + 3) / 4 + 6;
         };
-        std::vector<long> layout;              // indices into warps, -1 = padding
-        for (int range = 0; range < 2; ++range) {
+        // the local update runs the boundary range, then the interior range,
+        // with no barrier in between: balance boundary tiles first, then the
+        // interior ones on top of each warp's boundary load
+        std::vector<int64_t> load(kTileWarps, 0);
+        std::vector<std::vector<size_t>> per_range[2];
+        for (int range : {1, 0}) {
             const size_t r0 = range == 0 ? 0 : first_boundary_warp;
             const size_t r1 = range == 0 ? first_boundary_warp : warps.size();
-            if (range == 1) bi.tileb = bi.tile0 + (int)layout.size();
             std::vector<size_t> idx;
             for (size_t w = r0; w < r1; ++w) idx.push_back(w);
             std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) { return tile_cost(a) > tile_cost(c); });
-            std::vector<std::vector<size_t>> per(kTileWarps);
-            std::vector<int64_t> load(kTileWarps, 0);
+            std::vector<std::vector<size_t>>& per = per_range[range];
+            per.assign(kTileWarps, {});
             for (size_t w : idx) {
                 int best = 0;
                 for (int k = 1; k < kTileWarps; ++k)
@@ -279,6 +284,13 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
                 per[best].push_back(w);
                 load[best] += tile_cost(w);
             }
+        }
+        // lay each range out so that position q of the range is run by warp
+        // q % kTileWarps (empty padding tiles where a warp has fewer tiles)
+        std::vector<long> layout;              // indices into warps, -1 = padding
+        for (int range = 0; range < 2; ++range) {
+            if (range == 1) bi.tileb = bi.tile0 + (int)layout.size();
+            const std::vector<std::vector<size_t>>& per = per_range[range];
             size_t rows = 0;
             for (auto& v2 : per) rows = std::max(rows, v2.size());
             for (size_t k = 0; k < rows; ++k)

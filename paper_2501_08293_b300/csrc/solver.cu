@@ -199,14 +199,9 @@ __device__ __forceinline__ void load_quad(const double* p, double (&o)[4]) {
 // sm_100+ (two independent round-to-nearest fmas, so the same bits as two
 // scalar fmas); two fmas for FP64.
 __device__ __forceinline__ void fma_pair(float& y0, float& y1, float a0, float a1, float b0, float b1) {
-    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
-        "mov.b64 pa, {%2, %3};\n\t"
-        "mov.b64 pb, {%4, %5};\n\t"
-        "mov.b64 pc, {%0, %1};\n\t"
-        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
-        "mov.b64 {%0, %1}, pc;\n\t}"
-        : "+f"(y0), "+f"(y1)
-        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(b0, b1), make_float2(y0, y1));
+    y0 = r.x;
+    y1 = r.y;
 }
 __device__ __forceinline__ void fma_pair(double& y0, double& y1, double a0, double a1, double b0, double b1) {
     y0 = fma(a0, b0, y0);
@@ -252,6 +247,19 @@ __device__ __forceinline__ T tile_gemv_sh(const T* Pt, int L, int r, int nq, con
         fma_pair(y0, y1, p[2], p[3], w[2], w[3]);
     }
     return y0 + y1;
+}
+template <>
+__device__ __forceinline__ float tile_gemv_sh<float>(const float* Pt, int L, int r, int nq, const float* ub) {
+    float2 y = make_float2(0.f, 0.f);
+    const float4* P4 = reinterpret_cast<const float4*>(Pt) + r;
+    const float4* U4 = reinterpret_cast<const float4*>(ub);
+#pragma unroll 4
+    for (int q = 0; q < nq; ++q) {
+        const float4 p = P4[q * L], u = U4[q];
+        y = __ffma2_rn(make_float2(p.x, p.y), make_float2(u.x, u.y), y);
+        y = __ffma2_rn(make_float2(p.z, p.w), make_float2(u.z, u.w), y);
+    }
+    return y.x + y.y;
 }
 
 // Eq. (global_sparse) for global g from the copies in (xr, lr).
@@ -732,39 +740,63 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     // the start of an iteration so that their latency overlaps the
     // interior global update (kPre copies; raw words, tags checked later).
     constexpr int kW = Mail<T>::kWords;
-    constexpr int kPre = 8 / kW;
-    unsigned long long raw[8];
+    constexpr int kPre = 4;                     // copies prefetched per thread
+    unsigned long long raw[kPre * kW];
+    // halo entry h is handled by thread h % blockDim.x (interior and
+    // boundary entries alike, so no thread gets a second entry before every
+    // thread has one); hb1 = this thread's first boundary entry
+    const int hb1 = hb + (int)((threadIdx.x + blockDim.x - (unsigned)hb % blockDim.x) % blockDim.x);
     auto prefetch = [&](int t) {
-        const int h = hb + threadIdx.x;
+        const int h = hb1;
         if (t == 0 || h >= nh) return;
         const int q0 = hp[h], n = min(hp[h + 1] - q0, kPre);
 #pragma unroll
         for (int k = 0; k < kPre; ++k)
             if (k < n && hc[q0 + k] < 0) Mail<T>::fetch(mb, nlg, (t - 1) & 1, ~hc[q0 + k], raw + k * kW);
     };
-    auto zphase = [&](int h0, int h1, int t, bool& ok) {
+    // term of an internal copy (chunk-relative local c)
+    auto wint = [&](int c) -> T {
+        if constexpr (kF32) return ws[c];
+        else return copy_term(xs[c], ls[c], inv_rho);
+    };
+    // interior entries: every copy is in this chunk; pairs of loads, then
+    // the adds in CSR order
+    auto zinterior = [&]() {
+        for (int h = threadIdx.x; h < hb; h += blockDim.x) {
+            const int q0 = hp[h], q1 = hp[h + 1];
+            T sum = 0;
+            int q = q0;
+            for (; q + 1 < q1; q += 2) {
+                const T a = wint(hc[q]), c = wint(hc[q + 1]);
+                sum += a;
+                sum += c;
+            }
+            if (q < q1) sum += wint(hc[q]);
+            zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
+        }
+    };
+    // boundary entries: copies of other chunks come from the mailbox (or,
+    // at t == 0, from the initial iterate)
+    auto zboundary = [&](int t, bool& ok) {
         const int slot = (t - 1) & 1;
         const unsigned tag = (unsigned)t;
-        for (int h = h0 + threadIdx.x; h < h1 && ok; h += blockDim.x) {
+        for (int h = hb1; h < nh && ok; h += blockDim.x) {
             T sum = 0;
             const int q0 = hp[h], q1 = hp[h + 1];
-            // the prefetched words cover this thread's first boundary entry
-            const bool pre = h0 == hb && h == hb + (int)threadIdx.x && t > 0;
-            for (int qb = q0; qb < q1 && ok; qb += 8) {
-                // issue every copy's loads first, then add in CSR order
-                T w[8];
+            const bool pre = h == hb1 && t > 0;      // prefetched words of this entry
+            for (int qb = q0; qb < q1 && ok; qb += 4) {
+                T w[4];
                 unsigned miss = 0;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < 4; ++k) {
                     w[k] = 0;
                     if (qb + k < q1) {
                         const int c = hc[qb + k];
                         if (c >= 0) {
-                            if constexpr (kF32) w[k] = ws[c];
-                            else w[k] = copy_term(xs[c], ls[c], inv_rho);
+                            w[k] = wint(c);
                         } else if (t == 0) {
                             w[k] = copy_term(__ldcg(v.xl + ~c), __ldcg(v.lam + ~c), inv_rho);
-                        } else if (k < kPre && pre && qb == q0) {
+                        } else if (pre && qb == q0) {
                             if (!Mail<T>::decode(raw + k * kW, tag, w[k])) miss |= 1u << k;
                         } else if (!Mail<T>::get(mb, nlg, slot, ~c, tag, w[k])) {
                             miss |= 1u << k;
@@ -773,11 +805,11 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                 }
                 if (miss) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
+                    for (int k = 0; k < 4; ++k)
                         if (((miss >> k) & 1u) && ok) ok = mail_poll(mb, nlg, slot, ~hc[qb + k], tag, w[k], ctl, tmo, 1);
                 }
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
+                for (int k = 0; k < 4; ++k)
                     if (qb + k < q1) sum += w[k];
             }
             if (ok) zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
@@ -889,9 +921,9 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         // global update: interior halo entries (copies all in this chunk),
         // then boundary ones (the neighbours' terms of iteration t - 1)
         prefetch(t);
-        zphase(0, hb, t, okz);
+        zinterior();
         mark(0);
-        zphase(hb, nh, t, okz);
+        zboundary(t, okz);
         if (!__syncthreads_and(okz)) return;
         mark(1);
         // local update: boundary tiles first so that their terms reach the
