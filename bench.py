@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="8500", choices=["8500", "batch", "serve"])
+    ap.add_argument("--workload", default="8500", choices=["8500", "batch", "serve", "configs"])
+    ap.add_argument("--sweep-budget-iters", type=int, default=4_000_000)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-iters", type=int, default=2000)
     ap.add_argument("--requests", type=int, default=200)
@@ -191,6 +192,13 @@ def kernel_times(prob, params, stream):
     return prob.profile_kernels(params, reps=200, stream=stream)
 
 
+# persistent_smem_kernel<float> on the 8500-class feeder (seed 1, default
+# chunking): DRAM traffic per launch from ncu (see profiles/)
+PROFILED_BLOCKS = 296
+TRAFFIC_STAGING_B = 14_601_216
+TRAFFIC_PER_ITER_B = 28.9
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -277,6 +285,14 @@ def run_ours(args):
         launches += 3 if persistent else 2 * n + (n + args.check_every - 1) // args.check_every + 2
 
     peaks, kind = measured_peaks()
+    traffic, traffic_note = None, None
+    if persistent and prec == opf.FP32 and args.seed == 1 and d.n_blocks == PROFILED_BLOCKS:
+        # DRAM bytes of persistent_smem_kernel<float> on this workload from two
+        # ncu captures (2000 and 20000 iterations): one-time staging plus a
+        # small per-iteration term, extrapolated to this launch's iterations
+        traffic = TRAFFIC_STAGING_B + TRAFFIC_PER_ITER_B * (iters / args.steps)
+        traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                        "extrapolated from 2000- and 20000-iteration captures")
     if persistent:
         # the whole solve is one launch of persistent_kernel: its duration is
         # the event-timed solve; bytes = iterations x bytes per iteration
@@ -303,7 +319,8 @@ def run_ours(args):
         "final": {k: infos[-1][k] for k in ("status", "iters", "pres", "dres", "objective")},
         "roofline": {"kernel": kernel_name, "bound": "hbm",
                      "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_kind": kind,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_note": traffic_note,
+                     "peak_kind": kind,
                      "bytes_per_iter": bytes_iter, "flops_per_iter": flops_iter, "us_per_iter": us_iter,
                      "l2": {"peak": L2_READ_GBS, "frac": achieved / L2_READ_GBS,
                             "note": "the iterate is L2-resident within a solve; L2 peak from the project's read probe"},
@@ -505,6 +522,53 @@ def run_profile_solve(args):
     p.close()
 
 
+def run_configs(args):
+    """Every single-instance configuration once, to the ABS 1e-4 residual:
+    13-bus FP64 rho = 100; 123-bus FP64 and FP32 (rho = 10); the 8500-class
+    feeder (11,932 buses) in FP32 for rho in {10, 100, 1000}; the literal
+    8500-bus variant in FP32 (rho = 10).  One solve each after one warm-up
+    solve, event-timed; one JSON line with a row per run."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+    lp = golden_lp()
+    runs = [("13-bus", F.feeder_13(1), opf.FP64, 100.0, "13"), ("123-bus", F.feeder_123(1), opf.FP64, 10.0, "123"),
+            ("123-bus", F.feeder_123(1), opf.FP32, 10.0, "123")]
+    for rho in (10.0, 100.0, 1000.0):
+        runs.append(("8500-class (11932 buses)", F.feeder_8500(1), opf.FP32, rho, "8500"))
+    runs.append(("8500-bus literal", F.feeder_8500(1, n_bus=8500), opf.FP32, 10.0, None))
+    rows = []
+    stream = torch.cuda.current_stream()
+    with ClockSampler(0) as clk:
+        for name, f, prec, rho, key in runs:
+            p = opf.Problem.from_feeder(f)
+            prm = opf.default_params(rho=rho, precision=prec, check_every=args.check_every,
+                                     max_iter=args.sweep_budget_iters)
+            p.solve(opf.default_params(rho=rho, precision=prec, check_every=args.check_every, max_iter=1000))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = p.solve(prm)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            d = p.dims
+            rows.append({"config": name, "n_bus": f.n_bus, "precision": "fp64" if prec == opf.FP64 else "fp32",
+                         "rho": rho, "status": info.status, "iters": info.iters, "seconds": sec,
+                         "iters_per_s": info.iters / sec, "us_per_iter": 1e6 * sec / max(1, info.iters),
+                         "pres": info.pres, "dres": info.dres, "objective": info.objective,
+                         "objective_rel_err_vs_lp": (abs(info.objective - lp[key]) / abs(lp[key])
+                                                     if key in lp else None),
+                         "S": d.n_comp, "n_global": d.n_global, "n_local": d.n_local, "chunks": d.n_blocks,
+                         "engine": used_engine(p, prm)})
+            p.close()
+    print(json.dumps({"metric": "ADMM iterations/s and time to ABS 1e-4 per configuration", "unit": "iters/s",
+                      "n_gpus": 1, "data": "synthetic", "rows": rows, "clocks": clk.summary()}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.profile_solve:
@@ -515,5 +579,7 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "configs":
+        run_configs(a)
     else:
         run_ours(a)
