@@ -149,7 +149,7 @@ __device__ __forceinline__ bool mail_poll(const unsigned long long* mb, int nl, 
     unsigned long long deadline = 0;
     while (!Mail<T>::get(mb, nl, slot, j, tag, w)) {
         if ((++spins & 31u) == 0) {
-            if (ld_acquire(&ctl->abort)) return false;
+            if (ld_acquire(&ctl->abort) || ld_acquire(&ctl->halt)) return false;
             const unsigned long long tn = now_ns();
             if (deadline == 0) {
                 deadline = tn + tmo;
@@ -911,6 +911,13 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
             tp = tn;
         }
     };
+    auto flush_prof = [&]() {
+        if (prof) {
+            const double scale = (double)(now_ns() - g_start) / (double)max(1ll, clock64() - c_start);
+            for (int k = 0; k < 4; ++k) v.phase[(size_t)b * 4 + k] = (unsigned long long)((double)ph[k] * scale);
+        }
+    };
+    bool snap = false;          // the primary buffers hold the state of the last iteration
     while (!done) {
         const int nrem = maxit - (it0 + t);
         const bool check = ((t + 1) % K == 0) || nrem == 1;
@@ -924,7 +931,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         zinterior();
         mark(0);
         zboundary(t, okz);
-        if (!__syncthreads_and(okz)) return;
+        if (!__syncthreads_and(okz)) { flush_prof(); return; }
         mark(1);
         // local update: boundary tiles first so that their terms reach the
         // neighbours while the interior tiles are computed
@@ -933,8 +940,75 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         xphase(0, ntb, t, !defer, check, acc);
         __syncthreads();
         ++t;
-        if (check) {
-            cta_partials(acc, red, v.partials + (size_t)b * 8);
+        snap = false;
+        if (__builtin_expect(check, 0) && !adaptive && t >= 2) {
+            // Non-blocking check: the chunk's state after iteration t goes to
+            // the primary buffers (x_s, lambda; owners' x) as a snapshot,
+            // the partials to slot checkno & 1, a ticket elects the last CTA
+            // to decide, and nobody waits for the decision.  A stop decision
+            // raises `halt`; every CTA sees it at its next check (or while
+            // polling a neighbour that has left) and leaves: the snapshot of
+            // the deciding check is the result.  Before a check a CTA waits
+            // for the previous decision, so a slot and a snapshot are never
+            // overwritten while still needed.
+            if (checkno > 0) {
+                if (threadIdx.x == 0) {
+                    int okw = 1;
+                    const unsigned long long deadline = now_ns() + tmo;
+                    while (ld_acquire(&ctl->decided) < checkno) {
+                        if (ld_acquire(&ctl->abort)) { okw = 0; break; }
+                        if (now_ns() > deadline) {
+                            if (atomicCAS(&ctl->abort, 0, 1) == 0) { ctl->status = CTL_TIMEOUT; ctl->timeout_where = 2; }
+                            okw = 0;
+                            break;
+                        }
+                        __nanosleep(20);
+                    }
+                    s_ok = okw && !ld_acquire(&ctl->halt);
+                }
+                __syncthreads();
+                if (!s_ok) { flush_prof(); return; }
+            }
+            for (int h = threadIdx.x; h < nh; h += blockDim.x)
+                if (v.halo_own[bi.halo0 + h]) v.zg[v.halo_gid[bi.halo0 + h]] = zs[h];
+            for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
+                v.xl[bi.loc0 + j] = xs[j];
+                v.lam[bi.loc0 + j] = ls[j];
+            }
+            double* slot = v.partials + (size_t)(checkno & 1) * v.nblocks * 8;
+            cta_partials(acc, red, slot + (size_t)b * 8);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const unsigned long long ticket = atomicAdd(&ctl->arrive, 1ull);
+                s_last = ticket == (unsigned long long)v.nblocks * (checkno + 1) - 1;
+                s_stop = 0;
+            }
+            __syncthreads();
+            if (s_last) {
+                sum_partials_small(slot, v.nblocks, red, tot);
+                if (threadIdx.x == 0) {
+                    ctl->iter = it0 + t;
+                    const int stop = decide(ctl, tot, it0 + t);
+                    ctl->stop = stop;
+                    if (stop) ctl->halt = 1;
+                    __threadfence();
+                    st_release(&ctl->decided, checkno + 1);
+                    s_stop = stop;
+                }
+                __syncthreads();
+            }
+            ++checkno;
+            snap = true;
+            if (s_stop) done = true;
+        } else if (__builtin_expect(check, 0)) {
+            double* slot = v.partials + (size_t)(checkno & 1) * v.nblocks * 8;
+            if (checkno > 0 && threadIdx.x == 0) {   // previous (non-blocking) decision consumed that slot
+                const unsigned long long deadline = now_ns() + tmo;
+                while (ld_acquire(&ctl->decided) < checkno && now_ns() < deadline && !ld_acquire(&ctl->abort))
+                    __nanosleep(20);
+            }
+            cta_partials(acc, red, slot + (size_t)b * 8);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
@@ -943,7 +1017,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
             }
             __syncthreads();
             if (s_last) {
-                sum_partials_small(v.partials, v.nblocks, red, tot);
+                sum_partials_small(slot, v.nblocks, red, tot);
                 if (threadIdx.x == 0) {
                     ctl->iter = it0 + t;
                     ctl->stop = decide(ctl, tot, it0 + t);
@@ -985,10 +1059,8 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         if (it0 + t >= maxit) done = true;
         mark(3);
     }
-    if (prof) {
-        const double scale = (double)(now_ns() - g_start) / (double)max(1ll, clock64() - c_start);
-        for (int k = 0; k < 4; ++k) v.phase[(size_t)b * 4 + k] = (unsigned long long)((double)ph[k] * scale);
-    }
+    flush_prof();
+    if (snap) return;           // the last check's snapshot is the result
     // epilogue: owners publish the last global update, the chunk's iterate
     // goes back to the primary buffers.  Neighbours read those buffers only
     // at t == 0; after a one-iteration launch, wait until every neighbour
@@ -1207,7 +1279,7 @@ Layout layout_of(const opf_problem* p) {
     L.hcp = a.take<int32_t>(k.hcp.size()); L.hci = a.take<int32_t>(k.hci.size() + 1);
     L.flags = a.take<int32_t>(k.nblocks);
     L.cost = a.take<double>(k.ng);
-    L.partials = a.take<double>((size_t)k.nblocks * 8); L.ctl = a.take<Ctl>(1);
+    L.partials = a.take<double>((size_t)k.nblocks * 16); L.ctl = a.take<Ctl>(1);   // two check slots
     L.phase = a.take<unsigned long long>((size_t)k.nblocks * 4);
     L.mbox = a.take<unsigned long long>((size_t)k.nl * 4);     // 2 slots x 2 words (f64)
     L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.xl2 = a.take<double>(k.nl); L.lam2 = a.take<double>(k.nl);
@@ -1567,7 +1639,7 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     OPF_CUDA(cudaMemsetAsync(a + L.P32, 0, (k.mat_elems + 8) * 4, s));
     h2d(p->d64.P, k.P.data(), k.mat_elems * 8);
     h2d32(p->d32.P, k.P);
-    OPF_CUDA(cudaMemsetAsync(p->partials, 0, (size_t)k.nblocks * 8 * sizeof(double), s));
+    OPF_CUDA(cudaMemsetAsync(p->partials, 0, (size_t)k.nblocks * 16 * sizeof(double), s));
     OPF_CUDA(cudaMemsetAsync(p->flags, 0, (size_t)k.nblocks * sizeof(int32_t), s));
     OPF_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(Ctl), s));
     enqueue_init<double>(p, s);
@@ -1598,7 +1670,7 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
     const long long mi = (long long)c.iter + prm.max_iter;
     c.max_iter = (int32_t)(mi > INT32_MAX ? INT32_MAX : mi);
     c.status = CTL_RUNNING; c.stop = 0;
-    c.arrive = 0; c.decided = 0; c.abort = 0; c.timeout_where = 0;
+    c.arrive = 0; c.decided = 0; c.abort = 0; c.halt = 0; c.timeout_where = 0;
     c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
     c.adaptive = prm.adaptive_rho; c.rb_mu = prm.rb_mu; c.rb_tau = prm.rb_tau; c.rho_changes = 0;
     c.profile_phases = p->profile_phases;
@@ -1722,7 +1794,7 @@ Ctl solve_ctl(const opf_problem* p, const opf_params& prm, const Ctl& cur) {
     const long long mi = (long long)c.iter + prm.max_iter;
     c.max_iter = (int32_t)(mi > INT32_MAX ? INT32_MAX : mi);
     c.status = CTL_RUNNING; c.stop = 0;
-    c.arrive = 0; c.decided = 0; c.abort = 0; c.timeout_where = 0;
+    c.arrive = 0; c.decided = 0; c.abort = 0; c.halt = 0; c.timeout_where = 0;
     c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
     c.adaptive = prm.adaptive_rho; c.rb_mu = prm.rb_mu; c.rb_tau = prm.rb_tau; c.rho_changes = 0;
     return c;

@@ -305,3 +305,32 @@ def test_persistent_phase_profile(opf):
     per_iter = e0.elapsed_time(e1) * 1e3 / 300
     assert 0.3 * per_iter <= sum(prof["mean"].values()) <= 1.5 * per_iter
     p.close(); q.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nonblocking_checks_return_the_deciding_iterate(opf, prec):
+    """The shared-memory persistent kernel does not wait for the residual
+    decision: each check leaves a snapshot in the primary buffers and CTAs
+    run on until they learn the outcome.  The result must still be the
+    iterate of the deciding check: same iteration count, state and residuals
+    as the graph engine, for a converging solve on a multi-chunk feeder and
+    for a fixed iteration count that is not a multiple of the check interval."""
+    f = F.feeder_123(2)
+    for crit, max_iter in ((opf.CRIT_ABS, 200000), (opf.CRIT_NEVER, 1234)):
+        res = []
+        for engine, variant in ((opf.ENGINE_GRAPH, 0), (opf.ENGINE_PERSISTENT, 2)):
+            p = opf.Problem.from_feeder(f, chunks=12)
+            p.debug_config(variant=variant)
+            info = p.solve(opf.default_params(criterion=crit, max_iter=max_iter, check_every=50, engine=engine,
+                                              precision=prec, rho=10.0))
+            res.append((p.state(), info))
+            p.close()
+        (a, ia), (b, ib) = res
+        assert ia.iters == ib.iters and ia.status == ib.status
+        if crit == opf.CRIT_NEVER:
+            assert ib.iters == 1234
+        else:
+            assert ib.status == 0 and ib.iters % 50 == 0
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        assert ia.pres == ib.pres and ia.dres == ib.dres and ia.objective == ib.objective
