@@ -262,6 +262,17 @@ __device__ __forceinline__ float tile_gemv_sh<float>(const float* Pt, int L, int
     return y.x + y.y;
 }
 
+// Eq. (global_sparse) from a halo entry's copy sum and its constants
+// c = {lo, hi, 1/k, c/k} (one 16-byte load for FP32).
+__device__ __forceinline__ float halo_global(float sum, const float* c, float inv_rho) {
+    const float4 q = *reinterpret_cast<const float4*>(c);
+    return global_from_sum(sum, q.z, q.w, inv_rho, q.x, q.y);
+}
+__device__ __forceinline__ double halo_global(double sum, const double* c, double inv_rho) {
+    const double2 a = reinterpret_cast<const double2*>(c)[0], b = reinterpret_cast<const double2*>(c)[1];
+    return global_from_sum(sum, b.x, b.y, inv_rho, a.x, a.y);
+}
+
 // Eq. (global_sparse) for global g from the copies in (xr, lr).
 template <typename T, bool CG>
 __device__ __forceinline__ T global_value(const View<T>& v, int g, const T* xr, const T* lr, T inv_rho) {
@@ -611,7 +622,7 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
 // ----------------------------------------------- persistent, shared-memory
 // Per-launch shared-memory plan (byte offsets; every region 16-byte aligned).
 struct SmemPlan {
-    int P, xs, ls, ws, bb, mt, zs, hlo, hhi, hik, hck, hp, hc, us, big, tl, ush, total;
+    int P, xs, ls, ws, bb, mt, zs, hcon, hp, hc, us, big, tl, ush, total;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -650,10 +661,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     T* bb = reinterpret_cast<T*>(sm + sp.bb);
     int* mt = reinterpret_cast<int*>(sm + sp.mt);
     T* zs = reinterpret_cast<T*>(sm + sp.zs);
-    T* hlo = reinterpret_cast<T*>(sm + sp.hlo);
-    T* hhi = reinterpret_cast<T*>(sm + sp.hhi);
-    T* hik = reinterpret_cast<T*>(sm + sp.hik);
-    T* hck = reinterpret_cast<T*>(sm + sp.hck);
+    T* hcon = reinterpret_cast<T*>(sm + sp.hcon);      // per halo entry: lo, hi, 1/k, c/k (one 4-vector)
     int* hp = reinterpret_cast<int*>(sm + sp.hp);
     int* hc = reinterpret_cast<int*>(sm + sp.hc);
     T* usw = reinterpret_cast<T*>(sm + sp.us);          // big-tile staging, sp.big per warp
@@ -702,7 +710,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     }
     for (int h = threadIdx.x; h < nh; h += blockDim.x) {
         const int g = v.halo_gid[bi.halo0 + h];
-        hlo[h] = v.lo[g]; hhi[h] = v.hi[g]; hik[h] = v.invk[g]; hck[h] = v.cik[g];
+        hcon[4 * h] = v.lo[g]; hcon[4 * h + 1] = v.hi[g]; hcon[4 * h + 2] = v.invk[g]; hcon[4 * h + 3] = v.cik[g];
         hp[h] = v.hcp[bi.halo0 + h] - bi.cp0;
     }
     if (threadIdx.x == 0) hp[nh] = ncp;
@@ -772,7 +780,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                 sum += c;
             }
             if (q < q1) sum += wint(hc[q]);
-            zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
+            zs[h] = halo_global(sum, hcon + 4 * h, inv_rho);
         }
     };
     // boundary entries: copies of other chunks come from the mailbox (or,
@@ -812,7 +820,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                 for (int k = 0; k < 4; ++k)
                     if (qb + k < q1) sum += w[k];
             }
-            if (ok) zs[h] = global_from_sum(sum, hik[h], hck[h], inv_rho, hlo[h], hhi[h]);
+            if (ok) zs[h] = halo_global(sum, hcon + 4 * h, inv_rho);
         }
     };
     // publish the terms of this chunk's exported copies for iteration t
@@ -823,6 +831,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     auto xphase = [&](int q0, int q1, int t, bool pub, bool check, double* acc) {
         for (int q = q0 + warp; q < q1; q += kXWarps) {
             const Tile tl = stl[q];
+            if (tl.L == 0) continue;                    // padding tile
             const int jl0 = tl.loc0 - bi.loc0;
             const T* Pt = sP + (tl.mat0 - bi.mat0);
             if (!tl.big) {
@@ -1405,8 +1414,7 @@ SmemPlan smem_plan_of(const ChunkMax& k) {
     const bool f32 = w == 4;
     sp.xs = take((size_t)k.loc * w); sp.ls = take((size_t)k.loc * w); sp.ws = take(f32 ? (size_t)k.loc * w : 0);
     sp.bb = take((size_t)k.loc * w); sp.mt = take((size_t)k.loc * 4);
-    sp.zs = take((size_t)k.halo * w); sp.hlo = take((size_t)k.halo * w); sp.hhi = take((size_t)k.halo * w);
-    sp.hik = take((size_t)k.halo * w); sp.hck = take((size_t)k.halo * w);
+    sp.zs = take((size_t)k.halo * w); sp.hcon = take((size_t)k.halo * 4 * w);
     sp.hp = take((size_t)(k.halo + 1) * 4); sp.hc = take((size_t)std::max(1, k.copies) * 4);
     sp.big = k.big;
     sp.us = take((size_t)kXWarps * k.big * w);
