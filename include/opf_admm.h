@@ -381,6 +381,43 @@ void opf_batch_destroy(opf_batch* b);
  * device: the sum of the problems' chunk counts must not exceed it.        */
 int32_t opf_batch_capacity(int32_t precision, int32_t* max_chunks);
 
+/* --------------------------------------------------------------- scenarios
+ * Many load scenarios on one feeder topology iterated together (FP32
+ * sweeps, FP64 residual sums and objective).  loads holds n_scenarios x
+ * n_load records, scenario-major; every scenario's loads must match
+ * scenario 0's in bus, phases, connection, alpha and beta (only the draw a,
+ * b differs), else OPF_ERR_INVALID_ARG.  Each scenario is Algorithm 1 on
+ * its own model: the components that do not depend on the draw share their
+ * operator P_s, so their local update (Eq. closed_2) is one small matrix
+ * product over all scenarios; load components keep per-scenario bbar_s, and
+ * per-scenario P_s where the load is voltage dependent.  Each scenario
+ * checks its own residuals and stops at its own check; its iterates are the
+ * ones a single-instance FP32 solve of that scenario computes.  Device
+ * memory is allocated on the current device at create (cudaMalloc) and
+ * freed by destroy.  The paper solves one instance; this is the batch
+ * dimension applied to load scenarios.                                     */
+typedef struct opf_scenarios opf_scenarios;
+int32_t opf_scenarios_create(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
+                             const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
+                             int32_t n_scenarios, opf_scenarios** out);
+/* params: precision must be OPF_FP32 and adaptive_rho 0; warm_start continues
+ * every scenario from its current state.  infos: n_scenarios entries (may
+ * be NULL); status per scenario as for opf_admm_solve.                     */
+int32_t opf_scenarios_solve(opf_scenarios* sc, const opf_params* params, void* stream, opf_info* infos);
+/* State of one scenario in the canonical orders (host, caller-owned; any
+ * pointer may be NULL): x[n_global], xl[n_local], lam[n_local].            */
+int32_t opf_scenarios_get_state(const opf_scenarios* sc, int32_t scenario, double* x, double* xl, double* lam,
+                                void* stream);
+int32_t opf_scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* n_local, int64_t* device_bytes);
+/* Average device time in microseconds of each kernel of one iteration, each
+ * launched `reps` times back to back outside the solve graph: us[0] global
+ * update, us[1] local update of components with at most 8 locals, us[2] of
+ * the larger ones, us[3] both local updates on a check iteration, us[4] the
+ * per-scenario check.  Uses params->rho; leaves the scenarios at a cold
+ * start.                                                                   */
+int32_t opf_scenarios_profile(opf_scenarios* sc, const opf_params* params, int32_t reps, void* stream, double* us);
+void opf_scenarios_destroy(opf_scenarios* sc);
+
 /* ----------------------------------------------------------------- serving
  * Continuous batching: requests (feeders) are submitted at any time; each
  * opf_server_step collects the round in flight, retires finished instances,

@@ -27,6 +27,13 @@ void device_batch_free(opf_batch* B);
 int device_batch_capacity(int precision);
 void residuals_noalloc(const double* v, const double* z, const double* zp, const double* lam, long long n,
                        double rho, double eps_rel, double* out, cudaStream_t s);
+opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* lines, int nl, const opf_gen* gens,
+                                int ng, const opf_load* loads, int nd, int S);
+void scenarios_destroy(opf_scenarios* sc);
+void scenarios_solve(opf_scenarios* sc, const opf_params& prm, cudaStream_t s, opf_info* infos);
+void scenarios_get_state(const opf_scenarios* sc, int k, double* xg, double* xl, double* lam, cudaStream_t s);
+void scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* n_local, int64_t* device_bytes);
+void scenarios_profile(opf_scenarios* sc, const opf_params& prm, int reps, cudaStream_t s, double* us);
 }  // namespace opf
 
 namespace {
@@ -422,6 +429,62 @@ int32_t opf_batch_capacity(int32_t precision, int32_t* max_chunks) {
         *max_chunks = opf::device_batch_capacity(precision);
         return OPF_OK;
     });
+}
+
+int32_t opf_scenarios_create(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
+                             const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
+                             int32_t n_scenarios, opf_scenarios** out) {
+    return guarded([&]() -> int32_t {
+        if (!out) throw opf::Error(OPF_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        *out = opf::scenarios_create(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load, n_scenarios);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_scenarios_solve(opf_scenarios* sc, const opf_params* prm, void* stream, opf_info* infos) {
+    return guarded([&]() -> int32_t {
+        if (!sc || !prm) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "scenarios: precision must be FP32");
+        if (prm->adaptive_rho) throw opf::Error(OPF_ERR_INVALID_ARG, "scenarios: residual balancing not supported");
+        if (!(prm->rho > 0.0) || prm->check_every < 1 || prm->max_iter < 0)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
+        opf::scenarios_solve(sc, *prm, (cudaStream_t)stream, infos);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_scenarios_get_state(const opf_scenarios* sc, int32_t scenario, double* x, double* xl, double* lam,
+                                void* stream) {
+    return guarded([&]() -> int32_t {
+        if (!sc) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        opf::scenarios_get_state(sc, scenario, x, xl, lam, (cudaStream_t)stream);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* n_local, int64_t* device_bytes) {
+    return guarded([&]() -> int32_t {
+        if (!sc) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        opf::scenarios_dims(sc, n_global, n_local, device_bytes);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_scenarios_profile(opf_scenarios* sc, const opf_params* prm, int32_t reps, void* stream, double* us) {
+    return guarded([&]() -> int32_t {
+        if (!sc || !prm || !us) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (reps < 1 || !(prm->rho > 0.0)) throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
+        opf::scenarios_profile(sc, *prm, reps, (cudaStream_t)stream, us);
+        return OPF_OK;
+    });
+}
+
+void opf_scenarios_destroy(opf_scenarios* sc) {
+    try {
+        opf::scenarios_destroy(sc);
+    } catch (...) {
+    }
 }
 
 void opf_batch_destroy(opf_batch* b) {

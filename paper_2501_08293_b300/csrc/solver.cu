@@ -42,6 +42,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "arith.cuh"
 #include "problem.hpp"
 
 namespace opf {
@@ -169,20 +170,6 @@ __device__ __forceinline__ double warp_sum(double a) {
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
-// The arithmetic of one iteration, written once with explicit fused
-// multiply-adds (the library is built with -fmad=false, so nothing else is
-// contracted): every engine and kernel computes bit-identical iterates.
-template <typename T>
-__device__ __forceinline__ T copy_term(T x, T l, T inv_rho) { return fma(-l, inv_rho, x); }            // x - l/rho
-template <typename T>
-__device__ __forceinline__ T global_from_sum(T s, T invk, T cik, T inv_rho, T lo, T hi) {
-    const T xh = fma(s, invk, -(cik * inv_rho));                                                          // s/k - c/(rho k)
-    return fmin(fmax(xh, lo), hi);
-}
-template <typename T>
-__device__ __forceinline__ T u_of(T v, T l, T inv_rho) { return fma(l, inv_rho, v); }                 // Bx + l/rho
-template <typename T>
-__device__ __forceinline__ T dual_of(T l, T rho, T v, T xn) { return fma(rho, v - xn, l); }            // l + rho (Bx - z)
 
 // Operator columns 4q .. 4q+3 of one lane (quad layout of pack.cpp: column c
 // of lane r at ((c / 4) * L + r) * 4 + c % 4): one 16-byte load for FP32,

@@ -440,3 +440,20 @@ CONFIG_FEEDERS = {
     "123": feeder_123,
     "8500": feeder_8500,
 }
+
+
+def load_scenarios(f: Feeder, n: int, seed: int, lo: float = 0.5, hi: float = 1.0) -> np.ndarray:
+    """n load draws on the feeder's loads, scenario-major (n x n_load LOAD
+    records): scenario 0 is the feeder's own draw, scenario k scales each
+    load's a and b by its own factor ~ U[lo, hi] (Q/P kept; bus, phases,
+    connection and load model unchanged, so only the draw differs)."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    out = np.empty((n, len(f.loads)), dtype=LOAD_DTYPE)
+    for k in range(n):
+        out[k] = f.loads
+        if k == 0:
+            continue
+        fac = rng.uniform(lo, hi, size=len(f.loads))
+        out[k]["a"] = f.loads["a"] * fac[:, None]
+        out[k]["b"] = f.loads["b"] * fac[:, None]
+    return out

@@ -104,6 +104,13 @@ EXPORTS = {
     "opf_batch_solve": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, C.POINTER(Info)]),
     "opf_batch_destroy": (None, [_P]),
     "opf_batch_capacity": (C.c_int32, [C.c_int32, _I]),
+    "opf_scenarios_create": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32, C.c_int32,
+                                         C.POINTER(C.c_void_p)]),
+    "opf_scenarios_solve": (C.c_int32, [_P, C.POINTER(Params), _P, C.POINTER(Info)]),
+    "opf_scenarios_get_state": (C.c_int32, [_P, C.c_int32, _D, _D, _D, _P]),
+    "opf_scenarios_dims": (C.c_int32, [_P, _I, _I, C.POINTER(C.c_int64)]),
+    "opf_scenarios_profile": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
+    "opf_scenarios_destroy": (None, [_P]),
     "opf_server_config_default": (None, [C.POINTER(ServerConfig)]),
     "opf_server_create": (C.c_int32, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
     "opf_server_submit": (C.c_int32, [_P, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32,
@@ -352,6 +359,65 @@ class Batch:
     def close(self):
         if self._h:
             lib.opf_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scenarios:
+    """Many load scenarios on one topology iterated together (opf_scenarios_*).
+    loads: array of shape (n_scenarios, n_load) of LOAD records."""
+
+    def __init__(self, buses, lines, gens, loads, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: the solver has no CPU path")
+        arrs = [np.ascontiguousarray(a) for a in (buses, lines, gens)]
+        ld = np.ascontiguousarray(loads)
+        if ld.ndim != 2 or ld.dtype != _F.LOAD_DTYPE:
+            raise TypeError("loads must be a (n_scenarios, n_load) array of LOAD records")
+        self.n, n_load = ld.shape
+        self._keep = arrs + [ld]
+        self._h = C.c_void_p()
+        _check(lib.opf_scenarios_create(arrs[0].ctypes.data, len(arrs[0]), arrs[1].ctypes.data, len(arrs[1]),
+                                        arrs[2].ctypes.data, len(arrs[2]), ld.ctypes.data, n_load, self.n,
+                                        C.byref(self._h)), "opf_scenarios_create")
+        ng, nl, nb = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib.opf_scenarios_dims(self._h, C.byref(ng), C.byref(nl), C.byref(nb)), "opf_scenarios_dims")
+        self.n_global, self.n_local, self.device_bytes = ng.value, nl.value, nb.value
+
+    @classmethod
+    def from_feeder(cls, f, loads, **kw) -> "Scenarios":
+        return cls(f.buses, f.lines, f.gens, loads, **kw)
+
+    def solve(self, params: Params, stream=None) -> list:
+        infos = (Info * self.n)()
+        _check(lib.opf_scenarios_solve(self._h, C.byref(params), _stream_handle(stream), infos),
+               "opf_scenarios_solve")
+        return list(infos)
+
+    def profile(self, params: Params, reps: int = 50, stream=None) -> dict:
+        """Per-kernel microseconds of one iteration (opf_scenarios_profile)."""
+        us = np.zeros(5)
+        _check(lib.opf_scenarios_profile(self._h, C.byref(params), int(reps), _stream_handle(stream), _dp(us)),
+               "opf_scenarios_profile")
+        return dict(zip(("z", "x_small", "x_large", "x_check", "check"), us.tolist()))
+
+    def state(self, k: int, stream=None):
+        xg = np.empty(self.n_global)
+        xl = np.empty(self.n_local)
+        lam = np.empty(self.n_local)
+        _check(lib.opf_scenarios_get_state(self._h, int(k), _dp(xg), _dp(xl), _dp(lam), _stream_handle(stream)),
+               "opf_scenarios_get_state")
+        return xg, xl, lam
+
+    def close(self):
+        if self._h:
+            lib.opf_scenarios_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -122,3 +122,31 @@ def test_out_of_service_line_and_degenerate_feeders(opf):
     p = opf.Problem(buses, np.zeros(0, F.LINE_DTYPE), gens, np.zeros(0, F.LOAD_DTYPE), upload=False)
     assert p.dims.n_comp == 2 and p.dims.n_global == 9
     assert len(live) == f.n_bus - 1
+
+
+def test_scenario_inputs_are_validated_on_the_host(opf):
+    """opf_scenarios_create rejects scenarios whose loads differ in anything
+    but the draw (a, b) before it touches a device; load_scenarios keeps
+    everything but the draw."""
+    import ctypes as C
+    f = F.feeder_13(1)
+    loads = F.load_scenarios(f, 3, seed=2)
+    assert loads.shape == (3, len(f.loads)) and loads.dtype == F.LOAD_DTYPE
+    for k in range(3):
+        for fld in ("bus", "phases", "conn", "alpha", "beta"):
+            assert np.array_equal(loads[k][fld], f.loads[fld])
+    assert np.array_equal(loads[0]["a"], f.loads["a"])
+    assert not np.array_equal(loads[1]["a"], f.loads["a"])
+    bad = loads.copy()
+    bad[1]["conn"][0] = 1 - bad[1]["conn"][0]
+    arrs = [np.ascontiguousarray(a) for a in (f.buses, f.lines, f.gens)]
+    h = C.c_void_p()
+    st = opf.lib.opf_scenarios_create(arrs[0].ctypes.data, len(arrs[0]), arrs[1].ctypes.data, len(arrs[1]),
+                                      arrs[2].ctypes.data, len(arrs[2]), bad.ctypes.data, len(f.loads), 3,
+                                      C.byref(h))
+    assert st == -1 and not h.value
+    assert b"only the load draw" in opf.lib.opf_last_error()
+    st = opf.lib.opf_scenarios_create(arrs[0].ctypes.data, len(arrs[0]), arrs[1].ctypes.data, len(arrs[1]),
+                                      arrs[2].ctypes.data, len(arrs[2]), loads.ctypes.data, len(f.loads), 0,
+                                      C.byref(h))
+    assert st == -1

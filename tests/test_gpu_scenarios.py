@@ -1,0 +1,95 @@
+"""Multi-scenario engine: S load draws on one topology iterated together.
+Each scenario's iterates must equal a single-instance FP32 solve of that
+scenario (same arithmetic); its residuals agree to the rounding of their
+sums, converged scenarios reach the same check, and the FP32 objective is
+within 1e-4 of the FP64 path's at the same iteration."""
+import numpy as np
+import pytest
+
+from paper_2501_08293_b300 import feeders as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def opf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_08293_b300 import build
+    build.build()
+    from paper_2501_08293_b300 import opf as mod
+    return mod
+
+
+def alone(opf, f, loads_k, prm):
+    g = f.copy()
+    g.loads = loads_k.copy()
+    p = opf.Problem.from_feeder(g)
+    info = p.solve(prm)
+    st = p.state()
+    p.close()
+    return info, st
+
+
+@pytest.mark.parametrize("S, picks", [(8, range(8)), (70, (0, 1, 63, 64, 69))])
+def test_scenarios_equal_alone_fixed_iterations(opf, S, picks):
+    f = F.feeder_123(1)
+    loads = F.load_scenarios(f, S, seed=7)
+    sc = opf.Scenarios.from_feeder(f, loads)
+    prm = opf.default_params(precision=opf.FP32, rho=10.0, criterion=opf.CRIT_NEVER, max_iter=300, check_every=50)
+    infos = sc.solve(prm)
+    for k in picks:
+        ia, sa = alone(opf, f, loads[k], opf.default_params(precision=opf.FP32, rho=10.0, criterion=opf.CRIT_NEVER,
+                                                             max_iter=300, check_every=50))
+        assert infos[k].iters == ia.iters == 300
+        sb = sc.state(k)
+        for x, y in zip(sb, sa):
+            assert np.array_equal(x, y), k
+        # residual sums: FP32 within a component, FP64 across (single instance:
+        # FP64 throughout), different order
+        assert abs(infos[k].pres - ia.pres) <= 1e-5 * ia.pres
+        assert abs(infos[k].dres - ia.dres) <= 1e-5 * ia.dres
+        assert abs(infos[k].objective - ia.objective) <= 1e-12 * abs(ia.objective)
+    # a second solve continues from the state (warm start)
+    prm.warm_start = 1
+    prm.max_iter = 50
+    infos2 = sc.solve(prm)
+    assert all(i.iters == 350 for i in infos2)
+    sc.close()
+
+
+def test_scenarios_converge_like_alone(opf):
+    f = F.feeder_123(2)
+    S = 6
+    loads = F.load_scenarios(f, S, seed=3)
+    sc = opf.Scenarios.from_feeder(f, loads)
+    prm = opf.default_params(precision=opf.FP32, rho=10.0, max_iter=200000, check_every=50)
+    infos = sc.solve(prm)
+    for k in range(S):
+        ia, sa = alone(opf, f, loads[k], prm)
+        assert infos[k].status == ia.status == 0
+        # the residual sums differ only in summation order: same deciding check
+        assert infos[k].iters == ia.iters, k
+        for x, y in zip(sc.state(k), sa):
+            assert np.array_equal(x, y), k
+        # FP32 sweeps against the FP64 path, same scenario and iteration count
+        i64, _ = alone(opf, f, loads[k], opf.default_params(precision=opf.FP64, rho=10.0, criterion=opf.CRIT_NEVER,
+                                                             max_iter=infos[k].iters, check_every=50))
+        assert abs(infos[k].objective - i64.objective) <= 1e-4 * abs(i64.objective)
+        assert infos[k].pres <= 1e-4 and infos[k].dres <= 1e-4
+    sc.close()
+
+
+def test_scenarios_reject_bad_input(opf):
+    f = F.feeder_13(1)
+    loads = F.load_scenarios(f, 3, seed=1)
+    loads[2]["alpha"][0] = (loads[2]["alpha"][0] + 1) % 3
+    with pytest.raises(opf.OpfError):
+        opf.Scenarios.from_feeder(f, loads)
+    sc = opf.Scenarios.from_feeder(f, F.load_scenarios(f, 3, seed=1))
+    with pytest.raises(opf.OpfError):
+        sc.solve(opf.default_params(precision=opf.FP64))
+    with pytest.raises(opf.OpfError):
+        sc.state(3)
+    sc.close()
