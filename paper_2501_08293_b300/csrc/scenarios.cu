@@ -110,6 +110,7 @@ struct ScView {
     float* Z;      // global vector
     double* partials;
     ScState* st;
+    uint32_t* amask;         // active scenarios, one bit each
     ScCtl* ctl;
     int32_t ncomp, nl, ng, Sp, nctas, maxn;
     int32_t nsmall;          // comps[0, nsmall) have n <= kSmallN, the rest more
@@ -131,46 +132,54 @@ __global__ void sc_init_kernel(ScView v) {
     }
 }
 
-// Eq. (global_sparse) for global i, every scenario; warp per global.  The
+// Eq. (global_sparse) for global i, every scenario: one half-warp per
+// global, four scenarios per lane (16-byte loads of the copies' terms).  The
 // copy list is loaded by the lanes together and broadcast, so the copies'
 // rows are fetched without a dependent load between them.
 __global__ void __launch_bounds__(256) sc_z_kernel(ScView v, int q) {
     const ScCtl* ctl = v.ctl;
     if (ctl->iter + q >= ctl->max_iter) return;
-    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= v.ng) return;
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 4);
+    const int hl = threadIdx.x & 15;
+    const unsigned hm = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
+    if (i >= v.ng) return;                          // whole half-warps leave together
     const float inv_rho = ctl->inv_rho;
     const int b = v.gptr[i], e = v.gptr[i + 1];
     const float invk = v.invk[i], cik = v.cik[i], lo = v.lo[i], hi = v.hi[i];
-    for (int k0 = 2 * lane; k0 < v.Sp; k0 += 64) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int qb = b; qb < e; qb += 32) {
-            const int cnt = min(32, e - qb);
-            const int my = lane < cnt ? v.gcol[qb + lane] : 0;
+    for (int k0 = 4 * hl; k0 < v.Sp; k0 += 64) {
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int qb = b; qb < e; qb += 16) {
+            const int cnt = min(16, e - qb);
+            const int my = hl < cnt ? v.gcol[qb + hl] : 0;
             int c = 0;
             for (; c + 3 < cnt; c += 4) {
-                float2 w[4];
+                float4 w[4];
 #pragma unroll
                 for (int h = 0; h < 4; ++h)
-                    w[h] = *reinterpret_cast<const float2*>(v.W + (size_t)__shfl_sync(0xffffffffu, my, c + h) * v.Sp + k0);
+                    w[h] = *reinterpret_cast<const float4*>(v.W + (size_t)__shfl_sync(hm, my, c + h, 16) * v.Sp + k0);
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    s.x += w[h].x;
-                    s.y += w[h].y;
+                    s.x += w[h].x; s.y += w[h].y; s.z += w[h].z; s.w += w[h].w;
                 }
             }
             for (; c < cnt; ++c) {
-                const float2 w = *reinterpret_cast<const float2*>(v.W + (size_t)__shfl_sync(0xffffffffu, my, c) * v.Sp + k0);
-                s.x += w.x;
-                s.y += w.y;
+                const float4 w = *reinterpret_cast<const float4*>(v.W + (size_t)__shfl_sync(hm, my, c, 16) * v.Sp + k0);
+                s.x += w.x; s.y += w.y; s.z += w.z; s.w += w.w;
             }
         }
-        const float z0 = global_from_sum(s.x, invk, cik, inv_rho, lo, hi);
-        const float z1 = global_from_sum(s.y, invk, cik, inv_rho, lo, hi);
+        const unsigned act = (v.amask[k0 >> 5] >> (k0 & 31)) & 0xFu;
         float* zp = v.Z + (size_t)i * v.Sp + k0;
-        if (v.st[k0].active) zp[0] = z0;
-        if (v.st[k0 + 1].active) zp[1] = z1;
+        if (act == 0xFu) {
+            *reinterpret_cast<float4*>(zp) = make_float4(global_from_sum(s.x, invk, cik, inv_rho, lo, hi),
+                                                         global_from_sum(s.y, invk, cik, inv_rho, lo, hi),
+                                                         global_from_sum(s.z, invk, cik, inv_rho, lo, hi),
+                                                         global_from_sum(s.w, invk, cik, inv_rho, lo, hi));
+        } else {
+            if (act & 1u) zp[0] = global_from_sum(s.x, invk, cik, inv_rho, lo, hi);
+            if (act & 2u) zp[1] = global_from_sum(s.y, invk, cik, inv_rho, lo, hi);
+            if (act & 4u) zp[2] = global_from_sum(s.z, invk, cik, inv_rho, lo, hi);
+            if (act & 8u) zp[3] = global_from_sum(s.w, invk, cik, inv_rho, lo, hi);
+        }
     }
 }
 
@@ -235,12 +244,16 @@ __global__ void __launch_bounds__(kXsWarps * 32) sc_xs_kernel(ScView v, int q) {
     for (int k0 = 2 * lane, pass = 0; k0 < Sp; k0 += 64, ++pass) {
         const bool a0 = v.st[k0].active != 0, a1 = v.st[k0 + 1].active != 0;
         double acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+        // descriptor and globals of the next component are fetched while the
+        // current one is computed
+        ScComp ncd = gw < v.nsmall ? v.comps[gw] : ScComp{0, 0, 0, 0};
+        int ngl = lane < (ncd.nf & 0xFFFF) ? v.gidx[ncd.loc0 + lane] : 0;
         for (int s = gw; s < v.nsmall; s += nw) {
-            const ScComp cd = v.comps[s];
+            const ScComp cd = ncd;
+            const int gl = ngl;
             const int n = cd.nf & 0xFFFF;
             const int j0 = cd.loc0;
             const bool var = (cd.nf & kVarP) != 0;
-            const int gl = lane < n ? v.gidx[j0 + lane] : 0;
             float2 z[kSmallN], l[kSmallN];
 #pragma unroll
             for (int c = 0; c < kSmallN; ++c) {
@@ -253,28 +266,44 @@ __global__ void __launch_bounds__(kXsWarps * 32) sc_xs_kernel(ScView v, int q) {
                     l[c] = make_float2(0.f, 0.f);
                 }
             }
+            if (s + nw < v.nsmall) {
+                ncd = v.comps[s + nw];
+                ngl = lane < (ncd.nf & 0xFFFF) ? v.gidx[ncd.loc0 + lane] : 0;
+            }
             float2 y0[kSmallN], y1[kSmallN];
 #pragma unroll
             for (int r = 0; r < kSmallN; ++r) y0[r] = y1[r] = make_float2(0.f, 0.f);
             float f[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
-            const float* Ps = v.Ps + cd.poff;
             const float* Pv = v.Pv + cd.poff;
+            if (!var) {
+                // shared operator padded to 8 x 8 (zero past n): lanes 0-15
+                // hold it as float4s, element (c, r) comes from lane 2c + r/4;
+                // padded columns add exact zeros (u is zero there)
+                const float4 pq = lane < 16 ? reinterpret_cast<const float4*>(v.Ps + cd.poff)[lane]
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < kSmallN; ++c) {
-                if (c < n) {
+                for (int c = 0; c < kSmallN; ++c) {
                     const float2 u = make_float2(u_of(z[c].x, l[c].x, inv_rho), u_of(z[c].y, l[c].y, inv_rho));
 #pragma unroll
                     for (int r = 0; r < kSmallN; ++r) {
-                        if (r < n) {
-                            float2 p;
-                            if (!var) {
-                                const float ps = __ldg(Ps + c * n + r);
-                                p = make_float2(ps, ps);
-                            } else {
-                                p = *reinterpret_cast<const float2*>(Pv + (size_t)(c * n + r) * Sp + k0);
+                        const float pe = (r & 3) == 0 ? pq.x : (r & 3) == 1 ? pq.y : (r & 3) == 2 ? pq.z : pq.w;
+                        const float ps = __shfl_sync(0xffffffffu, pe, 2 * c + (r >> 2));
+                        if (c & 1) y1[r] = ffma2(make_float2(ps, ps), u, y1[r]);
+                        else y0[r] = ffma2(make_float2(ps, ps), u, y0[r]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < kSmallN; ++c) {
+                    if (c < n) {
+                        const float2 u = make_float2(u_of(z[c].x, l[c].x, inv_rho), u_of(z[c].y, l[c].y, inv_rho));
+#pragma unroll
+                        for (int r = 0; r < kSmallN; ++r) {
+                            if (r < n) {
+                                const float2 pv = *reinterpret_cast<const float2*>(Pv + (size_t)(c * n + r) * Sp + k0);
+                                if (c & 1) y1[r] = ffma2(pv, u, y1[r]);
+                                else y0[r] = ffma2(pv, u, y0[r]);
                             }
-                            if (c & 1) y1[r] = ffma2(p, u, y1[r]);
-                            else y0[r] = ffma2(p, u, y0[r]);
                         }
                     }
                 }
@@ -332,6 +361,7 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
     float2* us = sdyn;
     float2* zs = sdyn + (size_t)mn * 32;
     float2* ls = sdyn + (size_t)2 * mn * 32;
+    float* psm = reinterpret_cast<float*>(sdyn + (size_t)3 * mn * 32);   // shared operator, mn * mn
     for (int k0 = 2 * lane, pass = 0; k0 < Sp; k0 += 64, ++pass) {
         const bool a0 = v.st[k0].active != 0, a1 = v.st[k0 + 1].active != 0;
         double acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
@@ -339,6 +369,8 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
             const ScComp cd = v.comps[s];
             const int n = cd.nf & 0xFFFF;
             const int j0 = cd.loc0;
+            if (!(cd.nf & kVarP))
+                for (int e = threadIdx.x; e < n * n; e += blockDim.x) psm[e] = __ldg(v.Ps + cd.poff + e);
             for (int c = warp; c < n; c += kScWarps) {
                 const int g = v.gidx[j0 + c];
                 const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)g * Sp + k0);
@@ -349,7 +381,6 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
             }
             __syncthreads();
             const bool var = (cd.nf & kVarP) != 0;
-            const float* Ps = v.Ps + cd.poff;
             const float* Pv = v.Pv + cd.poff;
             float f[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};   // FP32 sums within the component
             for (int r = warp; r < n; r += kScWarps) {
@@ -361,7 +392,7 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
                 if (check) xo = *reinterpret_cast<const float2*>(v.X + e);
                 auto pval = [&](int cc) -> float2 {
                     if (!var) {
-                        const float p = __ldg(Ps + cc * n + r);
+                        const float p = psm[cc * n + r];
                         return make_float2(p, p);
                     }
                     return *reinterpret_cast<const float2*>(Pv + (size_t)(cc * n + r) * Sp + k0);
@@ -454,6 +485,11 @@ __global__ void __launch_bounds__(256) sc_cond_kernel(ScView v, int S, cudaGraph
     int mine = 0;
     for (int k = threadIdx.x; k < S; k += blockDim.x) mine += v.st[k].active;
     atomicAdd(&running, mine);
+    for (int w = threadIdx.x; w < v.Sp / 32; w += blockDim.x) {
+        uint32_t m = 0;
+        for (int b = 0; b < 32; ++b) m |= (uint32_t)(v.st[32 * w + b].active != 0) << b;
+        v.amask[w] = m;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         ScCtl* ctl = v.ctl;
@@ -490,6 +526,7 @@ struct opf_scenarios {
     opf::ScView view{};
     opf::ScCtl* ctl_host = nullptr;  // pinned
     opf::ScState* st_host = nullptr; // pinned, S entries
+    uint32_t* am_host = nullptr;     // pinned, Sp / 32 words
     bool cold = true;
     int graph_K = -1;
     cudaGraph_t graph = nullptr;
@@ -514,7 +551,10 @@ struct ScArena {
     }
 };
 
-size_t sc_x_smem(int maxn) { return (size_t)3 * std::max(1, maxn) * 32 * sizeof(float2); }
+size_t sc_x_smem(int maxn) {
+    const size_t m = (size_t)std::max(1, maxn);
+    return 3 * m * 32 * sizeof(float2) + ((m * m * sizeof(float) + 15) & ~size_t(15));
+}
 
 struct DevGuard {
     int prev = -1;
@@ -526,6 +566,17 @@ struct DevGuard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+// The active-scenario bitmask from the host copy of the states.
+void upload_mask(opf_scenarios* sc, cudaStream_t s) {
+    for (int w = 0; w < sc->Sp / 32; ++w) {
+        uint32_t m = 0;
+        for (int b = 0; b < 32; ++b) m |= (uint32_t)(sc->st_host[32 * w + b].active != 0) << b;
+        sc->am_host[w] = m;
+    }
+    SC_CUDA(cudaMemcpyAsync(sc->view.amask, sc->am_host, (size_t)(sc->Sp / 32) * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, s));
+}
 
 void build_graph(opf_scenarios* sc, int K) {
     if (sc->exec) cudaGraphExecDestroy(sc->exec);
@@ -547,7 +598,7 @@ void build_graph(opf_scenarios* sc, int K) {
     SC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     SC_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const ScView v = sc->view;
-    const int zblocks = (int)(((size_t)sc->ng * 32 + 255) / 256);
+    const int zblocks = (int)(((size_t)sc->ng * 16 + 255) / 256);
     for (int q = 0; q < K; ++q) {
         sc_z_kernel<<<zblocks, 256, 0, cs>>>(v, q);
         sc_xs_kernel<<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
@@ -645,9 +696,16 @@ opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* li
                     const Operator& o = lops[std::min(k, S - 1)][li];
                     for (int e = 0; e < n * n; ++e) Pv[cd.poff + (size_t)e * Sp + k] = (float)o.P[e];
                 }
+            } else if (n <= kSmallN) {
+                // 8 x 8, column-major, zero past n (16-byte aligned block)
+                cd.poff = (int32_t)Ps.size();
+                Ps.resize(Ps.size() + kSmallN * kSmallN, 0.f);
+                for (int c = 0; c < n; ++c)
+                    for (int r = 0; r < n; ++r) Ps[cd.poff + c * kSmallN + r] = (float)ops[s].P[(size_t)c * n + r];
             } else {
                 cd.poff = (int32_t)Ps.size();
                 for (int e = 0; e < n * n; ++e) Ps.push_back((float)ops[s].P[e]);
+                while (Ps.size() % 4) Ps.push_back(0.f);
             }
             if (varB) {
                 flags |= kVarB;
@@ -705,7 +763,7 @@ opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* li
         const size_t o_W = a.take<float>(per), o_L = a.take<float>(per), o_X = a.take<float>(per);
         const size_t o_Z = a.take<float>((size_t)K.ng * Sp);
         const size_t o_part = a.take<double>((size_t)sc->nctas * 5 * Sp);
-        const size_t o_st = a.take<ScState>(Sp), o_ctl = a.take<ScCtl>(1);
+        const size_t o_st = a.take<ScState>(Sp), o_ctl = a.take<ScCtl>(1), o_am = a.take<uint32_t>(Sp / 32);
         sc->bytes = (a.off + 255) & ~size_t(255);
         SC_CUDA(cudaMalloc((void**)&sc->buf, sc->bytes));
         char* d = sc->buf;
@@ -733,6 +791,7 @@ opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* li
         v.W = (float*)(d + o_W); v.L = (float*)(d + o_L); v.X = (float*)(d + o_X); v.Z = (float*)(d + o_Z);
         v.partials = (double*)(d + o_part);
         v.st = (ScState*)(d + o_st);
+        v.amask = (uint32_t*)(d + o_am);
         v.ctl = (ScCtl*)(d + o_ctl);
         v.ncomp = ncomp; v.nl = K.nl; v.ng = K.ng; v.Sp = Sp; v.nctas = sc->nctas; v.maxn = sc->maxn;
         v.nsmall = nsmall; v.nctas_s = nctas_s;
@@ -741,6 +800,7 @@ opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* li
         SC_CUDA(cudaFuncSetAttribute(sc_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
         SC_CUDA(cudaMallocHost((void**)&sc->ctl_host, sizeof(ScCtl)));
         SC_CUDA(cudaMallocHost((void**)&sc->st_host, (size_t)Sp * sizeof(ScState)));
+        SC_CUDA(cudaMallocHost((void**)&sc->am_host, (size_t)(Sp / 32) * sizeof(uint32_t)));
         std::memset(sc->ctl_host, 0, sizeof(ScCtl));
         std::memset(sc->st_host, 0, (size_t)Sp * sizeof(ScState));
         SC_CUDA(cudaEventCreateWithFlags(&sc->done, cudaEventDisableTiming));
@@ -760,6 +820,7 @@ void scenarios_destroy(opf_scenarios* sc) {
     if (sc->buf) cudaFree(sc->buf);
     if (sc->ctl_host) cudaFreeHost(sc->ctl_host);
     if (sc->st_host) cudaFreeHost(sc->st_host);
+    if (sc->am_host) cudaFreeHost(sc->am_host);
     delete sc;
 }
 
@@ -790,6 +851,7 @@ void scenarios_solve(opf_scenarios* sc, const opf_params& prm, cudaStream_t s, o
     }
     SC_CUDA(cudaMemcpyAsync(sc->view.ctl, sc->ctl_host, sizeof(ScCtl), cudaMemcpyHostToDevice, s));
     SC_CUDA(cudaMemcpyAsync(sc->view.st, sc->st_host, (size_t)Sp * sizeof(ScState), cudaMemcpyHostToDevice, s));
+    upload_mask(sc, s);
     if (!prm.warm_start || sc->cold) {
         sc_init_kernel<<<4 * 148, 256, 0, s>>>(sc->view);
         SC_CUDA(cudaGetLastError());
@@ -841,12 +903,13 @@ void scenarios_profile(opf_scenarios* sc, const opf_params& prm, int reps, cudaS
     }
     SC_CUDA(cudaMemcpyAsync(sc->view.ctl, sc->ctl_host, sizeof(ScCtl), cudaMemcpyHostToDevice, s));
     SC_CUDA(cudaMemcpyAsync(sc->view.st, sc->st_host, (size_t)sc->Sp * sizeof(ScState), cudaMemcpyHostToDevice, s));
+    upload_mask(sc, s);
     const ScView v = sc->view;
     sc_init_kernel<<<4 * 148, 256, 0, s>>>(v);
     cudaEvent_t e0, e1;
     SC_CUDA(cudaEventCreate(&e0));
     SC_CUDA(cudaEventCreate(&e1));
-    const int zblocks = (int)(((size_t)sc->ng * 32 + 255) / 256);
+    const int zblocks = (int)(((size_t)sc->ng * 16 + 255) / 256);
     const size_t xsm = sc_x_smem(sc->maxn);
     auto timeit = [&](auto&& launch) {
         launch();
