@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
     float2* us = sdyn;
     float2* zs = sdyn + (size_t)mn * 32;
     float2* ls = sdyn + (size_t)2 * mn * 32;
-    float* psm = reinterpret_cast<float*>(sdyn + (size_t)3 * mn * 32);   // shared operator, mn * mn
+    float2* bbs = sdyn + (size_t)3 * mn * 32;
+    float* psm = reinterpret_cast<float*>(sdyn + (size_t)4 * mn * 32);   // shared operator, mn * mn
     for (int k0 = 2 * lane, pass = 0; k0 < Sp; k0 += 64, ++pass) {
         const bool a0 = v.st[k0].active != 0, a1 = v.st[k0 + 1].active != 0;
         double acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
@@ -375,8 +376,12 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
                 const int g = v.gidx[j0 + c];
                 const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)g * Sp + k0);
                 const float2 l = *reinterpret_cast<const float2*>(v.L + (size_t)(j0 + c) * Sp + k0);
+                float2 bv;
+                if (cd.nf & kVarB) bv = *reinterpret_cast<const float2*>(v.bv + (size_t)(cd.boff + c) * Sp + k0);
+                else bv = make_float2(v.bs[cd.boff + c], v.bs[cd.boff + c]);
                 zs[c * 32 + lane] = z;
                 ls[c * 32 + lane] = l;
+                bbs[c * 32 + lane] = bv;
                 us[c * 32 + lane] = make_float2(u_of(z.x, l.x, inv_rho), u_of(z.y, l.y, inv_rho));
             }
             __syncthreads();
@@ -385,29 +390,49 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
             float f[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};   // FP32 sums within the component
             for (int r = warp; r < n; r += kScWarps) {
                 const size_t e = (size_t)(j0 + r) * Sp + k0;
-                float2 bb;
-                if (cd.nf & kVarB) bb = *reinterpret_cast<const float2*>(v.bv + (size_t)(cd.boff + r) * Sp + k0);
-                else bb = make_float2(v.bs[cd.boff + r], v.bs[cd.boff + r]);
+                const float2 bb = bbs[r * 32 + lane];
                 float2 xo = make_float2(0.f, 0.f);
                 if (check) xo = *reinterpret_cast<const float2*>(v.X + e);
-                auto pval = [&](int cc) -> float2 {
-                    if (!var) {
-                        const float p = psm[cc * n + r];
-                        return make_float2(p, p);
-                    }
-                    return *reinterpret_cast<const float2*>(Pv + (size_t)(cc * n + r) * Sp + k0);
-                };
                 float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
-                if (n <= 32) {
-                    int cc = 0;
-                    for (; cc + 1 < n; cc += 2) {
-                        const float2 p0 = pval(cc), p1 = pval(cc + 1);
-                        y0 = ffma2(p0, us[cc * 32 + lane], y0);
-                        y1 = ffma2(p1, us[(cc + 1) * 32 + lane], y1);
+                if (!var) {
+                    const float* pc = psm + r;              // column cc at pc[cc * n]
+                    if (n <= 32) {
+                        int cc = 0;
+#pragma unroll 4
+                        for (; cc + 1 < n; cc += 2) {
+                            const float p0 = pc[cc * n], p1 = pc[(cc + 1) * n];
+                            y0 = ffma2(make_float2(p0, p0), us[cc * 32 + lane], y0);
+                            y1 = ffma2(make_float2(p1, p1), us[(cc + 1) * 32 + lane], y1);
+                        }
+                        if (cc < n) {
+                            const float p0 = pc[cc * n];
+                            y0 = ffma2(make_float2(p0, p0), us[cc * 32 + lane], y0);
+                        }
+                    } else {
+#pragma unroll 4
+                        for (int cc = 0; cc < n; ++cc) {
+                            const float p0 = pc[cc * n];
+                            y0 = ffma2(make_float2(p0, p0), us[cc * 32 + lane], y0);
+                        }
                     }
-                    if (cc < n) y0 = ffma2(pval(cc), us[cc * 32 + lane], y0);
                 } else {
-                    for (int cc = 0; cc < n; ++cc) y0 = ffma2(pval(cc), us[cc * 32 + lane], y0);
+                    const float* pc = Pv + (size_t)r * Sp + k0;   // column cc at pc[cc * n * Sp]
+                    const size_t cs = (size_t)n * Sp;
+                    if (n <= 32) {
+                        int cc = 0;
+#pragma unroll 4
+                        for (; cc + 1 < n; cc += 2) {
+                            const float2 p0 = *reinterpret_cast<const float2*>(pc + cc * cs);
+                            const float2 p1 = *reinterpret_cast<const float2*>(pc + (cc + 1) * cs);
+                            y0 = ffma2(p0, us[cc * 32 + lane], y0);
+                            y1 = ffma2(p1, us[(cc + 1) * 32 + lane], y1);
+                        }
+                        if (cc < n) y0 = ffma2(*reinterpret_cast<const float2*>(pc + cc * cs), us[cc * 32 + lane], y0);
+                    } else {
+#pragma unroll 4
+                        for (int cc = 0; cc < n; ++cc)
+                            y0 = ffma2(*reinterpret_cast<const float2*>(pc + cc * cs), us[cc * 32 + lane], y0);
+                    }
                 }
                 const float2 z = zs[r * 32 + lane], l = ls[r * 32 + lane];
                 const float xn0 = (y0.x + y1.x) + bb.x, xn1 = (y0.y + y1.y) + bb.y;
@@ -553,7 +578,7 @@ struct ScArena {
 
 size_t sc_x_smem(int maxn) {
     const size_t m = (size_t)std::max(1, maxn);
-    return 3 * m * 32 * sizeof(float2) + ((m * m * sizeof(float) + 15) & ~size_t(15));
+    return 4 * m * 32 * sizeof(float2) + ((m * m * sizeof(float) + 15) & ~size_t(15));
 }
 
 struct DevGuard {
@@ -599,10 +624,21 @@ void build_graph(opf_scenarios* sc, int K) {
     SC_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const ScView v = sc->view;
     const int zblocks = (int)(((size_t)sc->ng * 16 + 255) / 256);
+    // the two local-update kernels depend only on the global update and
+    // write disjoint locals: they run as parallel branches of the body
+    cudaStream_t cs2;
+    SC_CUDA(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+    cudaEvent_t ev_z, ev_x;
+    SC_CUDA(cudaEventCreateWithFlags(&ev_z, cudaEventDisableTiming));
+    SC_CUDA(cudaEventCreateWithFlags(&ev_x, cudaEventDisableTiming));
     for (int q = 0; q < K; ++q) {
         sc_z_kernel<<<zblocks, 256, 0, cs>>>(v, q);
+        cudaEventRecord(ev_z, cs);
+        cudaStreamWaitEvent(cs2, ev_z, 0);
+        sc_x_kernel<<<v.nctas - v.nctas_s, kScWarps * 32, sc_x_smem(sc->maxn), cs2>>>(v, q);
+        cudaEventRecord(ev_x, cs2);
         sc_xs_kernel<<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
-        sc_x_kernel<<<v.nctas - v.nctas_s, kScWarps * 32, sc_x_smem(sc->maxn), cs>>>(v, q);
+        cudaStreamWaitEvent(cs, ev_x, 0);
     }
     sc_fin_kernel<<<sc->S, 256, 0, cs>>>(v);
     sc_cond_kernel<<<1, 256, 0, cs>>>(v, sc->S, h, 1);
@@ -610,6 +646,9 @@ void build_graph(opf_scenarios* sc, int K) {
     cudaGraph_t captured;
     const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
+    cudaStreamDestroy(cs2);
+    cudaEventDestroy(ev_z);
+    cudaEventDestroy(ev_x);
     if (le != cudaSuccess || ee != cudaSuccess)
         throw Error(OPF_ERR_CUDA, std::string("scenario graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ee));
     SC_CUDA(cudaGraphInstantiate(&sc->exec, sc->graph, 0));
@@ -733,6 +772,12 @@ opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* li
                 dcomps.push_back(comps[s]);
                 maxn_large = std::max(maxn_large, comps[s].nf & 0xFFFF);
             }
+        // largest first: CTA b takes components b, b + G, ... (balanced loads)
+        std::stable_sort(dcomps.begin() + nsmall, dcomps.end(), [](const ScComp& x, const ScComp& y) {
+            const int nx = x.nf & 0xFFFF, ny = y.nf & 0xFFFF;
+            const int cx = nx * nx * ((x.nf & kVarP) ? 8 : 1), cy = ny * ny * ((y.nf & kVarP) ? 8 : 1);
+            return cx > cy;
+        });
         comps.swap(dcomps);
         sc->maxn = maxn_large;
         // copies of each global in the CSR order of the single-instance engines
