@@ -217,6 +217,20 @@ int32_t opf_problem_create_ex(const opf_bus* buses, int32_t n_bus,
 
 int32_t opf_get_dims(const opf_problem* p, opf_dims* dims);
 
+/* New parameters for in-service lines of an uploaded problem: records[k]
+ * replaces line line_idx[k] (impedances r, x; shunts; taps; flow bounds).
+ * Ends, phases and the service state must not change (a topology change
+ * needs a new problem, see opf_server_submit's warm start), else
+ * OPF_ERR_INVALID_ARG before anything changes.  The touched components'
+ * operators of Eq. (closed_2) are recomputed on the device in FP64
+ * (Cholesky of A_s A_s^T; the rows of a line are of full rank) and written
+ * into both precisions; the iterate and duals are kept, so a following
+ * solve with warm_start continues from them.  OPF_ERR_STATE before upload.
+ * The paper precomputes once per topology; this is the incremental update
+ * for parameter changes (tap changers, ratings) at high rate.            */
+int32_t opf_update_lines(opf_problem* p, const int32_t* line_idx, const opf_line* records, int32_t count,
+                         void* stream);
+
 /* Copy the packed problem to the current CUDA device on `stream`.  With
  * device_arena != NULL the handle carves all its device buffers out of that
  * caller-owned region (>= dims.device_bytes bytes, 256-byte aligned; it must

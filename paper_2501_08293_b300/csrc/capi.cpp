@@ -4,10 +4,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "problem.hpp"
 
@@ -34,6 +36,8 @@ void scenarios_solve(opf_scenarios* sc, const opf_params& prm, cudaStream_t s, o
 void scenarios_get_state(const opf_scenarios* sc, int k, double* xg, double* xl, double* lam, cudaStream_t s);
 void scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* n_local, int64_t* device_bytes);
 void scenarios_profile(opf_scenarios* sc, const opf_params& prm, int reps, cudaStream_t s, double* us);
+void device_reprecompute(opf_problem* p, const std::vector<int>& comps, cudaStream_t s);
+void device_update_bounds(opf_problem* p, int g0, int g1, cudaStream_t s);
 }  // namespace opf
 
 namespace {
@@ -154,6 +158,58 @@ int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus, const opf_line* 
                            const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
                            opf_problem** out) {
     return opf_problem_create_ex(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load, nullptr, out);
+}
+
+int32_t opf_update_lines(opf_problem* p, const int32_t* line_idx, const opf_line* records, int32_t count,
+                         void* stream) {
+    return guarded([&]() -> int32_t {
+        if (!p || (count > 0 && (!line_idx || !records)) || count < 0)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        opf::Model& M = p->model;
+        // component of each line (canonical order)
+        std::vector<int> line_comp(M.n_line, -1);
+        for (size_t c = 0; c < M.comps.size(); ++c)
+            if (M.comps[c].kind == opf::COMP_LINE) line_comp[M.comps[c].index] = (int)c;
+        // validate everything before changing anything
+        std::vector<opf::Component> fresh;
+        fresh.reserve(count);
+        for (int k = 0; k < count; ++k) {
+            const int e = line_idx[k];
+            if (e < 0 || e >= M.n_line || line_comp[e] < 0)
+                throw opf::Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": no in-service line there");
+            fresh.push_back(opf::line_update(M, records[k], e));
+            if (fresh.back().gvars != M.comps[line_comp[e]].gvars)
+                throw opf::Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": structure differs");
+        }
+        if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "update before upload");
+        std::vector<int> comps;
+        for (int k = 0; k < count; ++k) {
+            const int e = line_idx[k];
+            const int c = line_comp[e];
+            M.comps[c].A = fresh[k].A;
+            M.comps[c].b = fresh[k].b;
+            M.comps[c].m = fresh[k].m;
+            comps.push_back(c);
+            // flow bounds: p_ij, q_ij, p_ji, q_ji on the line's phases (contiguous globals)
+            const opf_line& L = records[k];
+            int g0 = INT32_MAX, g1 = -1;
+            for (int ph = 0; ph < 3; ++ph) {
+                if (M.pij_idx[3 * e + ph] < 0) continue;
+                M.lo[M.pij_idx[3 * e + ph]] = L.p_lo[ph]; M.hi[M.pij_idx[3 * e + ph]] = L.p_hi[ph];
+                M.lo[M.pji_idx[3 * e + ph]] = L.p_lo[ph]; M.hi[M.pji_idx[3 * e + ph]] = L.p_hi[ph];
+                M.lo[M.qij_idx[3 * e + ph]] = L.q_lo[ph]; M.hi[M.qij_idx[3 * e + ph]] = L.q_hi[ph];
+                M.lo[M.qji_idx[3 * e + ph]] = L.q_lo[ph]; M.hi[M.qji_idx[3 * e + ph]] = L.q_hi[ph];
+                for (int32_t gi : {M.pij_idx[3 * e + ph], M.pji_idx[3 * e + ph], M.qij_idx[3 * e + ph],
+                                   M.qji_idx[3 * e + ph]}) {
+                    g0 = std::min(g0, (int)gi);
+                    g1 = std::max(g1, (int)gi + 1);
+                }
+            }
+            opf::device_update_bounds(p, g0, g1, (cudaStream_t)stream);
+        }
+        opf::device_reprecompute(p, comps, (cudaStream_t)stream);
+        return OPF_OK;
+    });
 }
 
 int32_t opf_get_dims(const opf_problem* p, opf_dims* d) {

@@ -99,6 +99,7 @@ struct Packed {
     std::vector<double> invk, cik;       // 1/k_i, c_i/k_i
     std::vector<double> bbar, xl0;       // device order
     std::vector<double> P;               // operator elements, tile layout
+    std::vector<int32_t> comp_tile;      // tile holding each (canonical) component
     int64_t mat_elems = 0;
     int64_t sum_n2 = 0;
     int max_n = 0;
@@ -113,6 +114,11 @@ struct Packed {
 Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
                   const opf_gen* gens, int ng, const opf_load* loads, int nd);
 Operator make_operator(const Component& c);
+// Line component of Eq. (power_flow_eqns) for in-service line e on the
+// global indices of M; line_update validates a new record for line e (same
+// ends, phases and service state) and returns its component.
+Component line_component(const Model& M, const opf_line& L, int e);
+Component line_update(const Model& M, const opf_line& L, int e);
 Packed pack(const Model& m, const std::vector<Operator>& ops, int nblocks_hint = 0);
 
 }  // namespace opf

@@ -59,6 +59,92 @@ struct RowSet {
 
 }  // namespace
 
+// Line component of Eq. (power_flow_eqns) for in-service line e, on the
+// global indices already assigned in M.
+Component line_component(const Model& M, const opf_line& L, int e) {
+    int ph[3], np;
+    Component C;
+    C.kind = COMP_LINE; C.index = e;
+    phases(L.phases, ph, &np);
+    const int i = L.from_bus, j = L.to_bus;
+    for (const std::vector<int32_t>* t : {&M.pij_idx, &M.qij_idx, &M.pji_idx, &M.qji_idx})
+        for (int a = 0; a < np; ++a) C.gvars.push_back((*t)[3 * e + ph[a]]);
+    for (int a = 0; a < np; ++a) C.gvars.push_back(M.w_idx[3 * i + ph[a]]);
+    for (int a = 0; a < np; ++a) C.gvars.push_back(M.w_idx[3 * j + ph[a]]);
+    // M^p, M^q (Section II-A) on phases a, b, c; sub-block read by phase.
+    double Mp[3][3], Mq[3][3];
+    const double* r = L.r;
+    const double* x = L.x;
+    auto R_ = [&](int u, int v) { return r[3 * u + v]; };
+    auto X_ = [&](int u, int v) { return x[3 * u + v]; };
+    // diagonal
+    for (int u = 0; u < 3; ++u) { Mp[u][u] = -2.0 * R_(u, u); Mq[u][u] = -2.0 * X_(u, u); }
+    // off-diagonal: sign s = +1 where the paper writes r - sqrt3 x (Mp) / x + sqrt3 r (Mq)
+    // pairs (1,2),(2,3),(3,1) take "- sqrt3 x"; pairs (1,3),(2,1),(3,2) take "+ sqrt3 x"
+    const int lag[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    const int lead[3][2] = {{0, 2}, {1, 0}, {2, 1}};
+    for (auto& pq : lag) {
+        int u = pq[0], v = pq[1];
+        Mp[u][v] = R_(u, v) - kSqrt3 * X_(u, v);
+        Mq[u][v] = X_(u, v) + kSqrt3 * R_(u, v);
+    }
+    for (auto& pq : lead) {
+        int u = pq[0], v = pq[1];
+        Mp[u][v] = R_(u, v) + kSqrt3 * X_(u, v);
+        Mq[u][v] = X_(u, v) - kSqrt3 * R_(u, v);
+    }
+    RowSet Rs(C.gvars);
+    for (int a = 0; a < np; ++a) {
+        const int p = ph[a];
+        const int32_t wi = M.w_idx[3 * i + p], wj = M.w_idx[3 * j + p];
+        int r1 = Rs.row(0.0);     // powerloss-1
+        Rs.add(r1, M.pij_idx[3 * e + p], 1.0);
+        Rs.add(r1, M.pji_idx[3 * e + p], 1.0);
+        Rs.add(r1, wi, -L.g_fr[p]);
+        Rs.add(r1, wj, -L.g_to[p]);
+        int r2 = Rs.row(0.0);     // powerloss-2
+        Rs.add(r2, M.qij_idx[3 * e + p], 1.0);
+        Rs.add(r2, M.qji_idx[3 * e + p], 1.0);
+        Rs.add(r2, wi, L.b_fr[p]);
+        Rs.add(r2, wj, L.b_to[p]);
+        int r3 = Rs.row(0.0);     // voltage_mag_diff
+        Rs.add(r3, wi, 1.0);
+        Rs.add(r3, wj, -L.tap[p]);
+        for (int bb = 0; bb < np; ++bb) {
+            const int s = ph[bb];
+            const int32_t wis = M.w_idx[3 * i + s];
+            Rs.add(r3, M.pij_idx[3 * e + s], Mp[p][s]);
+            Rs.add(r3, wis, -Mp[p][s] * L.g_fr[s]);
+            Rs.add(r3, M.qij_idx[3 * e + s], Mq[p][s]);
+            Rs.add(r3, wis, Mq[p][s] * L.b_fr[s]);
+        }
+    }
+    C.m = Rs.m; C.A = std::move(Rs.A); C.b = std::move(Rs.b);
+    return C;
+}
+
+Component line_update(const Model& M, const opf_line& L, int e) {
+    if (e < 0 || e >= M.n_line) throw Error(OPF_ERR_INVALID_ARG, "line index out of range");
+    if (L.from_bus != M.line_from[e] || L.to_bus != M.line_to[e])
+        throw Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": ends differ from the problem's");
+    if (!L.in_service) throw Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": out of service in the update");
+    for (int p = 0; p < 3; ++p) {
+        const bool here = M.pij_idx[3 * e + p] >= 0;
+        if (here != (((L.phases >> p) & 1u) != 0))
+            throw Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": phases or service state differ");
+        if (!here) continue;
+        check_bounds(L.p_lo[p], L.p_hi[p], "line", e);
+        check_bounds(L.q_lo[p], L.q_hi[p], "line", e);
+        for (double v : {L.g_fr[p], L.b_fr[p], L.g_to[p], L.b_to[p], L.tap[p]}) check_finite(v, "line", e);
+        for (int q = 0; q < 3; ++q)
+            if ((L.phases >> q) & 1u) {
+                check_finite(L.r[3 * p + q], "line", e);
+                check_finite(L.x[3 * p + q], "line", e);
+            }
+    }
+    return line_component(M, L, e);
+}
+
 Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
                   const opf_gen* gens, int ng, const opf_load* loads, int nd) {
     if (nb <= 0 || !buses) throw Error(OPF_ERR_INVALID_ARG, "no buses");
@@ -229,66 +315,8 @@ Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
 
     // ---- line components, Eq. (power_flow_eqns)
     for (int e = 0; e < nl; ++e) {
-        const opf_line& L = lines[e];
-        if (!L.in_service) continue;
-        Component C;
-        C.kind = COMP_LINE; C.index = e;
-        phases(L.phases, ph, &np);
-        const int i = L.from_bus, j = L.to_bus;
-        for (const std::vector<int32_t>* t : {&M.pij_idx, &M.qij_idx, &M.pji_idx, &M.qji_idx})
-            for (int a = 0; a < np; ++a) C.gvars.push_back((*t)[3 * e + ph[a]]);
-        for (int a = 0; a < np; ++a) C.gvars.push_back(M.w_idx[3 * i + ph[a]]);
-        for (int a = 0; a < np; ++a) C.gvars.push_back(M.w_idx[3 * j + ph[a]]);
-        // M^p, M^q (Section II-A) on phases a, b, c; sub-block read by phase.
-        double Mp[3][3], Mq[3][3];
-        const double* r = L.r;
-        const double* x = L.x;
-        auto R_ = [&](int u, int v) { return r[3 * u + v]; };
-        auto X_ = [&](int u, int v) { return x[3 * u + v]; };
-        // diagonal
-        for (int u = 0; u < 3; ++u) { Mp[u][u] = -2.0 * R_(u, u); Mq[u][u] = -2.0 * X_(u, u); }
-        // off-diagonal: sign s = +1 where the paper writes r - sqrt3 x (Mp) / x + sqrt3 r (Mq)
-        // pairs (1,2),(2,3),(3,1) take "- sqrt3 x"; pairs (1,3),(2,1),(3,2) take "+ sqrt3 x"
-        const int lag[3][2] = {{0, 1}, {1, 2}, {2, 0}};
-        const int lead[3][2] = {{0, 2}, {1, 0}, {2, 1}};
-        for (auto& pq : lag) {
-            int u = pq[0], v = pq[1];
-            Mp[u][v] = R_(u, v) - kSqrt3 * X_(u, v);
-            Mq[u][v] = X_(u, v) + kSqrt3 * R_(u, v);
-        }
-        for (auto& pq : lead) {
-            int u = pq[0], v = pq[1];
-            Mp[u][v] = R_(u, v) + kSqrt3 * X_(u, v);
-            Mq[u][v] = X_(u, v) - kSqrt3 * R_(u, v);
-        }
-        RowSet Rs(C.gvars);
-        for (int a = 0; a < np; ++a) {
-            const int p = ph[a];
-            const int32_t wi = M.w_idx[3 * i + p], wj = M.w_idx[3 * j + p];
-            int r1 = Rs.row(0.0);     // powerloss-1
-            Rs.add(r1, M.pij_idx[3 * e + p], 1.0);
-            Rs.add(r1, M.pji_idx[3 * e + p], 1.0);
-            Rs.add(r1, wi, -L.g_fr[p]);
-            Rs.add(r1, wj, -L.g_to[p]);
-            int r2 = Rs.row(0.0);     // powerloss-2
-            Rs.add(r2, M.qij_idx[3 * e + p], 1.0);
-            Rs.add(r2, M.qji_idx[3 * e + p], 1.0);
-            Rs.add(r2, wi, L.b_fr[p]);
-            Rs.add(r2, wj, L.b_to[p]);
-            int r3 = Rs.row(0.0);     // voltage_mag_diff
-            Rs.add(r3, wi, 1.0);
-            Rs.add(r3, wj, -L.tap[p]);
-            for (int bb = 0; bb < np; ++bb) {
-                const int s = ph[bb];
-                const int32_t wis = M.w_idx[3 * i + s];
-                Rs.add(r3, M.pij_idx[3 * e + s], Mp[p][s]);
-                Rs.add(r3, wis, -Mp[p][s] * L.g_fr[s]);
-                Rs.add(r3, M.qij_idx[3 * e + s], Mq[p][s]);
-                Rs.add(r3, wis, Mq[p][s] * L.b_fr[s]);
-            }
-        }
-        C.m = Rs.m; C.A = std::move(Rs.A); C.b = std::move(Rs.b);
-        M.comps.push_back(std::move(C));
+        if (!lines[e].in_service) continue;
+        M.comps.push_back(line_component(M, lines[e], e));
     }
 
     // ---- load components, Eq. (volt_load_model)

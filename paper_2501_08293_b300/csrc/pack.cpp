@@ -183,6 +183,7 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
     }
     K.nblocks = (int)chunk_start.size() - 1;
 
+    K.comp_tile.assign(K.ncomp, -1);
     K.dev_of_canon.assign(K.nl, -1);
     K.canon_of_dev.assign(K.nl, -1);
     K.meta.assign(K.nl, 0);
@@ -305,6 +306,7 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
                 continue;
             }
             const size_t w = (size_t)lw;
+            for (int s2 : warps[w]) K.comp_tile[s2] = (int32_t)K.tiles.size();
             mat = (mat + 3) & ~int64_t(3);   // 32-byte aligned tile start (f64)
             if (mat > INT32_MAX) throw Error(OPF_ERR_INVALID_ARG, "problem too large");
             Tile t;

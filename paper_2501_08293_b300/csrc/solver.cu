@@ -1201,6 +1201,95 @@ __global__ void warm_gather_kernel(const int32_t* __restrict__ map, const T* __r
     }
 }
 
+// ------------------------------------------------------- re-precompute
+// Device FP64 precompute of Eq. (closed_2) for components whose rows
+// changed (a line's impedances, shunts or taps): with the Cholesky factor L
+// of A A^T (A of full row rank), W = L^-1 A, P = I - W^T W (= -Abar) and
+// bbar = W^T L^-1 b.  One warp per component; the result goes into both
+// precisions' packed operators and bbar, and a dense copy for the host.
+struct RpDesc {
+    int32_t m, n, aoff, boff;      // rows, locals, offsets into the A (row-major) and b buffers
+    int32_t mat0, L, base, big;    // destination tile: first element, lanes, lane base, big flag
+    int32_t loc0, outoff, woff, _pad;   // device index of local 0; dense output; scratch offset
+};
+
+__global__ void __launch_bounds__(32) reprecompute_kernel(const RpDesc* __restrict__ ds, const double* __restrict__ A,
+                                                         const double* __restrict__ bv, double* scratch, double* P64,
+                                                         float* P32, double* bb64, float* bb32, double* out, int* err) {
+    const RpDesc d = ds[blockIdx.x];
+    const int lane = threadIdx.x, m = d.m, n = d.n;
+    double* G = scratch + d.woff;                  // m x m, lower triangle
+    double* W = G + m * m;                         // m x n
+    double* y = W + (size_t)m * n;                 // m
+    const double* Ar = A + d.aoff;
+    // G = A A^T (lower triangle)
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, k = e % m;
+        if (k > i) continue;
+        double s = 0;
+        for (int c = 0; c < n; ++c) s += Ar[i * n + c] * Ar[k * n + c];
+        G[i * m + k] = s;
+    }
+    __syncwarp();
+    double gmax = 0;
+    for (int i = 0; i < m; ++i) gmax = fmax(gmax, G[i * m + i]);
+    // right-looking Cholesky
+    for (int k = 0; k < m; ++k) {
+        if (lane == 0) {
+            const double dk = G[k * m + k];
+            if (!(dk > 1e-13 * gmax)) atomicExch(err, 1);   // rank deficient: the host path is needed
+            G[k * m + k] = sqrt(fmax(dk, 1e-300));
+        }
+        __syncwarp();
+        const double lkk = G[k * m + k];
+        for (int i = k + 1 + lane; i < m; i += 32) G[i * m + k] /= lkk;
+        __syncwarp();
+        for (int e = lane; e < m * m; e += 32) {
+            const int i = e / m, j = e % m;
+            if (j > k && j <= i) G[i * m + j] -= G[i * m + k] * G[j * m + k];
+        }
+        __syncwarp();
+    }
+    // W = L^-1 A (columns in parallel), y = L^-1 b
+    for (int c = lane; c < n; c += 32)
+        for (int i = 0; i < m; ++i) {
+            double s = Ar[i * n + c];
+            for (int p = 0; p < i; ++p) s -= G[i * m + p] * W[p * n + c];
+            W[i * n + c] = s / G[i * m + i];
+        }
+    if (lane == 0)
+        for (int i = 0; i < m; ++i) {
+            double s = bv[d.boff + i];
+            for (int p = 0; p < i; ++p) s -= G[i * m + p] * y[p];
+            y[i] = s / G[i * m + i];
+        }
+    __syncwarp();
+    // P = I - W^T W (one triangle, mirrored: exactly symmetric), bbar = W^T y
+    for (int e = lane; e < n * n; e += 32) {
+        const int c = e / n, r = e % n;
+        if (r < c) continue;
+        double s = 0;
+        for (int i = 0; i < m; ++i) s += W[i * n + c] * W[i * n + r];
+        const double pv = (c == r ? 1.0 : 0.0) - s;
+        auto put = [&](int cc, int rr) {
+            const size_t at = d.big ? (size_t)d.mat0 + (size_t)cc * n + rr
+                                    : (size_t)d.mat0 + ((size_t)(cc / 4) * d.L + d.base + rr) * 4 + cc % 4;
+            P64[at] = pv;
+            P32[at] = (float)pv;
+            out[d.outoff + cc * n + rr] = pv;
+        };
+        put(c, r);
+        if (r != c) put(r, c);
+    }
+    for (int c = lane; c < n; c += 32) {
+        double s = 0;
+        for (int i = 0; i < m; ++i) s += W[i * n + c] * y[i];
+        bb64[d.loc0 + c] = s;
+        bb32[d.loc0 + c] = (float)s;
+        out[d.outoff + n * n + c] = s;
+    }
+}
+
 // ------------------------------------------------------------ misc kernels
 template <typename T>
 __global__ void init_kernel(View<T> v) {
@@ -2109,6 +2198,94 @@ void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters,
         out[k] = sum / nb;
         out[4 + k] = mx;
     }
+}
+
+// Recompute the operators of components `comps` (whose A, b in p->model were
+// updated) on the device and refresh the host copies in p->ops.
+void device_reprecompute(opf_problem* p, const std::vector<int>& comps, cudaStream_t s) {
+    if (comps.empty()) return;
+    DeviceGuard g(p->device);
+    const Packed& K = p->pk;
+    std::vector<RpDesc> ds;
+    std::vector<double> A, b;
+    int32_t out = 0, wo = 0;
+    for (int c : comps) {
+        const Component& C = p->model.comps[c];
+        const int n = C.n(), m = C.m;
+        if (n == 0 || K.comp_tile[c] < 0) continue;
+        if (m == 0) throw Error(OPF_ERR_INVALID_ARG, "component without rows");
+        const Tile& t = K.tiles[K.comp_tile[c]];
+        const int32_t loc0 = K.dev_of_canon[p->canon_comp_ptr[c]];
+        RpDesc d{};
+        d.m = m; d.n = n;
+        d.aoff = (int32_t)A.size(); d.boff = (int32_t)b.size();
+        d.mat0 = t.mat0; d.L = t.L; d.big = t.big;
+        d.base = t.big ? 0 : (K.meta[loc0] >> 24) & 0x1F;
+        d.loc0 = loc0;
+        d.outoff = out; out += n * n + n;
+        d.woff = wo; wo += m * m + m * n + m;
+        A.insert(A.end(), C.A.begin(), C.A.end());
+        b.insert(b.end(), C.b.begin(), C.b.end());
+        ds.push_back(d);
+    }
+    if (ds.empty()) return;
+    const size_t bd = ds.size() * sizeof(RpDesc), ba = A.size() * 8, bb = b.size() * 8;
+    const size_t bs = (size_t)wo * 8, bo = (size_t)out * 8;
+    const size_t o_d = 0, o_a = (bd + 255) & ~size_t(255), o_b = o_a + ((ba + 255) & ~size_t(255));
+    const size_t o_s = o_b + ((bb + 255) & ~size_t(255)), o_o = o_s + ((bs + 255) & ~size_t(255));
+    const size_t o_e = o_o + ((bo + 255) & ~size_t(255)), total = o_e + 256;
+    char* buf = nullptr;
+    OPF_CUDA(cudaMallocAsync((void**)&buf, total, s));
+    std::vector<double> hout(out);
+    int herr = 0;
+    try {
+        OPF_CUDA(cudaMemcpyAsync(buf + o_d, ds.data(), bd, cudaMemcpyHostToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync(buf + o_a, A.data(), ba, cudaMemcpyHostToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync(buf + o_b, b.data(), bb, cudaMemcpyHostToDevice, s));
+        OPF_CUDA(cudaMemsetAsync(buf + o_e, 0, sizeof(int), s));
+        reprecompute_kernel<<<(unsigned)ds.size(), 32, 0, s>>>(
+            (const RpDesc*)(buf + o_d), (const double*)(buf + o_a), (const double*)(buf + o_b), (double*)(buf + o_s),
+            (double*)p->d64.P, (float*)p->d32.P, (double*)p->d64.bbar, (float*)p->d32.bbar, (double*)(buf + o_o),
+            (int*)(buf + o_e));
+        OPF_CUDA(cudaGetLastError());
+        OPF_CUDA(cudaMemcpyAsync(hout.data(), buf + o_o, bo, cudaMemcpyDeviceToHost, s));
+        OPF_CUDA(cudaMemcpyAsync(&herr, buf + o_e, sizeof(int), cudaMemcpyDeviceToHost, s));
+        OPF_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        cudaFreeAsync(buf, s);
+        throw;
+    }
+    OPF_CUDA(cudaFreeAsync(buf, s));
+    if (herr) throw Error(OPF_ERR_NUMERIC, "re-precompute: a component's rows are rank deficient");
+    size_t k = 0;
+    for (int c : comps) {
+        const Component& C = p->model.comps[c];
+        if (C.n() == 0 || K.comp_tile[c] < 0) continue;
+        const RpDesc& d = ds[k++];
+        Operator& op = p->ops[c];
+        op.n = d.n;
+        op.P.assign(hout.begin() + d.outoff, hout.begin() + d.outoff + (size_t)d.n * d.n);
+        op.bbar.assign(hout.begin() + d.outoff + (size_t)d.n * d.n, hout.begin() + d.outoff + (size_t)d.n * d.n + d.n);
+        op.m_reduced = d.m;
+    }
+}
+
+// Upload the bounds of globals [g0, g1) from p->model to both precisions.
+void device_update_bounds(opf_problem* p, int g0, int g1, cudaStream_t s) {
+    if (g1 <= g0) return;
+    DeviceGuard g(p->device);
+    const Model& M = p->model;
+    const size_t n = (size_t)(g1 - g0);
+    std::vector<float> f(2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        f[i] = (float)M.lo[g0 + i];
+        f[n + i] = (float)M.hi[g0 + i];
+    }
+    OPF_CUDA(cudaMemcpyAsync((double*)p->d64.lo + g0, M.lo.data() + g0, n * 8, cudaMemcpyHostToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync((double*)p->d64.hi + g0, M.hi.data() + g0, n * 8, cudaMemcpyHostToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync((float*)p->d32.lo + g0, f.data(), n * 4, cudaMemcpyHostToDevice, s));
+    OPF_CUDA(cudaMemcpyAsync((float*)p->d32.hi + g0, f.data() + n, n * 4, cudaMemcpyHostToDevice, s));
+    OPF_CUDA(cudaStreamSynchronize(s));
 }
 
 void device_free(opf_problem* p) {

@@ -85,6 +85,7 @@ EXPORTS = {
     "opf_problem_create_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32,
                                           C.POINTER(CreateOptions), C.POINTER(C.c_void_p)]),
     "opf_get_dims": (C.c_int32, [_P, C.POINTER(Dims)]),
+    "opf_update_lines": (C.c_int32, [_P, _I, _P, C.c_int32, _P]),
     "opf_problem_upload": (C.c_int32, [_P, _P, C.c_size_t, _P]),
     "opf_admm_solve": (C.c_int32, [_P, C.POINTER(Params), _P, C.POINTER(Info)]),
     "opf_get_state": (C.c_int32, [_P, _D, _D, _D, _P]),
@@ -272,6 +273,18 @@ class Problem:
         out = np.zeros((self.dims.n_blocks, len(self.CHUNK_STATS)), dtype=np.int32)
         _check(lib.opf_chunk_stats(self._h, out.ctypes.data_as(_I)), "opf_chunk_stats")
         return {k: out[:, i].copy() for i, k in enumerate(self.CHUNK_STATS)}
+
+    def update_lines(self, idx, records, stream=None):
+        """New parameters for in-service lines (same ends, phases, service
+        state); operators recomputed on the device, iterate kept."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        rec = np.ascontiguousarray(records)
+        if rec.dtype != _F.LINE_DTYPE or len(rec) != len(idx):
+            raise TypeError("records must be LINE records, one per index")
+        _check(lib.opf_update_lines(self._h, idx.ctypes.data_as(_I), rec.ctypes.data, len(idx),
+                                    _stream_handle(stream)), "opf_update_lines")
+        for k, e in enumerate(idx):
+            self._arrays[1][e] = rec[k]
 
     def persistent_ok(self, params: Params) -> bool:
         e = C.c_int32()

@@ -150,3 +150,34 @@ def test_scenario_inputs_are_validated_on_the_host(opf):
                                       arrs[2].ctypes.data, len(arrs[2]), loads.ctypes.data, len(f.loads), 0,
                                       C.byref(h))
     assert st == -1
+
+
+def test_line_updates_are_validated_on_the_host(opf):
+    """opf_update_lines checks every record before touching a device: a
+    line that is not in service, other ends or phases are rejected; a valid
+    update of a problem that is not uploaded reports the state."""
+    import ctypes as C
+    f = F.feeder_123(1)
+    p = opf.Problem.from_feeder(f, upload=False)
+    live = int(np.flatnonzero(f.lines["in_service"] == 1)[3])
+    dead = np.flatnonzero(f.lines["in_service"] == 0)
+
+    def call(idx, rec):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        rec = np.ascontiguousarray(rec)
+        return opf.lib.opf_update_lines(p._h, idx.ctypes.data_as(opf._I), rec.ctypes.data, len(idx), None)
+
+    rec = f.lines[[live]].copy()
+    rec["r"] *= 1.1
+    assert call([live], rec) == -7                  # valid, but not uploaded
+    bad = rec.copy(); bad["to_bus"] = (bad["to_bus"] + 1) % len(f.buses)
+    assert call([live], bad) == -1
+    bad = rec.copy(); bad["in_service"] = 0
+    assert call([live], bad) == -1
+    bad = rec.copy(); bad["phases"] = 7 if int(bad["phases"][0]) != 7 else 1
+    assert call([live], bad) == -1
+    bad = rec.copy(); bad["p_lo"] = 1.0; bad["p_hi"] = 0.0
+    assert call([live], bad) == -1
+    if len(dead):
+        assert call([int(dead[0])], f.lines[[int(dead[0])]]) == -1
+    assert call([len(f.lines)], rec) == -1

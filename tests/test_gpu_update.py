@@ -1,0 +1,93 @@
+"""Incremental re-precompute: new impedances, shunts, taps and flow bounds
+for some lines of an uploaded problem, operators recomputed on the device.
+The device operators must equal the host precompute of a problem built with
+the new records, and a warm solve after the update must follow the iterates
+of that fresh problem started from the same state."""
+import numpy as np
+import pytest
+
+from paper_2501_08293_b300 import feeders as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def opf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_08293_b300 import build
+    build.build()
+    from paper_2501_08293_b300 import opf as mod
+    return mod
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1.0))
+
+
+def changed_lines(f, rng, count):
+    live = np.flatnonzero(f.lines["in_service"] == 1)
+    idx = np.sort(rng.choice(live, size=count, replace=False)).astype(np.int32)
+    rec = f.lines[idx].copy()
+    rec["r"] *= rng.uniform(0.8, 1.25, size=(count, 1))
+    rec["x"] *= rng.uniform(0.8, 1.25, size=(count, 1))
+    rec["tap"] = rng.uniform(0.97, 1.03, size=(count, 3))
+    rec["b_fr"] *= 1.1
+    rec["p_hi"] *= 1.2
+    rec["p_lo"] *= 1.2
+    return idx, rec
+
+
+@pytest.mark.parametrize("maker", [lambda: F.feeder_123(1), lambda: F.feeder_8500(2, n_bus=1500)])
+def test_device_operators_match_host_precompute(opf, maker):
+    f = maker()
+    rng = np.random.default_rng(5)
+    idx, rec = changed_lines(f, rng, 12)
+    p = opf.Problem.from_feeder(f)
+    p.update_lines(idx, rec)
+    g = f.copy()
+    g.lines[idx] = rec
+    q = opf.Problem.from_feeder(g, upload=False)
+    st = p.structure()
+    line_comp = {int(e): s for s, (k, e) in enumerate(zip(st["kind"], st["index"])) if k == 1}
+    for e in idx:
+        s = line_comp[int(e)]
+        Pa, ba = p.operator(s)
+        Pb, bb = q.operator(s)
+        assert np.max(np.abs(Pa - Pb)) <= 1e-11 and np.max(np.abs(ba - bb)) <= 1e-11
+        assert np.array_equal(Pa, Pa.T)
+    # untouched components keep their operators
+    s0 = next(s for s, k in enumerate(st["kind"]) if k == 1 and int(st["index"][s]) not in set(idx.tolist()))
+    assert np.array_equal(p.operator(s0)[0], q.operator(s0)[0])
+    p.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_warm_solve_after_update_follows_fresh_problem(opf, prec):
+    f = F.feeder_123(2)
+    rng = np.random.default_rng(9)
+    idx, rec = changed_lines(f, rng, 8)
+    prm = opf.default_params(precision=prec, rho=10.0, criterion=opf.CRIT_NEVER, max_iter=300, check_every=50)
+    a = opf.Problem.from_feeder(f)
+    a.solve(prm)
+    _, xl, lam = a.state()
+    a.update_lines(idx, rec)
+    prm.warm_start = 1
+    a.solve(prm)
+    g = f.copy()
+    g.lines[idx] = rec
+    b = opf.Problem.from_feeder(g)
+    b.set_state(xl, lam)
+    b.solve(prm)
+    tol = 1e-9 if prec == 0 else 1e-5
+    for x, y in zip(a.state(), b.state()):
+        assert rel(x, y) <= tol
+    # and it converges like the fresh problem
+    prm2 = opf.default_params(precision=0, rho=10.0, max_iter=200000, check_every=50, warm_start=1)
+    ia = a.solve(prm2)
+    ib = b.solve(prm2)
+    assert ia.status == ib.status == 0
+    assert abs(ia.objective - ib.objective) <= 1e-6 * abs(ib.objective)
+    a.close()
+    b.close()
