@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--scenario-iters", type=int, default=1000)
     ap.add_argument("--sweep-budget-iters", type=int, default=4_000_000)
+    ap.add_argument("--configs-quick", action="store_true", help="configs workload: small feeders only")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-iters", type=int, default=2000)
     ap.add_argument("--requests", type=int, default=200)
@@ -612,7 +613,9 @@ def run_configs(args):
     13-bus FP64 rho = 100; 123-bus FP64 and FP32 (rho = 10); the 8500-class
     feeder (11,932 buses) in FP32 for rho in {10, 100, 1000}; the literal
     8500-bus variant in FP32 (rho = 10).  One solve each after one warm-up
-    solve, event-timed; one JSON line with a row per run."""
+    solve, event-timed; then the latency of opf_update_lines on the
+    8500-class feeder.  One JSON line."""
+    import numpy as np
     import torch
     torch.cuda.set_device(0)
     from paper_2501_08293_b300 import build as B
@@ -625,6 +628,8 @@ def run_configs(args):
     for rho in (10.0, 100.0, 1000.0):
         runs.append(("8500-class (11932 buses)", F.feeder_8500(1), opf.FP32, rho, "8500"))
     runs.append(("8500-bus literal", F.feeder_8500(1, n_bus=8500), opf.FP32, 10.0, None))
+    if args.configs_quick:
+        runs = runs[:3]
     rows = []
     stream = torch.cuda.current_stream()
     with ClockSampler(0) as clk:
@@ -650,8 +655,30 @@ def run_configs(args):
                          "S": d.n_comp, "n_global": d.n_global, "n_local": d.n_local, "chunks": d.n_blocks,
                          "engine": used_engine(p, prm)})
             p.close()
+    # incremental re-precompute: k lines of the 8500-class feeder get new
+    # impedances and taps (opf_update_lines, host call to return) against
+    # building the problem again on the host
+    f = F.feeder_8500(1)
+    rng = np.random.default_rng(args.seed)
+    p = opf.Problem.from_feeder(f)
+    live = np.flatnonzero(f.lines["in_service"] == 1)
+    upd = []
+    for k in (1, 16, 256):
+        idx = np.sort(rng.choice(live, size=k, replace=False)).astype(np.int32)
+        rec = f.lines[idx].copy()
+        rec["r"] *= 1.05
+        rec["tap"] = 1.01
+        p.update_lines(idx, rec)                  # warm-up of this size
+        t0 = time.perf_counter()
+        p.update_lines(idx, rec)
+        upd.append({"lines": k, "seconds": time.perf_counter() - t0})
+    p.close()
+    t0 = time.perf_counter()
+    opf.Problem.from_feeder(f, upload=False).close()
+    rebuild = time.perf_counter() - t0
     print(json.dumps({"metric": "ADMM iterations/s and time to ABS 1e-4 per configuration", "unit": "iters/s",
-                      "n_gpus": 1, "data": "synthetic", "rows": rows, "clocks": clk.summary()}))
+                      "n_gpus": 1, "data": "synthetic", "rows": rows, "clocks": clk.summary(),
+                      "line_update_8500": {"device_reprecompute": upd, "host_rebuild_s": rebuild}}))
 
 
 if __name__ == "__main__":

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "problem.hpp"
@@ -37,7 +38,7 @@ void scenarios_get_state(const opf_scenarios* sc, int k, double* xg, double* xl,
 void scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* n_local, int64_t* device_bytes);
 void scenarios_profile(opf_scenarios* sc, const opf_params& prm, int reps, cudaStream_t s, double* us);
 void device_reprecompute(opf_problem* p, const std::vector<int>& comps, cudaStream_t s);
-void device_update_bounds(opf_problem* p, int g0, int g1, cudaStream_t s);
+void device_update_bounds(opf_problem* p, const std::vector<std::pair<int, int>>& ranges, cudaStream_t s);
 }  // namespace opf
 
 namespace {
@@ -183,6 +184,7 @@ int32_t opf_update_lines(opf_problem* p, const int32_t* line_idx, const opf_line
         }
         if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "update before upload");
         std::vector<int> comps;
+        std::vector<std::pair<int, int>> ranges;
         for (int k = 0; k < count; ++k) {
             const int e = line_idx[k];
             const int c = line_comp[e];
@@ -205,8 +207,9 @@ int32_t opf_update_lines(opf_problem* p, const int32_t* line_idx, const opf_line
                     g1 = std::max(g1, (int)gi + 1);
                 }
             }
-            opf::device_update_bounds(p, g0, g1, (cudaStream_t)stream);
+            ranges.emplace_back(g0, g1);
         }
+        opf::device_update_bounds(p, ranges, (cudaStream_t)stream);
         opf::device_reprecompute(p, comps, (cudaStream_t)stream);
         return OPF_OK;
     });

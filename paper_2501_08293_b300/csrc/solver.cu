@@ -2270,21 +2270,28 @@ void device_reprecompute(opf_problem* p, const std::vector<int>& comps, cudaStre
     }
 }
 
-// Upload the bounds of globals [g0, g1) from p->model to both precisions.
-void device_update_bounds(opf_problem* p, int g0, int g1, cudaStream_t s) {
-    if (g1 <= g0) return;
+// Upload the bounds of the global ranges [g0, g1) from p->model to both
+// precisions (one synchronization for all).
+void device_update_bounds(opf_problem* p, const std::vector<std::pair<int, int>>& ranges, cudaStream_t s) {
+    if (ranges.empty()) return;
     DeviceGuard g(p->device);
     const Model& M = p->model;
-    const size_t n = (size_t)(g1 - g0);
-    std::vector<float> f(2 * n);
-    for (size_t i = 0; i < n; ++i) {
-        f[i] = (float)M.lo[g0 + i];
-        f[n + i] = (float)M.hi[g0 + i];
+    std::vector<std::vector<float>> keep;
+    for (const auto& r : ranges) {
+        const int g0 = r.first, g1 = r.second;
+        if (g1 <= g0) continue;
+        const size_t n = (size_t)(g1 - g0);
+        keep.emplace_back(2 * n);
+        std::vector<float>& f = keep.back();
+        for (size_t i = 0; i < n; ++i) {
+            f[i] = (float)M.lo[g0 + i];
+            f[n + i] = (float)M.hi[g0 + i];
+        }
+        OPF_CUDA(cudaMemcpyAsync((double*)p->d64.lo + g0, M.lo.data() + g0, n * 8, cudaMemcpyHostToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync((double*)p->d64.hi + g0, M.hi.data() + g0, n * 8, cudaMemcpyHostToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync((float*)p->d32.lo + g0, f.data(), n * 4, cudaMemcpyHostToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync((float*)p->d32.hi + g0, f.data() + n, n * 4, cudaMemcpyHostToDevice, s));
     }
-    OPF_CUDA(cudaMemcpyAsync((double*)p->d64.lo + g0, M.lo.data() + g0, n * 8, cudaMemcpyHostToDevice, s));
-    OPF_CUDA(cudaMemcpyAsync((double*)p->d64.hi + g0, M.hi.data() + g0, n * 8, cudaMemcpyHostToDevice, s));
-    OPF_CUDA(cudaMemcpyAsync((float*)p->d32.lo + g0, f.data(), n * 4, cudaMemcpyHostToDevice, s));
-    OPF_CUDA(cudaMemcpyAsync((float*)p->d32.hi + g0, f.data() + n, n * 4, cudaMemcpyHostToDevice, s));
     OPF_CUDA(cudaStreamSynchronize(s));
 }
 
