@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-iters", type=int, default=2000)
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--serve-requests-default", type=int, default=100,
+                    help="requests of the serving stream in the default bench line")
+    ap.add_argument("--no-serve", action="store_true", help="default bench line without the serving stream")
     ap.add_argument("--rate", type=float, default=4.0, help="request arrivals per second")
     ap.add_argument("--serve-max-bus", type=int, default=2500)
     ap.add_argument("--serve-budget-iters", type=int, default=200000)
@@ -198,8 +201,8 @@ def kernel_times(prob, params, stream):
 # persistent_smem_kernel<float> on the 8500-class feeder (seed 1, default
 # chunking): DRAM traffic per launch from ncu (see profiles/)
 PROFILED_BLOCKS = 296
-TRAFFIC_STAGING_B = 14_601_216
-TRAFFIC_PER_ITER_B = 28.9
+TRAFFIC_STAGING_B = 14_737_000
+TRAFFIC_PER_ITER_B = 29.0
 
 
 def run_ours(args):
@@ -352,6 +355,9 @@ def run_ours(args):
         "fp64_vs_lp_objective_rel": (abs(res["fp64"]["objective"] - lp["123"]) / abs(lp["123"]) if "123" in lp else None),
     }
     out["precision"] = prec_rep
+    # the metric's serving half: a short Poisson stream through the server
+    if rank == 0 and world == 1 and not args.no_serve:
+        out["serving"] = serve_stream(args, args.serve_requests_default, args.rate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, n, dt = cpu_oracle_rate(f, args.rho, args.cpu_seconds)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -445,32 +451,29 @@ def run_batch(args):
     }))
 
 
-def run_serve(args):
-    """Poisson stream of requests (sizes log-uniform, 30 % topology switches
-    of a resident feeder warm-started from its last iterate), continuous
-    batching; reports solves/s and p50/p99 latency."""
+def serve_stream(args, requests: int, rate: float) -> dict:
+    """Poisson stream of `requests` requests at `rate`/s (sizes log-uniform
+    in [13, serve-max-bus] buses, 30 % topology switches of a resident
+    feeder warm-started from its last iterate) through the continuous-
+    batching server; returns solves/s, p50/p99 latency and server counters."""
     import numpy as np
-    import torch
-    torch.cuda.set_device(0)
-    from paper_2501_08293_b300 import build as B
-    B.build()
     from paper_2501_08293_b300 import feeders as F
     from paper_2501_08293_b300 import opf
     rng = np.random.default_rng(args.seed)
     prec = opf.FP64 if args.precision == "fp64" else opf.FP32
     srv = opf.Server(precision=prec, rho=args.rho, max_iter=args.serve_budget_iters, check_every=50,
                      round_iters=1000, max_active=256)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=args.requests))
-    sizes = np.exp(rng.uniform(np.log(13), np.log(args.serve_max_bus), size=args.requests)).astype(int)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=requests))
+    sizes = np.exp(rng.uniform(np.log(13), np.log(args.serve_max_bus), size=requests)).astype(int)
     done_feeders = []            # (request id, feeder) finished and possibly resident
     kind = {}
     t0 = time.perf_counter()
     nxt = 0
     results = {}
     warm_n = 0
-    while len(results) < args.requests:
+    while len(results) < requests:
         now = time.perf_counter() - t0
-        while nxt < args.requests and arrivals[nxt] <= now:
+        while nxt < requests and arrivals[nxt] <= now:
             if done_feeders and rng.random() < 0.3:
                 rid0, f0 = done_feeders[int(rng.integers(0, len(done_feeders)))]
                 g = F.reconfigure(f0, rng)
@@ -494,15 +497,27 @@ def run_serve(args):
     conv = sum(1 for r in results if results[r].status == opf.OK)
     st = srv.stats()
     srv.close()
+    return {"solves_per_s": len(results) / wall, "requests": requests, "rate_per_s": rate,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean())},
+            "converged": conv, "warm_requests": warm_n, "wall_s": wall, "server": st,
+            "workload": f"{requests} requests, Poisson {rate}/s, n_bus log-uniform [13, {args.serve_max_bus}], "
+                        f"30% topology switches warm-started, ABS 1e-4, budget {args.serve_budget_iters} iterations"}
+
+
+def run_serve(args):
+    """The serving workload alone: solves/s and p50/p99 latency."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    r = serve_stream(args, args.requests, args.rate)
     print(json.dumps({
-        "metric": "served OPF solves/s (continuous batching)", "value": len(results) / wall, "unit": "solves/s",
-        "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == opf.FP64 else "f32", "data": "synthetic",
-        "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, n_bus log-uniform [13, {args.serve_max_bus}], "
-                               f"30% topology switches warm-started, ABS 1e-4, budget {args.serve_budget_iters} iterations",
-                   "rho": args.rho},
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "mean": float(lat.mean())},
-        "converged": conv, "warm_requests": warm_n, "wall_s": wall, "server": st,
+        "metric": "served OPF solves/s (continuous batching)", "value": r["solves_per_s"], "unit": "solves/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic", "config": {"workload": r["workload"], "rho": args.rho},
+        "latency_s": r["latency_s"], "converged": r["converged"], "warm_requests": r["warm_requests"],
+        "wall_s": r["wall_s"], "server": r["server"],
     }))
 
 
