@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="default bench line without the serving stream")
     ap.add_argument("--rate", type=float, default=4.0, help="request arrivals per second")
     ap.add_argument("--serve-max-bus", type=int, default=2500)
+    ap.add_argument("--serve-bus-per-chunk", type=int, default=0,
+                    help="serving: buses per chunk of a new request (0: the server's default)")
     ap.add_argument("--serve-budget-iters", type=int, default=200000)
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run one solve of this many iterations (a small case for ncu captures)")
@@ -485,7 +487,8 @@ def serve_stream(args, requests: int, rate: float) -> dict:
                 g = F.make_feeder(nb, int(rng.integers(1 << 30)), n_loads=max(1, nb // 8),
                                   load_sampler=lambda r: r.lognormal(-4.0, 1.0), n_pv=max(1, nb // 60),
                                   n_switches=4, line_mix=(0.6, 0.15, 0.25), v_ll_kv=12.47, lateral_mean=5.0)
-                rid = srv.submit(g)
+                ch = max(1, min(64, nb // args.serve_bus_per_chunk)) if args.serve_bus_per_chunk > 0 else 0
+                rid = srv.submit(g, chunks=ch)
                 kind[rid] = ("cold", g)
             nxt += 1
         srv.step()
