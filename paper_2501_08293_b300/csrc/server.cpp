@@ -220,12 +220,25 @@ void launch_round(opf_server* S, cudaStream_t s) {
     S->round = S->active;
     S->round_params.clear();
     S->batch.probs.clear();
+    // Every instance runs in the same launch, so a round lasts as long as its
+    // slowest instance's iterations.  An instance's time per iteration grows
+    // with its largest chunk (its CTAs run the chunk's tiles and halo every
+    // iteration): the slowest instance gets round_iters iterations, faster
+    // ones proportionally more (whole check intervals, at most 8x), so they
+    // do not sit idle for the rest of the round.
+    auto t_iter = [](const opf_problem* p) { return 1.5 + 0.004 * (double)p->pk.max_loc; };
+    double t_max = 0;
+    for (int64_t id : S->round) t_max = std::max(t_max, t_iter(S->reqs.at(id).p));
+    const int K = std::max(1, S->cfg.params.check_every);
     for (int64_t id : S->round) {
         Request& r = S->reqs.at(id);
         opf_params q = S->cfg.params;
         q.warm_start = (r.started || r.warm_from >= 0) ? 1 : 0;
         const int left = S->cfg.params.max_iter - (r.started ? r.info.iters : 0);
-        q.max_iter = std::max(0, std::min(S->cfg.round_iters, left));
+        const double scale = std::min(8.0, t_max / t_iter(r.p));
+        int iters = (int)(S->cfg.round_iters * scale) / K * K;
+        iters = std::max(S->cfg.round_iters, iters);
+        q.max_iter = std::max(0, std::min(iters, left));
         S->round_params.push_back(q);
         S->batch.probs.push_back(r.p);
     }
