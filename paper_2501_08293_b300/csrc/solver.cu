@@ -8,10 +8,13 @@
 //     and the residual sums of Eq. (termination): per component
 //     u = B_s x + lambda_s / rho, x_s = P_s u + bbar_s (P_s = -Abar_s),
 //     lambda_s += rho (B_s x - x_s).  One warp per tile of components (see
-//     pack.cpp); operator columns are contiguous across lanes, u is
-//     broadcast by warp shuffles.  On check iterations each CTA writes five
-//     FP64 partial sums: ||Bx - z||^2, ||z - z_prev||^2, ||Bx||^2, ||z||^2,
-//     ||lambda||^2; they are summed in a fixed order (deterministic).
+//     pack.cpp); the tile's operator columns are stored in lane-interleaved
+//     groups of four, so a lane reads four columns with one 16-byte load;
+//     u is broadcast by warp shuffles (graph engine, FP64) or read from
+//     shifted shared-memory rows (FP32 persistent kernel).  On check
+//     iterations each CTA writes five FP64 partial sums: ||Bx - z||^2,
+//     ||z - z_prev||^2, ||Bx||^2, ||z||^2, ||lambda||^2; they are summed in a
+//     fixed order (deterministic).
 //
 // Engines:
 //   GRAPH       z_kernel + x_kernel per iteration and finalize_kernel every
@@ -35,7 +38,10 @@
 //               each half of the double with the tag) into a two-slot
 //               mailbox; a reader polls exactly the words it needs until the
 //               tags match.  A single-copy-atomic word carries its own
-//               validity, so no release / acquire ordering is involved.
+//               validity, so no release / acquire ordering is involved.  Its
+//               checks do not wait for the decision: each leaves a snapshot
+//               of the state, and a stop raises a halt flag that every CTA
+//               sees at its next check or while polling a neighbour.
 #include <cuda_runtime.h>
 
 #include <chrono>
