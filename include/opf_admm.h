@@ -468,7 +468,7 @@ typedef struct opf_server_stats {
 
 void opf_server_config_default(opf_server_config* c);  /* FP32, rho 10, ABS 1e-4, 8 GiB */
 int32_t opf_server_create(const opf_server_config* cfg, opf_server** out);
-/* chunks <= 0: one chunk per 150 buses (1..64).  *id receives the request id. */
+/* chunks <= 0: one chunk per 50 buses (1..64).  *id receives the request id. */
 int32_t opf_server_submit(opf_server* s, const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
                           const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
                           int32_t chunks, int64_t warm_from, int64_t* id);

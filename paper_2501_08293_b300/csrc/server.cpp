@@ -317,9 +317,9 @@ int32_t opf_server_submit(opf_server* S, const opf_bus* buses, int32_t n_bus, co
         if (!S || !id) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
         const double t = now_s();
         opf_create_options o{};
-        // default: one chunk per 150 buses -- enough instances co-resident for
+        // default: one chunk per 50 buses (1..64) -- instances co-resident for
         // throughput, chunks small enough for short rounds
-        o.chunks = chunks > 0 ? chunks : std::max(1, std::min(64, n_bus / 150));
+        o.chunks = chunks > 0 ? chunks : std::max(1, std::min(64, n_bus / 50));
         opf_problem* p = nullptr;
         const int32_t st = opf_problem_create_ex(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load, &o, &p);
         if (st != OPF_OK) throw opf::Error(st, std::string("submit: ") + opf_last_error());

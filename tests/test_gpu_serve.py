@@ -25,7 +25,7 @@ def opf():
 
 
 def chunks_for(f):
-    return max(1, min(64, f.n_bus // 150))     # the server's default chunking
+    return max(1, min(64, f.n_bus // 50))      # the server's default chunking
 
 
 def drain(srv, want, max_steps=100000):
