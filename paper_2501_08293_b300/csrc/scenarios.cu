@@ -13,21 +13,27 @@
 // j * Sp + k (Sp = S rounded up to a multiple of 64), so the 32 lanes of a
 // warp hold 64 consecutive scenarios as float2 pairs.  Kernels, FP32 sweeps
 // with FP64 residual sums:
-//   sc_z_kernel   one warp per global: the copy terms of every scenario,
+//   sc_z_kernel   one half-warp per global: the copy terms of every scenario,
 //                 summed in the CSR order of the single-instance engines,
 //                 Eq. (global_sparse); stopped scenarios are not written;
-//   sc_x_kernel   one warp per component (grid-stride, fixed order): u for
-//                 all scenarios into shared memory, then per row r the GEMV
-//                 sum_c P[c][r] u_c with packed fmas on scenario pairs (P
-//                 broadcast; per-scenario P for voltage-dependent loads), the
-//                 dual update of Eq. (ADMM-3), the copy term for the next
-//                 global update, and on check iterations per-scenario FP64
-//                 partial sums of Eq. (termination);
-//   sc_fin_kernel one thread per scenario: fixed-order sum of the partials,
+//   sc_xs_kernel  components of at most 8 locals, one warp each (grid-
+//                 stride, fixed order): u of every column in registers, per
+//                 row r the GEMV sum_c P[c][r] u_c with packed fmas on
+//                 scenario pairs (P broadcast by shuffles; per-scenario P for
+//                 voltage-dependent loads), the dual update of Eq. (ADMM-3)
+//                 and the copy term for the next global update;
+//   sc_x_kernel   larger components, one CTA each: u staged in shared
+//                 memory, rows spread over the warps, same arithmetic;
+//                 both come as a plain and a check instantiation, the check
+//                 one also forming per-scenario FP64 partial sums of
+//                 Eq. (termination);
+//   sc_fin_kernel one CTA per scenario: fixed-order sum of the partials,
 //                 the stopping rule; a stopped scenario keeps the state of
 //                 its deciding check.
 // A CUDA graph runs K iterations and the check in the body of a device-side
-// while node until every scenario has stopped.
+// while node until every scenario has stopped (a body that has fewer than K
+// iterations left runs them at its last positions, so its check is still the
+// last one).
 //
 // The arithmetic of a scenario is the same sequence of operations as the
 // single-instance engines (same copy order, even/odd GEMV accumulators,
@@ -121,6 +127,14 @@ constexpr int kXsWarps = 8;
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// A body of the sweep runs r = min(K, max_iter - iter) iterations at its
+// last r positions q = K - r, ..., K - 1, so the check iteration is always
+// q = K - 1: the local-update kernels come in a check and a plain
+// instantiation, and the plain one carries no residual code.
+__device__ __forceinline__ int body_start(const ScCtl* ctl) {
+    return ctl->K - min(ctl->K, ctl->max_iter - ctl->iter);
+}
+
 __global__ void sc_init_kernel(ScView v) {
     const size_t n = (size_t)v.nl * v.Sp;
     const float inv_rho = v.ctl->inv_rho;
@@ -138,7 +152,7 @@ __global__ void sc_init_kernel(ScView v) {
 // rows are fetched without a dependent load between them.
 __global__ void __launch_bounds__(256) sc_z_kernel(ScView v, int q) {
     const ScCtl* ctl = v.ctl;
-    if (ctl->iter + q >= ctl->max_iter) return;
+    if (q < body_start(ctl)) return;
     const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 4);
     const int hl = threadIdx.x & 15;
     const unsigned hm = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
@@ -226,17 +240,79 @@ __device__ __forceinline__ void sc_partials(const double (&acc)[2][5], double (*
 }
 
 // Components of at most kSmallN locals (most of a feeder): one warp per
-// component, the operands of every column in registers (loads of all
-// columns issued together), the GEMV fully unrolled; same accumulation
-// order as the single-instance engines (even columns into y0, odd into y1).
-__global__ void __launch_bounds__(kXsWarps * 32) sc_xs_kernel(ScView v, int q) {
-    __shared__ double red[kXsWarps][5][64];
+// component.  u of every column for the lane's scenario pair is held in
+// registers (the loads of all columns are issued together), then each row's
+// GEMV runs over NC = 4, 6 or 8 columns (n rounded up; the padded operator
+// is zero past n, so those columns add exact zeros) in the order of the
+// single-instance engines: even columns into y0, odd into y1.  z and lambda
+// of a row are read again at the row (first-level cache hits) instead of
+// being kept in registers, which lets four CTAs share an SM.
+template <bool check, int NC>
+__device__ __forceinline__ void sc_small_rows(const ScView& v, const ScComp& cd, int gl, int k0, int lane, bool a0,
+                                              bool a1, bool keepx, float rho, float inv_rho, const float2 (&u)[kSmallN],
+                                              float (&f)[2][5]) {
+    const int n = cd.nf & 0xFFFF, j0 = cd.loc0, Sp = v.Sp;
+    const bool var = (cd.nf & kVarP) != 0;
+    const float4 pq = (!var && lane < 16) ? reinterpret_cast<const float4*>(v.Ps + cd.poff)[lane]
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* Pv = v.Pv + cd.poff;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+        if (r < n) {
+            float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+            if (!var) {
+                // element (c, r) of the padded 8 x 8 operator: lane 2c + r/4
+                const float pe = (r & 3) == 0 ? pq.x : (r & 3) == 1 ? pq.y : (r & 3) == 2 ? pq.z : pq.w;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const float ps = __shfl_sync(0xffffffffu, pe, 2 * c + (r >> 2));
+                    if (c & 1) y1 = ffma2(make_float2(ps, ps), u[c], y1);
+                    else y0 = ffma2(make_float2(ps, ps), u[c], y0);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c < n) {
+                        const float2 pv = *reinterpret_cast<const float2*>(Pv + (size_t)(c * n + r) * Sp + k0);
+                        if (c & 1) y1 = ffma2(pv, u[c], y1);
+                        else y0 = ffma2(pv, u[c], y0);
+                    }
+                }
+            }
+            const size_t e = (size_t)(j0 + r) * Sp + k0;
+            const int g = __shfl_sync(0xffffffffu, gl, r);
+            const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)g * Sp + k0);
+            const float2 l = *reinterpret_cast<const float2*>(v.L + e);
+            float2 bb;
+            if (cd.nf & kVarB) bb = *reinterpret_cast<const float2*>(v.bv + (size_t)(cd.boff + r) * Sp + k0);
+            else bb = make_float2(v.bs[cd.boff + r], v.bs[cd.boff + r]);
+            const float xn0 = (y0.x + y1.x) + bb.x, xn1 = (y0.y + y1.y) + bb.y;
+            const float ln0 = dual_of(l.x, rho, z.x, xn0), ln1 = dual_of(l.y, rho, z.y, xn1);
+            const float wn0 = copy_term(xn0, ln0, inv_rho), wn1 = copy_term(xn1, ln1, inv_rho);
+            if constexpr (check) {
+                const float2 xo = *reinterpret_cast<const float2*>(v.X + e);
+                sc_terms(f, z, make_float2(xn0, xn1), xo, make_float2(ln0, ln1));
+            }
+            if (a0) {
+                v.L[e] = ln0;
+                v.W[e] = wn0;
+                if (keepx) v.X[e] = xn0;
+            }
+            if (a1) {
+                v.L[e + 1] = ln1;
+                v.W[e + 1] = wn1;
+                if (keepx) v.X[e + 1] = xn1;
+            }
+        }
+    }
+}
+
+template <bool check>
+__global__ void __launch_bounds__(kXsWarps * 32, check ? 2 : 4) sc_xs_kernel(ScView v, int q) {
+    __shared__ double red[check ? kXsWarps : 1][5][64];
     const ScCtl* ctl = v.ctl;
-    const int iter = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
-    if (iter + q >= maxit) return;
-    const int last = min(K, maxit - iter) - 1;
-    const bool check = q == last;
-    const bool keepx = q >= last - 1;
+    if (q < body_start(ctl)) return;
+    const bool keepx = q >= ctl->K - 2;             // x before and at a check
     const float rho = ctl->rho, inv_rho = ctl->inv_rho;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kXsWarps + warp, nw = gridDim.x * kXsWarps;
@@ -253,116 +329,51 @@ __global__ void __launch_bounds__(kXsWarps * 32) sc_xs_kernel(ScView v, int q) {
             const int gl = ngl;
             const int n = cd.nf & 0xFFFF;
             const int j0 = cd.loc0;
-            const bool var = (cd.nf & kVarP) != 0;
-            float2 z[kSmallN], l[kSmallN];
+            float2 u[kSmallN];
 #pragma unroll
             for (int c = 0; c < kSmallN; ++c) {
                 const int g = __shfl_sync(0xffffffffu, gl, c);
                 if (c < n) {
-                    z[c] = *reinterpret_cast<const float2*>(v.Z + (size_t)g * Sp + k0);
-                    l[c] = *reinterpret_cast<const float2*>(v.L + (size_t)(j0 + c) * Sp + k0);
+                    const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)g * Sp + k0);
+                    const float2 l = *reinterpret_cast<const float2*>(v.L + (size_t)(j0 + c) * Sp + k0);
+                    u[c] = make_float2(u_of(z.x, l.x, inv_rho), u_of(z.y, l.y, inv_rho));
                 } else {
-                    z[c] = make_float2(0.f, 0.f);
-                    l[c] = make_float2(0.f, 0.f);
+                    u[c] = make_float2(0.f, 0.f);
                 }
             }
             if (s + nw < v.nsmall) {
                 ncd = v.comps[s + nw];
                 ngl = lane < (ncd.nf & 0xFFFF) ? v.gidx[ncd.loc0 + lane] : 0;
             }
-            float2 y0[kSmallN], y1[kSmallN];
-#pragma unroll
-            for (int r = 0; r < kSmallN; ++r) y0[r] = y1[r] = make_float2(0.f, 0.f);
             float f[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
-            const float* Pv = v.Pv + cd.poff;
-            if (!var) {
-                // shared operator padded to 8 x 8 (zero past n): lanes 0-15
-                // hold it as float4s, element (c, r) comes from lane 2c + r/4;
-                // padded columns add exact zeros (u is zero there)
-                const float4 pq = lane < 16 ? reinterpret_cast<const float4*>(v.Ps + cd.poff)[lane]
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int c = 0; c < kSmallN; ++c) {
-                    const float2 u = make_float2(u_of(z[c].x, l[c].x, inv_rho), u_of(z[c].y, l[c].y, inv_rho));
-#pragma unroll
-                    for (int r = 0; r < kSmallN; ++r) {
-                        const float pe = (r & 3) == 0 ? pq.x : (r & 3) == 1 ? pq.y : (r & 3) == 2 ? pq.z : pq.w;
-                        const float ps = __shfl_sync(0xffffffffu, pe, 2 * c + (r >> 2));
-                        if (c & 1) y1[r] = ffma2(make_float2(ps, ps), u, y1[r]);
-                        else y0[r] = ffma2(make_float2(ps, ps), u, y0[r]);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < kSmallN; ++c) {
-                    if (c < n) {
-                        const float2 u = make_float2(u_of(z[c].x, l[c].x, inv_rho), u_of(z[c].y, l[c].y, inv_rho));
-#pragma unroll
-                        for (int r = 0; r < kSmallN; ++r) {
-                            if (r < n) {
-                                const float2 pv = *reinterpret_cast<const float2*>(Pv + (size_t)(c * n + r) * Sp + k0);
-                                if (c & 1) y1[r] = ffma2(pv, u, y1[r]);
-                                else y0[r] = ffma2(pv, u, y0[r]);
-                            }
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < kSmallN; ++r) {
-                if (r < n) {
-                    const size_t e = (size_t)(j0 + r) * Sp + k0;
-                    float2 bb;
-                    if (cd.nf & kVarB) bb = *reinterpret_cast<const float2*>(v.bv + (size_t)(cd.boff + r) * Sp + k0);
-                    else bb = make_float2(v.bs[cd.boff + r], v.bs[cd.boff + r]);
-                    const float xn0 = (y0[r].x + y1[r].x) + bb.x, xn1 = (y0[r].y + y1[r].y) + bb.y;
-                    const float ln0 = dual_of(l[r].x, rho, z[r].x, xn0), ln1 = dual_of(l[r].y, rho, z[r].y, xn1);
-                    const float wn0 = copy_term(xn0, ln0, inv_rho), wn1 = copy_term(xn1, ln1, inv_rho);
-                    if (check) {
-                        const float2 xo = *reinterpret_cast<const float2*>(v.X + e);
-                        sc_terms(f, z[r], make_float2(xn0, xn1), xo, make_float2(ln0, ln1));
-                    }
-                    if (a0) {
-                        v.L[e] = ln0;
-                        v.W[e] = wn0;
-                        if (keepx) v.X[e] = xn0;
-                    }
-                    if (a1) {
-                        v.L[e + 1] = ln1;
-                        v.W[e + 1] = wn1;
-                        if (keepx) v.X[e + 1] = xn1;
-                    }
-                }
-            }
-            if (check) sc_accumulate(acc, f);
+            if (n <= 4) sc_small_rows<check, 4>(v, cd, gl, k0, lane, a0, a1, keepx, rho, inv_rho, u, f);
+            else if (n <= 6) sc_small_rows<check, 6>(v, cd, gl, k0, lane, a0, a1, keepx, rho, inv_rho, u, f);
+            else sc_small_rows<check, 8>(v, cd, gl, k0, lane, a0, a1, keepx, rho, inv_rho, u, f);
+            if constexpr (check) sc_accumulate(acc, f);
         }
-        if (check) sc_partials<kXsWarps>(acc, red, v.partials, blockIdx.x, Sp, pass);
+        if constexpr (check) sc_partials<kXsWarps>(acc, red, v.partials, blockIdx.x, Sp, pass);
     }
 }
 
 // Components of more than kSmallN locals: one CTA per component (grid-
-// stride), its warps stage u, the gathered globals and lambda of every
-// column for the lane's scenario pair in shared memory, then warp w updates
-// rows r = w, w + kScWarps, ...  GEMV order as the single-instance engines:
-// even columns into y0, odd into y1 up to 32 locals, one sequential
-// accumulator above.
-__global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
-    extern __shared__ float2 sdyn[];               // u, z, lambda: maxn x 32 each
-    __shared__ double red[kScWarps][5][64];
+// stride).  Its warps stage u of every column for the lane's scenario pair
+// in shared memory (and the component's operator when it is shared), then
+// warp w updates rows r = w, w + kScWarps, ... -- the rows whose columns it
+// staged, so z and lambda of a row are read again from the first-level
+// cache.  GEMV order as the single-instance engines: even columns into y0,
+// odd into y1 up to 32 locals, one sequential accumulator above.
+template <bool check>
+__global__ void __launch_bounds__(kScWarps * 32, check ? 4 : 8) sc_x_kernel(ScView v, int q) {
+    extern __shared__ float2 sdyn[];               // u: maxn x 32, then the operator
+    __shared__ double red[check ? kScWarps : 1][5][64];
     const ScCtl* ctl = v.ctl;
-    const int iter = ctl->iter, maxit = ctl->max_iter, K = ctl->K;
-    if (iter + q >= maxit) return;
-    const int last = min(K, maxit - iter) - 1;
-    const bool check = q == last;
-    const bool keepx = q >= last - 1;               // x before and at a check
+    if (q < body_start(ctl)) return;
+    const bool keepx = q >= ctl->K - 2;             // x before and at a check
     const float rho = ctl->rho, inv_rho = ctl->inv_rho;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Sp = v.Sp, mn = v.maxn;
     float2* us = sdyn;
-    float2* zs = sdyn + (size_t)mn * 32;
-    float2* ls = sdyn + (size_t)2 * mn * 32;
-    float2* bbs = sdyn + (size_t)3 * mn * 32;
-    float* psm = reinterpret_cast<float*>(sdyn + (size_t)4 * mn * 32);   // shared operator, mn * mn
+    float* psm = reinterpret_cast<float*>(sdyn + (size_t)mn * 32);   // shared operator, mn * mn
     for (int k0 = 2 * lane, pass = 0; k0 < Sp; k0 += 64, ++pass) {
         const bool a0 = v.st[k0].active != 0, a1 = v.st[k0 + 1].active != 0;
         double acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
@@ -376,12 +387,6 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
                 const int g = v.gidx[j0 + c];
                 const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)g * Sp + k0);
                 const float2 l = *reinterpret_cast<const float2*>(v.L + (size_t)(j0 + c) * Sp + k0);
-                float2 bv;
-                if (cd.nf & kVarB) bv = *reinterpret_cast<const float2*>(v.bv + (size_t)(cd.boff + c) * Sp + k0);
-                else bv = make_float2(v.bs[cd.boff + c], v.bs[cd.boff + c]);
-                zs[c * 32 + lane] = z;
-                ls[c * 32 + lane] = l;
-                bbs[c * 32 + lane] = bv;
                 us[c * 32 + lane] = make_float2(u_of(z.x, l.x, inv_rho), u_of(z.y, l.y, inv_rho));
             }
             __syncthreads();
@@ -390,9 +395,6 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
             float f[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};   // FP32 sums within the component
             for (int r = warp; r < n; r += kScWarps) {
                 const size_t e = (size_t)(j0 + r) * Sp + k0;
-                const float2 bb = bbs[r * 32 + lane];
-                float2 xo = make_float2(0.f, 0.f);
-                if (check) xo = *reinterpret_cast<const float2*>(v.X + e);
                 float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
                 if (!var) {
                     const float* pc = psm + r;              // column cc at pc[cc * n]
@@ -434,11 +436,19 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
                             y0 = ffma2(*reinterpret_cast<const float2*>(pc + cc * cs), us[cc * 32 + lane], y0);
                     }
                 }
-                const float2 z = zs[r * 32 + lane], l = ls[r * 32 + lane];
+                const int g = v.gidx[j0 + r];
+                const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)g * Sp + k0);
+                const float2 l = *reinterpret_cast<const float2*>(v.L + e);
+                float2 bb;
+                if (cd.nf & kVarB) bb = *reinterpret_cast<const float2*>(v.bv + (size_t)(cd.boff + r) * Sp + k0);
+                else bb = make_float2(v.bs[cd.boff + r], v.bs[cd.boff + r]);
                 const float xn0 = (y0.x + y1.x) + bb.x, xn1 = (y0.y + y1.y) + bb.y;
                 const float ln0 = dual_of(l.x, rho, z.x, xn0), ln1 = dual_of(l.y, rho, z.y, xn1);
                 const float wn0 = copy_term(xn0, ln0, inv_rho), wn1 = copy_term(xn1, ln1, inv_rho);
-                if (check) sc_terms(f, z, make_float2(xn0, xn1), xo, make_float2(ln0, ln1));
+                if constexpr (check) {
+                    const float2 xo = *reinterpret_cast<const float2*>(v.X + e);
+                    sc_terms(f, z, make_float2(xn0, xn1), xo, make_float2(ln0, ln1));
+                }
                 if (a0) {
                     v.L[e] = ln0;
                     v.W[e] = wn0;
@@ -450,10 +460,10 @@ __global__ void __launch_bounds__(kScWarps * 32) sc_x_kernel(ScView v, int q) {
                     if (keepx) v.X[e + 1] = xn1;
                 }
             }
-            if (check) sc_accumulate(acc, f);
+            if constexpr (check) sc_accumulate(acc, f);
             __syncthreads();                        // before the next component's staging
         }
-        if (check) sc_partials<kScWarps>(acc, red, v.partials, v.nctas_s + blockIdx.x, Sp, pass);
+        if constexpr (check) sc_partials<kScWarps>(acc, red, v.partials, v.nctas_s + blockIdx.x, Sp, pass);
     }
 }
 
@@ -578,7 +588,7 @@ struct ScArena {
 
 size_t sc_x_smem(int maxn) {
     const size_t m = (size_t)std::max(1, maxn);
-    return 4 * m * 32 * sizeof(float2) + ((m * m * sizeof(float) + 15) & ~size_t(15));
+    return m * 32 * sizeof(float2) + ((m * m * sizeof(float) + 15) & ~size_t(15));
 }
 
 struct DevGuard {
@@ -635,9 +645,11 @@ void build_graph(opf_scenarios* sc, int K) {
         sc_z_kernel<<<zblocks, 256, 0, cs>>>(v, q);
         cudaEventRecord(ev_z, cs);
         cudaStreamWaitEvent(cs2, ev_z, 0);
-        sc_x_kernel<<<v.nctas - v.nctas_s, kScWarps * 32, sc_x_smem(sc->maxn), cs2>>>(v, q);
+        if (q == K - 1) sc_x_kernel<true><<<v.nctas - v.nctas_s, kScWarps * 32, sc_x_smem(sc->maxn), cs2>>>(v, q);
+        else sc_x_kernel<false><<<v.nctas - v.nctas_s, kScWarps * 32, sc_x_smem(sc->maxn), cs2>>>(v, q);
         cudaEventRecord(ev_x, cs2);
-        sc_xs_kernel<<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
+        if (q == K - 1) sc_xs_kernel<true><<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
+        else sc_xs_kernel<false><<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
         cudaStreamWaitEvent(cs, ev_x, 0);
     }
     sc_fin_kernel<<<sc->S, 256, 0, cs>>>(v);
@@ -796,7 +808,7 @@ opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* li
         SC_CUDA(cudaGetDevice(&dev));
         SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         sc->device = dev;
-        const int nctas_s = 4 * sms, nctas_l = 4 * sms;
+        const int nctas_s = 4 * sms, nctas_l = 8 * sms;   // one wave each (plain sweeps)
         sc->nctas = nctas_s + nctas_l;
         ScArena a;
         const size_t o_comps = a.take<ScComp>(ncomp), o_Ps = a.take<float>(Ps.size()), o_Pv = a.take<float>(Pv.size());
@@ -842,7 +854,8 @@ opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* li
         v.nsmall = nsmall; v.nctas_s = nctas_s;
         const size_t xsm = sc_x_smem(sc->maxn);
         if (xsm > 200 * 1024) throw Error(OPF_ERR_INVALID_ARG, "a component is too large for the scenario engine");
-        SC_CUDA(cudaFuncSetAttribute(sc_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+        SC_CUDA(cudaFuncSetAttribute(sc_x_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+        SC_CUDA(cudaFuncSetAttribute(sc_x_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
         SC_CUDA(cudaMallocHost((void**)&sc->ctl_host, sizeof(ScCtl)));
         SC_CUDA(cudaMallocHost((void**)&sc->st_host, (size_t)Sp * sizeof(ScState)));
         SC_CUDA(cudaMallocHost((void**)&sc->am_host, (size_t)(Sp / 32) * sizeof(uint32_t)));
@@ -968,11 +981,11 @@ void scenarios_profile(opf_scenarios* sc, const opf_params& prm, int reps, cudaS
     };
     // q = 0 with K = 2^20: a plain iteration; q = K - 1: a check iteration
     us[0] = timeit([&] { sc_z_kernel<<<zblocks, 256, 0, s>>>(v, 0); });
-    us[1] = timeit([&] { sc_xs_kernel<<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, 0); });
-    us[2] = timeit([&] { sc_x_kernel<<<v.nctas - v.nctas_s, kScWarps * 32, xsm, s>>>(v, 0); });
+    us[1] = timeit([&] { sc_xs_kernel<false><<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, 0); });
+    us[2] = timeit([&] { sc_x_kernel<false><<<v.nctas - v.nctas_s, kScWarps * 32, xsm, s>>>(v, 0); });
     us[3] = timeit([&] {
-        sc_xs_kernel<<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, (1 << 20) - 1);
-        sc_x_kernel<<<v.nctas - v.nctas_s, kScWarps * 32, xsm, s>>>(v, (1 << 20) - 1);
+        sc_xs_kernel<true><<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, (1 << 20) - 1);
+        sc_x_kernel<true><<<v.nctas - v.nctas_s, kScWarps * 32, xsm, s>>>(v, (1 << 20) - 1);
     });
     us[4] = timeit([&] {
         sc_fin_kernel<<<sc->S, 256, 0, s>>>(v);

@@ -59,6 +59,32 @@ def test_scenarios_equal_alone_fixed_iterations(opf, S, picks):
     sc.close()
 
 
+def test_scenarios_short_last_body(opf):
+    """A sweep body with fewer than K iterations left runs them at its last
+    positions, so its check is still the last one: 130 = 2 x 50 + 30
+    iterations, then one warm iteration (a one-iteration body whose previous
+    x comes from the last check), each equal to solving alone."""
+    f = F.feeder_123(1)
+    S = 4
+    loads = F.load_scenarios(f, S, seed=5)
+    sc = opf.Scenarios.from_feeder(f, loads)
+    for warm, iters, total in ((0, 130, 130), (1, 1, 131)):
+        prm = opf.default_params(precision=opf.FP32, rho=10.0, criterion=opf.CRIT_NEVER, max_iter=iters,
+                                 check_every=50)
+        prm.warm_start = warm
+        infos = sc.solve(prm)
+        for k in range(S):
+            ia, sa = alone(opf, f, loads[k], opf.default_params(precision=opf.FP32, rho=10.0,
+                                                                 criterion=opf.CRIT_NEVER, max_iter=total,
+                                                                 check_every=50))
+            assert infos[k].iters == ia.iters == total
+            for x, y in zip(sc.state(k), sa):
+                assert np.array_equal(x, y), (k, total)
+            assert abs(infos[k].pres - ia.pres) <= 1e-5 * ia.pres
+            assert abs(infos[k].dres - ia.dres) <= 1e-5 * ia.dres
+    sc.close()
+
+
 def test_scenarios_converge_like_alone(opf):
     f = F.feeder_123(2)
     S = 6
