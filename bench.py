@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--serve-bus-per-chunk", type=int, default=0,
                     help="serving: buses per chunk of a new request (0: the server's default)")
     ap.add_argument("--serve-budget-iters", type=int, default=200000)
+    ap.add_argument("--profile-scenarios", type=int, default=0,
+                    help="launch each multi-scenario kernel this many times outside the graph (64 draws on the "
+                         "8500-class feeder; the small case for ncu) and exit")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run one solve of this many iterations (a small case for ncu captures)")
     return ap.parse_args()
@@ -543,6 +546,22 @@ def run_profile_solve(args):
     p.close()
 
 
+def run_profile_scenarios(args):
+    """Each kernel of one multi-scenario iteration launched a few times outside
+    the graph (64 draws on the 8500-class feeder): the small case for ncu."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+    f = F.feeder_8500(args.seed)
+    sc = opf.Scenarios.from_feeder(f, F.load_scenarios(f, args.scenarios, seed=args.seed + 100))
+    kt = sc.profile(opf.default_params(rho=args.rho, precision=opf.FP32, check_every=50), reps=args.profile_scenarios)
+    print("profile scenarios", {k: round(v, 2) for k, v in kt.items()})
+    sc.close()
+
+
 def run_scenarios(args):
     """64 load draws on the 8500-class topology (each load's a, b scaled by its
     own factor ~ U[0.5, 1]) iterated together by the multi-scenario engine,
@@ -701,7 +720,9 @@ def run_configs(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.profile_solve:
+    if a.profile_scenarios:
+        run_profile_scenarios(a)
+    elif a.profile_solve:
         run_profile_solve(a)
     elif a.impl == "reference":
         run_reference(a)

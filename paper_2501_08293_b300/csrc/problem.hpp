@@ -62,7 +62,7 @@ struct View {
     const int32_t* nbrs;
     const int32_t* hcp;
     const int32_t* hci;
-    int32_t* flags;
+    int32_t* flags;                   // per chunk: iteration flag (global-memory kernel) or claim word (shared-memory kernel)
     const T* P;
     const double* cost;
     double* partials;

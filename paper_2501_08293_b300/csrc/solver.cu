@@ -1083,10 +1083,40 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     }
 }
 
+// Which chunk a CTA runs.  Chunks are numbered along the feeder, so most
+// neighbours are adjacent numbers; the exchange between the two CTAs of one
+// SM is the cheapest, so the k-th CTA to start on SM `smid` prefers chunk
+// 2 smid + k.  A CTA whose preferred chunk is out of range or already taken
+// takes the first free one, so every chunk gets exactly one CTA whatever the
+// placement (`claim`: one zeroed word per chunk).  Which CTA runs a chunk
+// does not change any result: the chunk's work and its slot in the residual
+// reduction depend only on the chunk number.
+__device__ __forceinline__ int claim_chunk(int32_t* claim, int nblocks) {
+    __shared__ int s_b;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        int b = -1;
+        if (2 * (int)smid + 1 < nblocks) {
+            const int first = atomicCAS(claim + 2 * smid, 0, 1) == 0;
+            if (first) b = 2 * (int)smid;
+            else if (atomicCAS(claim + 2 * smid + 1, 0, 1) == 0) b = 2 * (int)smid + 1;
+        }
+        for (int c = 0; b < 0 && c < nblocks; ++c)
+            if (atomicCAS(claim + c, 0, 1) == 0) b = c;
+        s_b = b;
+    }
+    __syncthreads();
+    return s_b;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kXWarps * 32, 2) persistent_smem_kernel(View<T> v, SmemPlan sp) {
     extern __shared__ __align__(128) unsigned char sm[];
-    chunk_smem(v, blockIdx.x, sp, sm);
+    // nblocks CTAs claim nblocks chunks one each: the scan always finds one
+    const int b = claim_chunk(v.flags, v.nblocks);
+    if (b < 0) return;
+    chunk_smem(v, b, sp, sm);
 }
 
 // ------------------------------------------------------------------ batch
