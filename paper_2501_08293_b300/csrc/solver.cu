@@ -1084,24 +1084,23 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
 }
 
 // Which chunk a CTA runs.  Chunks are numbered along the feeder, so most
-// neighbours are adjacent numbers; the exchange between the two CTAs of one
-// SM is the cheapest, so the k-th CTA to start on SM `smid` prefers chunk
-// 2 smid + k.  A CTA whose preferred chunk is out of range or already taken
-// takes the first free one, so every chunk gets exactly one CTA whatever the
-// placement (`claim`: one zeroed word per chunk).  Which CTA runs a chunk
-// does not change any result: the chunk's work and its slot in the residual
-// reduction depend only on the chunk number.
-__device__ __forceinline__ int claim_chunk(int32_t* claim, int nblocks) {
+// neighbours are adjacent numbers; the exchange between CTAs of one SM is
+// the cheapest, so the k-th CTA to start on SM `smid` prefers chunk
+// per * smid + k (`per`: CTAs resident per SM).  A CTA whose preferred
+// chunks are out of range or already taken takes the first free one, so
+// every chunk gets exactly one CTA whatever the placement (`claim`: one
+// zeroed word per chunk).  Which CTA runs a chunk does not change any
+// result: the chunk's work and its slot in the residual reduction depend
+// only on the chunk number.
+__device__ __forceinline__ int claim_chunk(int32_t* claim, int nblocks, int per) {
     __shared__ int s_b;
     if (threadIdx.x == 0) {
         unsigned smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
         int b = -1;
-        if (2 * (int)smid + 1 < nblocks) {
-            const int first = atomicCAS(claim + 2 * smid, 0, 1) == 0;
-            if (first) b = 2 * (int)smid;
-            else if (atomicCAS(claim + 2 * smid + 1, 0, 1) == 0) b = 2 * (int)smid + 1;
-        }
+        if (per >= 1 && ((long long)smid + 1) * per <= nblocks)
+            for (int k = 0; k < per && b < 0; ++k)
+                if (atomicCAS(claim + (size_t)per * smid + k, 0, 1) == 0) b = per * (int)smid + k;
         for (int c = 0; b < 0 && c < nblocks; ++c)
             if (atomicCAS(claim + c, 0, 1) == 0) b = c;
         s_b = b;
@@ -1114,7 +1113,7 @@ template <typename T>
 __global__ void __launch_bounds__(kXWarps * 32, 2) persistent_smem_kernel(View<T> v, SmemPlan sp) {
     extern __shared__ __align__(128) unsigned char sm[];
     // nblocks CTAs claim nblocks chunks one each: the scan always finds one
-    const int b = claim_chunk(v.flags, v.nblocks);
+    const int b = claim_chunk(v.flags, v.nblocks, 2);
     if (b < 0) return;
     chunk_smem(v, b, sp, sm);
 }
@@ -1128,21 +1127,30 @@ struct CtaMap {
     int32_t inst, chunk;
 };
 
+// The map lists each instance's chunks consecutively; CTAs claim map
+// entries by SM as above (`per` CTAs resident per SM), so an instance's
+// neighbouring chunks tend to share an SM.
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32, 3) batch_smem_kernel(const View<T>* views, const CtaMap* map, SmemPlan sp) {
+__global__ void __launch_bounds__(kXWarps * 32, 3) batch_smem_kernel(const View<T>* views, const CtaMap* map, SmemPlan sp,
+                                                                     int32_t* claim, int per) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ View<T> sv;
-    const CtaMap m = map[blockIdx.x];
+    const int i = claim_chunk(claim, gridDim.x, per);
+    if (i < 0) return;
+    const CtaMap m = map[i];
     if (threadIdx.x == 0) sv = views[m.inst];
     __syncthreads();
     chunk_smem(sv, m.chunk, sp, sm);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32, 4) batch_global_kernel(const View<T>* views, const CtaMap* map) {
+__global__ void __launch_bounds__(kXWarps * 32, 4) batch_global_kernel(const View<T>* views, const CtaMap* map,
+                                                                       int32_t* claim, int per) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ View<T> sv;
-    const CtaMap m = map[blockIdx.x];
+    const int i = claim_chunk(claim, gridDim.x, per);
+    if (i < 0) return;
+    const CtaMap m = map[i];
     if (threadIdx.x == 0) sv = views[m.inst];
     __syncthreads();
     chunk_global(sv, m.chunk, smem_raw);
@@ -1545,6 +1553,18 @@ SmemPlan smem_plan(const opf_problem* p) {
 
 
 // Can every chunk's CTA be co-resident with `smem` dynamic bytes?
+// CTAs of `kernel` (kXWarps warps, `smem` bytes dynamic) resident per SM;
+// 0 if the query fails.
+template <typename KernelT>
+int resident_per_sm(KernelT kernel, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kXWarps * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
 template <typename KernelT>
 bool coop_fits(KernelT kernel, size_t smem, int nblocks) {
     int dev = 0, coop = 0, sms = 0, per_sm = 0, optin = 0;
@@ -1986,7 +2006,8 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     const size_t map_off = views_off + (((size_t)n * sizeof(View<T>) + 255) & ~size_t(255));
     const size_t zmap_off = map_off + (((size_t)nctas * sizeof(CtaMap) + 255) & ~size_t(255));
     const size_t run_off = zmap_off + (((size_t)std::max(1, nz) * sizeof(ZMap) + 255) & ~size_t(255));
-    const size_t bytes = run_off + 256;
+    const size_t claim_off = run_off + 256;                 // zeroed claim words, one per CTA
+    const size_t bytes = claim_off + (((size_t)nctas * sizeof(int32_t) + 255) & ~size_t(255));
     if (bytes > B->dev_bytes) {
         if (B->dev_buf) OPF_CUDA(cudaFreeAsync(B->dev_buf, s));
         B->dev_buf = nullptr;
@@ -2039,6 +2060,7 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
         for (int g0 = 0; g0 < p->pk.ng; g0 += kZThreads) hzmap[cz++] = ZMap{i, g0};
     }
     *hrun = running;
+    std::memset(B->host_buf + claim_off, 0, bytes - claim_off);
     for (int i = 0; i < n; ++i)
         OPF_CUDA(cudaMemcpyAsync(B->probs[i]->ctl, hctl + i, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     char* d = static_cast<char*>(B->dev_buf);
@@ -2047,17 +2069,20 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     const CtaMap* dmap = reinterpret_cast<const CtaMap*>(d + map_off);
     const ZMap* dzmap = reinterpret_cast<const ZMap*>(d + zmap_off);
     int* drun = reinterpret_cast<int*>(d + run_off);
+    int32_t* dclaim = reinterpret_cast<int32_t*>(d + claim_off);
     Ctl* dctl = reinterpret_cast<Ctl*>(d + ctl_off);
     const bool smem_var = engine == OPF_ENGINE_PERSISTENT && coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas);
     batch_clear_flags<T><<<std::min(n, 1024), 256, 0, s>>>(dviews, n, smem_var ? 1 : 0);
     OPF_CUDA(cudaGetLastError());
     if (running > 0 && engine == OPF_ENGINE_PERSISTENT) {
         if (smem_var) {
-            void* args[] = {&dviews, &dmap, &sp};
+            int per = resident_per_sm(batch_smem_kernel<T>, (size_t)sp.total);
+            void* args[] = {&dviews, &dmap, &sp, &dclaim, &per};
             OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_smem_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
                                                  args, (size_t)sp.total, s));
         } else if (coop_fits(batch_global_kernel<T>, gsmem, nctas)) {
-            void* args[] = {&dviews, &dmap};
+            int per = resident_per_sm(batch_global_kernel<T>, gsmem);
+            void* args[] = {&dviews, &dmap, &dclaim, &per};
             OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_global_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
                                                  args, gsmem, s));
         } else {
