@@ -1552,7 +1552,6 @@ SmemPlan smem_plan(const opf_problem* p) {
 }
 
 
-// Can every chunk's CTA be co-resident with `smem` dynamic bytes?
 // CTAs of `kernel` (kXWarps warps, `smem` bytes dynamic) resident per SM;
 // 0 if the query fails.
 template <typename KernelT>
@@ -1565,6 +1564,7 @@ int resident_per_sm(KernelT kernel, size_t smem) {
     return per_sm;
 }
 
+// Can every chunk's CTA be co-resident with `smem` dynamic bytes?
 template <typename KernelT>
 bool coop_fits(KernelT kernel, size_t smem, int nblocks) {
     int dev = 0, coop = 0, sms = 0, per_sm = 0, optin = 0;
