@@ -141,17 +141,23 @@ def measured_peaks():
 
 
 def cpu_oracle_rate(feeder, rho, seconds, max_iter=None):
-    """Oracle (as it stands) iterations/s on a bounded sample of the workload."""
+    """Oracle (as it stands) iterations/s on a bounded sample of the workload,
+    on one host thread: the BLAS pool is limited to one thread for the timed
+    loop (left alone, its threads spin beside a step that is mostly serial
+    numpy work: 8 threads gave 5 % more iterations/s for 8x the CPU time),
+    so the reported core count is the one actually used."""
+    from threadpoolctl import threadpool_limits
     from oracle import admm as OA, model as OM, precompute as OP
     m = OM.build_feeder(feeder)
     pre = OP.precompute(m)
     s = OA.ADMM(m, pre, rho)
-    t0 = time.perf_counter()
-    n = 0
-    while time.perf_counter() - t0 < seconds and (max_iter is None or n < max_iter):
-        s.step()
-        n += 1
-    dt = time.perf_counter() - t0
+    with threadpool_limits(limits=1):
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < seconds and (max_iter is None or n < max_iter):
+            s.step()
+            n += 1
+        dt = time.perf_counter() - t0
     return n / dt, n, dt
 
 
@@ -173,7 +179,8 @@ def run_reference(args):
         iters += n
         secs += dt
     value = iters / secs
-    sample = f"cold-start ADMM iterations for {per_step:.1f} s per step on {WORKLOAD}"
+    sample = (f"cold-start ADMM iterations for {per_step:.1f} s per step on {WORKLOAD}; one host thread "
+              f"(BLAS pool limited to 1)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -371,7 +378,7 @@ def run_ours(args):
         r, n, dt = cpu_oracle_rate(f, args.rho, args.cpu_seconds)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": f"{n} cold-start iterations ({dt:.1f} s) of the same feeder, "
-                                         f"FP64 numpy/scipy, single thread"}
+                                         f"FP64 numpy/scipy, one host thread (BLAS pool limited to 1)"}
     if rank == 0:
         print(json.dumps(out))
     prob.close()
