@@ -141,24 +141,34 @@ def measured_peaks():
 
 
 def cpu_oracle_rate(feeder, rho, seconds, max_iter=None):
-    """Oracle (as it stands) iterations/s on a bounded sample of the workload,
-    on one host thread: the BLAS pool is limited to one thread for the timed
-    loop (left alone, its threads spin beside a step that is mostly serial
-    numpy work: 8 threads gave 5 % more iterations/s for 8x the CPU time),
-    so the reported core count is the one actually used."""
-    from threadpoolctl import threadpool_limits
+    """Oracle (as it stands) iterations/s on a bounded sample of the workload.
+    Returns (rate, iterations, seconds, cores, threads_note).  Where
+    threadpoolctl is importable the BLAS pool is limited to one thread for
+    the timed loop (left alone its threads mostly spin beside a step that is
+    serial numpy work: on an 8-core host 8 threads gave 5 % more iterations/s
+    for 8x the CPU time); otherwise the pool is left as it is and `cores` is
+    the CPU time over the wall time of the loop, i.e. the cores it kept busy."""
+    import contextlib
     from oracle import admm as OA, model as OM, precompute as OP
     m = OM.build_feeder(feeder)
     pre = OP.precompute(m)
     s = OA.ADMM(m, pre, rho)
-    with threadpool_limits(limits=1):
+    try:
+        from threadpoolctl import threadpool_limits
+        limit, note = threadpool_limits(limits=1), "one host thread (BLAS pool limited to 1)"
+    except ImportError:
+        limit, note = contextlib.nullcontext(), "BLAS pool at its default (cores = CPU time / wall time)"
+    with limit:
         t0 = time.perf_counter()
+        c0 = time.process_time()
         n = 0
         while time.perf_counter() - t0 < seconds and (max_iter is None or n < max_iter):
             s.step()
             n += 1
         dt = time.perf_counter() - t0
-    return n / dt, n, dt
+        cpu = time.process_time() - c0
+    cores = 1 if note.startswith("one") else max(1, int(round(cpu / max(dt, 1e-9))))
+    return n / dt, n, dt, cores, note
 
 
 # ----------------------------------------------------------------- arms
@@ -173,20 +183,20 @@ def run_reference(args):
     per_step = max(2.0, min(10.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_oracle_rate(f, args.rho, 0.5)
-    iters, secs = 0, 0.0
+    iters, secs, cores, note = 0, 0.0, 1, ""
     for _ in range(args.steps):
-        r, n, dt = cpu_oracle_rate(f, args.rho, per_step)
+        r, n, dt, c, note = cpu_oracle_rate(f, args.rho, per_step)
         iters += n
         secs += dt
+        cores = max(cores, c)
     value = iters / secs
-    sample = (f"cold-start ADMM iterations for {per_step:.1f} s per step on {WORKLOAD}; one host thread "
-              f"(BLAS pool limited to 1)")
+    sample = f"cold-start ADMM iterations for {per_step:.1f} s per step on {WORKLOAD}; {note}"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "oracle": "numpy/scipy FP64"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -281,6 +291,16 @@ def run_ours(args):
     w = 8 if prec == opf.FP64 else 4
     bytes_iter = w * d.sum_n2 + d.n_local * (8 * w + 8) + d.n_global * (5 * w + 4)
     flops_iter = 2 * d.sum_n2
+    # the same with the operator in factor form (P_s = I - Q Q^T with Q of
+    # r_s columns, or N N^T with n_s - r_s; r_s = rows kept by the row
+    # reduction): reported for comparison, not used -- the dense P_s stays in
+    # shared memory for the whole solve
+    import numpy as np
+    st = prob.structure()
+    n_s = np.diff(st["comp_ptr"]).astype(np.int64)
+    r_s = st["m_reduced"].astype(np.int64)
+    factor_elems = int(np.sum(n_s * np.minimum(r_s, n_s - r_s)))
+    bytes_iter_factor = bytes_iter - w * d.sum_n2 + w * factor_elems
     kt = kernel_times(prob, params, stream)
 
     # e2e: host records -> create (host precompute) -> upload (H2D) -> solve
@@ -344,6 +364,7 @@ def run_ours(args):
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_note": traffic_note,
                      "peak_kind": kind,
                      "bytes_per_iter": bytes_iter, "flops_per_iter": flops_iter, "us_per_iter": us_iter,
+                     "bytes_per_iter_factor_form": bytes_iter_factor,
                      "l2": {"peak": L2_READ_GBS, "frac": achieved / L2_READ_GBS,
                             "note": "the iterate is L2-resident within a solve; L2 peak from the project's read probe"},
                      "kernel_us_graph_engine": kt},
@@ -375,10 +396,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_serve:
         out["serving"] = serve_stream(args, args.serve_requests_default, args.rate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, n, dt = cpu_oracle_rate(f, args.rho, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+        r, n, dt, cores, note = cpu_oracle_rate(f, args.rho, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{n} cold-start iterations ({dt:.1f} s) of the same feeder, "
-                                         f"FP64 numpy/scipy, one host thread (BLAS pool limited to 1)"}
+                                         f"FP64 numpy/scipy, {note}"}
     if rank == 0:
         print(json.dumps(out))
     prob.close()
