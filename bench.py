@@ -221,13 +221,13 @@ def kernel_times(prob, params, stream):
 
 
 # persistent_smem_kernel<float> on the 8500-class feeder (seed 1, default
-# chunking): DRAM traffic per launch from ncu (see profiles/)
+# chunking): DRAM traffic per launch from ncu (dram__bytes_read + write)
 PROFILED_BLOCKS = 296
 TRAFFIC_STAGING_B = 14_697_000
 TRAFFIC_PER_ITER_B = 41.7
 # the multi-scenario sweep (64 draws on the same feeder): DRAM bytes of one
 # plain iteration (global update + both local updates) from one cold-cache
-# ncu capture of the three kernels (see profiles/)
+# ncu capture of the three kernels
 SC_TRAFFIC_PER_ITER_B = 143_900_000
 
 
