@@ -330,21 +330,27 @@ int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine)
  * does not fit co-resident).                                               */
 int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block, int32_t persistent_variant);
 
-/* Allocation-free residual norms (the paper has no counterpart; it exists for
- * callers that may not allocate device memory: code running inside a fixed
- * memory pool, plugins handed pre-allocated buffers, processes that forbid
- * cudaMalloc after start-up).  Inputs are caller-owned device arrays of
- * n_local doubles: v = B x (the global vector gathered per local copy),
- * x_local and x_local_prev (stacked x_s at this and the previous iteration),
- * lam (stacked duals).  out is a caller-owned device array of 4 doubles that
- * receives pres, dres, eps_prim, eps_dual of Eq. (termination) (sum over s
- * outside the norm, as printed).  Work is enqueued on `stream`; the call does
- * not synchronize.  No cudaMalloc, cudaFree or allocating routine is called:
- * the per-CTA partial sums live in a fixed 128 KiB array inside the library,
- * which every GPU that loads the library holds until the process exits.
- * Limit: n_local <= 4,194,304, otherwise OPF_ERR_INVALID_ARG.  The first call
- * on each device looks up that array's device address (make it before any
- * stream capture).  All calls share the array: two calls whose work overlaps
+/* Allocation-free residual norms.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory -- code that
+ * runs inside a fixed memory pool that must not grow, plugins that are handed
+ * pre-allocated buffers, processes that forbid cudaMalloc after start-up.
+ * Inputs are caller-owned device arrays of n_local doubles: v (the global
+ * vector gathered per local copy, v_j = x[gidx_j]), x_local and x_local_prev
+ * (stacked local copies at this and at the previous iteration), lam (stacked
+ * duals).  out is a caller-owned device array of 4 doubles that receives,
+ * with 2-norms over all n_local entries,
+ *   out[0] = ||v - x_local||,
+ *   out[1] = rho * ||x_local - x_local_prev||,
+ *   out[2] = eps_rel * max(||v||, ||x_local||),
+ *   out[3] = eps_rel * ||lam||.
+ * Work is enqueued on `stream`; the call does not synchronize.  No cudaMalloc,
+ * cudaFree or allocating routine is called: the per-CTA partial sums live in
+ * a fixed 128 KiB array inside the library, which every GPU that loads the
+ * library holds until the process exits.  Limit: n_local <= 4,194,304,
+ * otherwise OPF_ERR_INVALID_ARG.  The first call in each CUDA context (each
+ * device's primary context, or any other context the caller makes current)
+ * looks up that array's device address in that context; make it before any
+ * stream capture.  All calls share the array: two calls whose work overlaps
  * on the GPU (different streams, or different host threads) race and give
  * wrong results; calls in one stream are ordered and safe.  Each call writes
  * every slot it reads, so no clearing is needed between calls.             */
@@ -357,6 +363,19 @@ int32_t opf_residuals_noalloc(const double* v, const double* x_local, const doub
  * bbar[n_s]; either pointer may be NULL.  *n_s (may be NULL) gets n_s.
  * No device work; valid right after opf_problem_create.                   */
 int32_t opf_get_operator(const opf_problem* p, int32_t s, double* P, double* bbar, int32_t* n_s);
+
+/* The precompute of Section IV-B and Eq. (closed_2) applied to caller-given
+ * rows: A[m*n] row-major and b[m] (host arrays, read only).  Row reduction
+ * keeps a maximal independent subset of the rows (*m_reduced gets its size;
+ * may be NULL); P[n*n] row-major receives -Abar_s = I - A^T (A A^T)^{-1} A
+ * and bbar[n] receives A^T (A A^T)^{-1} b for the kept rows (either may be
+ * NULL).  m = 0 gives P = I, bbar = 0.  Errors: OPF_ERR_INCONSISTENT when a
+ * dropped row is not satisfied (the row reduction's 0 = b, b != 0),
+ * OPF_ERR_INVALID_ARG for sizes outside [0, 4096] x [1, 4096] or a
+ * non-finite entry.  Host only: the same routine opf_problem_create runs on
+ * every component of the model.                                            */
+int32_t opf_component_operator(const double* A, const double* b, int32_t m, int32_t n, double* P, double* bbar,
+                               int32_t* m_reduced);
 
 void opf_destroy(opf_problem* p);
 

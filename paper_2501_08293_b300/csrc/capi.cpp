@@ -430,6 +430,30 @@ int32_t opf_get_operator(const opf_problem* p, int32_t s, double* P, double* bba
     });
 }
 
+int32_t opf_component_operator(const double* A, const double* b, int32_t m, int32_t n, double* P, double* bbar,
+                               int32_t* m_reduced) {
+    return guarded([&]() -> int32_t {
+        if (m < 0 || m > 4096 || n < 1 || n > 4096) throw opf::Error(OPF_ERR_INVALID_ARG, "m or n out of range");
+        if ((m > 0 && (!A || !b))) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL rows");
+        opf::Component c;
+        c.kind = -1;
+        c.index = -1;
+        c.gvars.assign(n, 0);
+        c.m = m;
+        c.A.assign(A, A + (size_t)m * n);
+        c.b.assign(b, b + m);
+        for (double a : c.A)
+            if (!std::isfinite(a)) throw opf::Error(OPF_ERR_INVALID_ARG, "non-finite entry in A");
+        for (double a : c.b)
+            if (!std::isfinite(a)) throw opf::Error(OPF_ERR_INVALID_ARG, "non-finite entry in b");
+        const opf::Operator op = opf::make_operator(c);
+        if (P) std::memcpy(P, op.P.data(), op.P.size() * sizeof(double));
+        if (bbar) std::memcpy(bbar, op.bbar.data(), op.bbar.size() * sizeof(double));
+        if (m_reduced) *m_reduced = op.m_reduced;
+        return OPF_OK;
+    });
+}
+
 void opf_destroy(opf_problem* p) {
     if (!p) return;
     try {

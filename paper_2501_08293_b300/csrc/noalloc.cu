@@ -1,5 +1,6 @@
-// Residual norms of Eq. (termination) for caller-owned device vectors, with
-// no device allocation at all.
+// Residual norms for caller-owned device vectors, with no device allocation
+// at all: pres = ||v - z||, dres = rho ||z - z_prev||, eps_prim = eps_rel
+// max(||v||, ||z||), eps_dual = eps_rel ||lambda|| (2-norms over all locals).
 //
 // Who needs this: code that runs where cudaMalloc / cudaFree (and any
 // allocating library routine) are off limits -- inside a caller's memory
@@ -14,6 +15,7 @@
 // them to its slot of the scratch array; one CTA then adds the slots in a
 // fixed order.  Every slot that the second stage reads is written by the
 // first stage of the same call, so nothing has to be cleared between calls.
+#include <cuda.h>            // driver types only (entry points resolved through the runtime)
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -80,26 +82,77 @@ __global__ void __launch_bounds__(kNaThreads) noalloc_finish(const double* scrat
     }
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the symbol's host-side name is not a device address).
-constexpr int kMaxDevices = 64;
+// Device address of the scratch array.  The array's host-side name is not a
+// device address: cudaGetSymbolAddress gives the address in the current
+// context's copy of this module.  A context has its own copy (a non-primary
+// context, or the primary context again after cudaDeviceReset, loads the
+// module anew, possibly at another address), so the address is cached per
+// context, keyed by the driver's unique context id (cuCtxGetId, never
+// reused within a process), and looked up once per context.
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
 std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+constexpr int kCacheSlots = 64;
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;
+    double* ptr = nullptr;
+};
+ScratchSlot g_cache[kCacheSlots];
+int g_cache_next = 0;
 
-double* scratch_for_current_device() {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) throw Error(OPF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) throw Error(OPF_ERR_INVALID_ARG, "device index beyond 63");
+void resolve_driver_entry_points() {
+    if (g_ctx_get_current && g_ctx_get_id) return;
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0 = cudaDriverEntryPointSymbolNotFound, q1 = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e0 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+    cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+    if (e0 != cudaSuccess || e1 != cudaSuccess || q0 != cudaDriverEntryPointSuccess ||
+        q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+        throw Error(OPF_ERR_CUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not available");
+    g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f0);
+    g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f1);
+}
+
+// Unique id of the calling thread's current context; 0 when there is none.
+unsigned long long current_context_id() {
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    unsigned long long id = 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+double* symbol_address() {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+        throw Error(OPF_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    return static_cast<double*>(ptr);
+}
+
+double* scratch_for_current_context() {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
-            throw Error(OPF_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = static_cast<double*>(ptr);
+    resolve_driver_entry_points();
+    unsigned long long id = current_context_id();
+    if (id == 0) {
+        // no current context yet: the runtime makes the device's primary
+        // context current when it resolves the symbol
+        double* p = symbol_address();
+        id = current_context_id();
+        if (id == 0) throw Error(OPF_ERR_CUDA, "no current CUDA context after resolving the scratch array");
+        g_cache[g_cache_next] = ScratchSlot{id, p};
+        g_cache_next = (g_cache_next + 1) % kCacheSlots;
+        return p;
     }
-    return g_scratch_ptr[dev];
+    for (const ScratchSlot& c : g_cache)
+        if (c.ctx_id == id) return c.ptr;
+    double* p = symbol_address();
+    g_cache[g_cache_next] = ScratchSlot{id, p};
+    g_cache_next = (g_cache_next + 1) % kCacheSlots;
+    return p;
 }
 
 }  // namespace
@@ -111,7 +164,7 @@ void residuals_noalloc(const double* v, const double* z, const double* zp, const
                                              std::to_string(kNaMaxLocals) + "], the size the fixed scratch supports");
     if (!out || (n > 0 && (!v || !z || !zp || !lam))) throw Error(OPF_ERR_INVALID_ARG, "NULL device pointer");
     if (!(rho > 0.0)) throw Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
-    double* scratch = scratch_for_current_device();
+    double* scratch = scratch_for_current_context();
     const int per_block = kNaThreads * kNaPerThread;
     const int nb = n > 0 ? (int)((n + per_block - 1) / per_block) : 1;
     noalloc_partials<<<nb, kNaThreads, 0, s>>>(v, z, zp, lam, (int)n, scratch);

@@ -30,7 +30,7 @@ struct Ctl {
     int32_t abort;                // a wait gave up: every CTA leaves
     int32_t halt;                 // a check decided to stop (non-blocking checks): CTAs leave
     int32_t skip_block;           // test hook: this CTA withholds its flag (-1: none)
-    int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait, 4 staging
+    int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait, 4 staging, 5 staging copy never landed
     int32_t profile_phases;       // persistent kernel: accumulate per-phase time
     int32_t adaptive;             // residual balancing on
     int32_t rho_changes;

@@ -722,10 +722,18 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         }
     }
     if (!__syncthreads_and(ok)) {
-        // give the copy in flight a second bounded chance to land before leaving
-        const unsigned long long deadline = now_ns() + tmo;
-        while (!mbar_try_wait(&mbar, 0) && now_ns() < deadline) {
+        // The solve is abandoned (OPF_ERR_TIMEOUT), but the bulk copy still
+        // targets this CTA's shared memory: stay resident until it lands.
+        // The wait is bounded (8x the wait limit, at least 4 s); a copy that
+        // has not landed by then is recorded as site 5 before the CTA leaves.
+        if (threadIdx.x == 0) {
+            const unsigned long long lim = max(tmo, 500000000ull) * 8ull;
+            const unsigned long long deadline = now_ns() + lim;
+            bool landed = false;
+            while (!(landed = mbar_try_wait(&mbar, 0)) && now_ns() < deadline) __nanosleep(256);
+            if (!landed) ctl->timeout_where = 5;
         }
+        __syncthreads();
         return;
     }
 

@@ -100,6 +100,7 @@ EXPORTS = {
     "opf_profile_persistent_ctas": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
     "opf_chunk_stats": (C.c_int32, [_P, _I]),
     "opf_residuals_noalloc": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, _P, _P]),
+    "opf_component_operator": (C.c_int32, [_D, _D, C.c_int32, C.c_int32, _D, _D, _I]),
     "opf_destroy": (None, [_P]),
     "opf_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "opf_batch_solve": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, C.POINTER(Info)]),
@@ -178,6 +179,21 @@ def residuals_noalloc(v, x_local, x_local_prev, lam, rho: float, eps_rel: float,
     _check(lib.opf_residuals_noalloc(v.data_ptr(), x_local.data_ptr(), x_local_prev.data_ptr(), lam.data_ptr(),
                                      n, rho, eps_rel, out.data_ptr(), _stream_handle(stream)),
            "opf_residuals_noalloc")
+
+
+def component_operator(A, b):
+    """P = -Abar_s and bbar_s of Eq. (closed_2) for caller-given rows A_s, b_s
+    after row reduction (opf_component_operator, host only); returns
+    (P, bbar, m_reduced)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m, n = A.shape
+    P = np.empty((n, n))
+    bbar = np.empty(n)
+    mr = C.c_int32()
+    _check(lib.opf_component_operator(_dp(A) if m else None, _dp(b) if m else None, m, n, _dp(P), _dp(bbar),
+                                      C.byref(mr)), "opf_component_operator")
+    return P, bbar, mr.value
 
 
 class Problem:

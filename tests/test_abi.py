@@ -181,3 +181,55 @@ def test_line_updates_are_validated_on_the_host(opf):
     if len(dead):
         assert call([int(dead[0])], f.lines[[int(dead[0])]]) == -1
     assert call([len(f.lines)], rec) == -1
+
+
+def test_component_operator_inconsistent_rows(opf):
+    """Rows that contradict each other (x0 + x1 = 1 and 2 x0 + 2 x1 = 3)
+    are refused with OPF_ERR_INCONSISTENT through the C ABI: the row
+    reduction of Section IV-B meets 0 = b, b != 0.  The physical model's
+    rows are always consistent, so this is the way to reach that status."""
+    A = np.array([[1.0, 1.0, 0.0], [2.0, 2.0, 0.0]])
+    for b, ok in (([1.0, 3.0], False), ([1.0, 2.0], True)):
+        b = np.array(b)
+        P = np.empty((3, 3)); bb = np.empty(3); mr = C.c_int32()
+        st = opf.lib.opf_component_operator(A.ctypes.data_as(opf._D), b.ctypes.data_as(opf._D), 2, 3,
+                                            P.ctypes.data_as(opf._D), bb.ctypes.data_as(opf._D), C.byref(mr))
+        if ok:
+            assert st == 0 and mr.value == 1
+            # the minimum-norm solution of x0 + x1 = 1 and the projector onto its null space
+            np.testing.assert_allclose(bb, [0.5, 0.5, 0.0], atol=1e-15)
+            np.testing.assert_allclose(P, [[0.5, -0.5, 0.0], [-0.5, 0.5, 0.0], [0.0, 0.0, 1.0]], atol=1e-15)
+        else:
+            assert st == -2, st
+            assert "no common solution" in opf.lib.opf_last_error().decode()
+    # a zero row with a nonzero right-hand side
+    A = np.zeros((1, 2)); b = np.array([1.0])
+    assert opf.lib.opf_component_operator(A.ctypes.data_as(opf._D), b.ctypes.data_as(opf._D), 1, 2,
+                                          None, None, None) == -2
+    # non-finite entries and bad sizes
+    A = np.array([[np.nan, 1.0]]); b = np.array([0.0])
+    assert opf.lib.opf_component_operator(A.ctypes.data_as(opf._D), b.ctypes.data_as(opf._D), 1, 2,
+                                          None, None, None) == -1
+    assert opf.lib.opf_component_operator(None, None, 0, 0, None, None, None) == -1
+
+
+def test_component_operator_matches_oracle_row_reduction(opf):
+    """Random rank-deficient but consistent systems: the library's QR
+    precompute agrees with the oracle's row reduction + Cholesky (ranks,
+    projectors, minimum-norm bbar); m = 0 gives P = I, bbar = 0."""
+    from oracle import precompute as OP
+    rng = np.random.default_rng(7)
+    for trial in range(40):
+        n = int(rng.integers(2, 30))
+        r = int(rng.integers(1, n))
+        m = int(rng.integers(r, r + 5))
+        A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))     # rank r
+        b = A @ rng.standard_normal(n)                                    # consistent
+        P, bb, mr = opf.component_operator(A, b)
+        Ar, br, piv = OP.rref(A, b)
+        Abar, bbar = OP.closed_form(Ar, br)
+        assert mr == Ar.shape[0] == r
+        np.testing.assert_allclose(P, -Abar, atol=1e-9)
+        np.testing.assert_allclose(bb, bbar, atol=1e-9 * max(1.0, np.abs(bbar).max()))
+    P, bb, mr = opf.component_operator(np.zeros((0, 4)), np.zeros(0))
+    assert mr == 0 and np.array_equal(P, np.eye(4)) and np.array_equal(bb, np.zeros(4))

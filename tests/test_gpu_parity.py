@@ -1,12 +1,15 @@
 """GPU parity: the sm_103a path through the C ABI against the FP64 oracle on
 the same seeded feeders.
 
-Tolerance (FP64 path): 1e-9 relative, normwise per iterate
-(||gpu - oracle|| <= 1e-9 * max(||oracle||, 1)) for the global vector, the
-stacked locals and the duals, at several iterations; residuals likewise.
-Both sides run Algorithm 1 in FP64 with different summation orders and
-different (but equivalent) precompute factorizations (operators agree to
-~1e-11), and ADMM is non-expansive, so the gap stays at rounding level.
+Tolerance (FP64 path): 1e-9 relative per iterate, for the global vector,
+the stacked locals and the duals, at several iterations, checked two ways:
+normwise, ||gpu - oracle|| <= 1e-9 ||oracle||, and element by element,
+|gpu_i - oracle_i| <= 1e-9 (|oracle_i| + ||oracle||_inf), so that a wrong
+small entry (a near-zero dual, a slack flow) cannot hide behind the large
+ones; residuals likewise.  Both sides run Algorithm 1 in FP64 with
+different summation orders and different (but equivalent) precompute
+factorizations (operators agree to ~1e-11), and ADMM is non-expansive, so
+the gap stays at rounding level.
 """
 import numpy as np
 import pytest
@@ -29,7 +32,15 @@ def opf():
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1.0))
+    """Normwise relative difference (0 when both are exactly zero), and the
+    largest element-wise ratio |a_i - b_i| / (|b_i| + ||b||_inf); the larger
+    of the two is returned so that one bound checks both."""
+    nb = float(np.linalg.norm(b))
+    d = a - b
+    if nb == 0.0:
+        return 0.0 if not np.any(d) else float("inf")
+    scale = np.abs(b) + float(np.max(np.abs(b)))
+    return max(float(np.linalg.norm(d)) / nb, float(np.max(np.abs(d) / scale)))
 
 
 def oracle_solver(f, rho):
@@ -143,6 +154,38 @@ def test_full_size_8500_class_parity(opf):
     assert abs(info.pres - r.pres) <= TOL * r.pres and abs(info.dres - r.dres) <= TOL * r.dres
     # invariants at full size: bounds hold exactly, local rows hold
     assert np.all(xg >= m.lo) and np.all(xg <= m.hi)
+    p.close()
+
+
+# FP32 sweeps against the FP64 oracle: FP32 unit roundoff u = 2^-24 = 6e-8.
+# Per iteration each local entry is a sum of at most n_s (<= 39) products and
+# each global a sum over its copies; ADMM is non-expansive, so rounding
+# errors add up at most linearly over iterations and, being of random sign,
+# typically as the square root: sqrt(t * mean n_s) u ~ sqrt(200 * 7) * 6e-8
+# ~ 2e-6 at t = 200, plus the one-time rounding of the operators to FP32 (u
+# per entry).  The bound below keeps a factor of ~5 over that estimate.
+TOL_FP32_T200 = 1e-5
+
+
+@pytest.mark.parametrize("rho", [10.0, 100.0])
+def test_fp32_per_iterate_parity_8500_class(opf, rho):
+    """The headline configuration (8500-class feeder, FP32 sweeps with FP64
+    residual sums, default engine and chunking, check every 50) against the
+    FP64 oracle at t = 200: x, z and lambda within TOL_FP32_T200 normwise and
+    element by element (scale |oracle_i| + max |oracle|), residuals within
+    1e-3 relative."""
+    f = F.feeder_8500(1)
+    p = opf.Problem.from_feeder(f)
+    m, pre, s = oracle_solver(f, rho)
+    info = p.solve(opf.default_params(rho=rho, criterion=opf.CRIT_NEVER, max_iter=200, check_every=50,
+                                      precision=opf.FP32))
+    for _ in range(200):
+        r = s.step()
+    xg, xl, lam = p.state()
+    errs = {"x": rel(xg, s.x), "z": rel(xl, s.z), "lam": rel(lam, s.lam)}
+    assert max(errs.values()) <= TOL_FP32_T200, errs
+    assert abs(info.pres - r.pres) <= 1e-3 * r.pres and abs(info.dres - r.dres) <= 1e-3 * r.dres
+    assert abs(info.eps_prim - r.eps_prim) <= 1e-5 * r.eps_prim
     p.close()
 
 

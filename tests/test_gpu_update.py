@@ -23,7 +23,15 @@ def opf():
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1.0))
+    """Normwise relative difference (0 when both are exactly zero), and the
+    largest element-wise ratio |a_i - b_i| / (|b_i| + ||b||_inf); the larger
+    of the two is returned so that one bound checks both."""
+    nb = float(np.linalg.norm(b))
+    d = a - b
+    if nb == 0.0:
+        return 0.0 if not np.any(d) else float("inf")
+    scale = np.abs(b) + float(np.max(np.abs(b)))
+    return max(float(np.linalg.norm(d)) / nb, float(np.max(np.abs(d) / scale)))
 
 
 def changed_lines(f, rng, count):

@@ -482,3 +482,77 @@ def test_golden_lp_objectives_reproduce():
     for name, f in (("13", F.feeder_13(1)), ("123", F.feeder_123(1))):
         r = OL.solve_lp(OM.build_feeder(f))
         assert r.status == 0 and abs(r.fun - g[name]["objective"]) <= 1e-9 * abs(r.fun)
+
+
+def test_residual_balancing_rule_on_scripted_residuals():
+    """Residual balancing (Section III-D names it; the rule is the standard
+    one of Boyd et al., 2011, "Distributed Optimization and Statistical
+    Learning via the ADMM", Sec. 3.4.1, Eq. 3.13): at a check that does not
+    stop, rho -> tau rho if ||r|| > mu ||s||, rho -> rho / tau if
+    ||s|| > mu ||r||, else unchanged (r = primal, s = dual residual).  The
+    oracle's step is replaced by a scripted residual sequence; the rho in
+    effect at each step is worked out by hand below (mu = 10, tau = 2,
+    rho0 = 100), including the strict comparison, no change at max_iter and
+    no change on the check that stops."""
+    m = OM.build_feeder(F.feeder_tiny(3, 1))
+    s = OA.ADMM(m, OP.precompute(m), 100.0)
+    script = [(1.0, 0.01), (1.0, 0.2), (0.001, 1.0), (0.001, 1.0), (10.0, 1.0), (10.0001, 1.0), (1.0, 0.0)]
+    seen = []
+
+    def fake_step(form=OA.RES_PAPER, eps_rel=1e-3):
+        seen.append(s.rho)
+        pr, du = script[len(seen) - 1]
+        s.t += 1
+        return OA.Residuals(pr, du, 1.0, 1.0)
+
+    s.step = fake_step
+    out = s.run(len(script), criterion=OA.CRIT_NEVER, check_every=1, adaptive_rho=True, rb_mu=10.0, rb_tau=2.0)
+    assert seen == [100.0, 200.0, 200.0, 100.0, 50.0, 50.0, 100.0]
+    assert out["rho"] == 100.0 and out["rho_changes"] == 4
+    # checks every 2 iterations: only the residuals at t = 2 (no change),
+    # 4 (halve), 6 (double) count; t = 7 is max_iter (no change)
+    s.rho, s.t = 100.0, 0
+    seen.clear()
+    out = s.run(len(script), criterion=OA.CRIT_NEVER, check_every=2, adaptive_rho=True)
+    assert seen == [100.0, 100.0, 100.0, 100.0, 50.0, 50.0, 100.0]
+    assert out["rho_changes"] == 2
+    # the check that stops leaves rho alone
+    script[:] = [(1.0, 0.001), (1e-6, 1e-3)]
+    s.rho, s.t = 100.0, 0
+    seen.clear()
+    out = s.run(10, criterion=OA.CRIT_ABS, eps_abs_prim=1e-4, eps_abs_dual=1e-2, check_every=1, adaptive_rho=True)
+    assert out["converged"] and out["iters"] == 2 and seen == [100.0, 200.0] and out["rho"] == 200.0
+
+
+def test_residual_balancing_equals_restart_at_new_rho():
+    """Abar_s and bbar_s do not depend on rho and the duals are unscaled, so
+    continuing after a residual-balancing change of rho is the same as a
+    fresh Algorithm 1 at the new rho started from the same (x, z, lambda):
+    the adaptive run must equal, bit for bit, a chain of fixed-rho runs
+    restarted at every change.  (A plausible slip -- rescaling lambda as in
+    the scaled-dual form, or applying the new rho one iteration late --
+    breaks the equality.)"""
+    f = F.feeder_13(2)
+    m = OM.build_feeder(f)
+    pre = OP.precompute(m)
+    K, T = 40, 800
+    a = OA.ADMM(m, pre, 100.0)
+    ref = a.run(T, criterion=OA.CRIT_NEVER, check_every=K, adaptive_rho=True)
+    assert ref["rho_changes"] >= 2
+    # rho in effect after each check j (a run of K j + 1 iterations applies
+    # the decision of check j and stops before the next one)
+    rhos = [100.0]
+    for j in range(1, T // K):
+        r = OA.ADMM(m, pre, 100.0).run(K * j + 1, criterion=OA.CRIT_NEVER, check_every=K, adaptive_rho=True)
+        rhos.append(r["rho"])
+    assert len(set(rhos)) >= 3
+    b = OA.ADMM(m, pre, rhos[0])
+    for j in range(T // K):
+        if j and rhos[j] != rhos[j - 1]:
+            fresh = OA.ADMM(m, pre, rhos[j])
+            fresh.x, fresh.z, fresh.lam, fresh.t = b.x, b.z, b.lam, b.t
+            b = fresh
+        for _ in range(K):
+            b.step()
+    assert b.t == a.t == T and b.rho == ref["rho"]
+    assert np.array_equal(b.x, a.x) and np.array_equal(b.z, a.z) and np.array_equal(b.lam, a.lam)

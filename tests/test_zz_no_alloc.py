@@ -65,3 +65,29 @@ def test_residuals_noalloc_match_solver(env):
                                        4_194_305, rho, eps_rel, C.c_void_p(out.data_ptr()), None)
     assert st == -1 and "4194304" in opf.lib.opf_last_error().decode()
     p.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2048 * 8 * 3 + 777, 2048 * 8 * 256])
+def test_residuals_noalloc_sizes(env, n):
+    """Seeded random vectors at the edges of the fixed scratch: no locals,
+    one, a partial last CTA, and the largest size it supports (every slot
+    in use).  Two calls in a row on different data; each is compared with
+    numpy FP64 norms at 1e-12 relative."""
+    torch, opf = env
+    rng = np.random.default_rng(1234 + n)
+    rho, eps_rel = 37.5, 2e-3
+    out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    for call in range(2):
+        a = [rng.standard_normal(n) * s for s in (1.0, 1.0, 0.5, 3.0)]
+        v, z, zp, l = a[0], a[0] + 1e-3 * a[1], a[0] + 1e-3 * a[1] + 1e-4 * a[2], a[3]
+        d = [torch.from_numpy(x).to("cuda") if n else torch.zeros(1, dtype=torch.float64, device="cuda")
+             for x in (v, z, zp, l)]
+        st = opf.lib.opf_residuals_noalloc(*[C.c_void_p(t.data_ptr()) for t in d], n, rho, eps_rel,
+                                           C.c_void_p(out.data_ptr()),
+                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == 0, opf.lib.opf_last_error().decode()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        nrm = lambda x: float(np.sqrt(np.sum(x * x)))
+        want = np.array([nrm(v - z), rho * nrm(z - zp), eps_rel * max(nrm(v), nrm(z)), eps_rel * nrm(l)])
+        assert np.all(np.abs(got - want) <= 1e-12 * np.abs(want)), (n, call, got, want)
