@@ -110,7 +110,17 @@ typedef struct opf_load {
 /* ------------------------------------------------------------- parameters */
 enum { OPF_CRIT_ABS = 0, OPF_CRIT_REL = 1, OPF_CRIT_BOTH = 2, OPF_CRIT_NEVER = 3 };
 enum { OPF_FP64 = 0, OPF_FP32 = 1 };
-enum { OPF_RES_PAPER = 0 };
+/* Residual form of Eq. (termination).  PAPER (as printed): the sum over
+ * components outside the norm, dres = rho sqrt(sum_s ||B_s^T (x_s -
+ * x_s_prev)||^2) and eps_dual = eps_rel sqrt(sum_s ||B_s^T lambda_s||^2);
+ * since B_s^T only places entries, these equal rho ||x_loc - x_loc_prev||
+ * and eps_rel ||lambda|| over the stacked locals.  TEXTBOOK: the sum inside
+ * the norm, dres = rho ||sum_s B_s^T (x_s - x_s_prev)|| and eps_dual =
+ * eps_rel ||sum_s B_s^T lambda_s|| (per global variable, the copies'
+ * changes and duals added up first).  pres and eps_prim are the same in
+ * both.  TEXTBOOK runs on the GRAPH and HOSTLOOP engines (AUTO picks GRAPH;
+ * PERSISTENT, batches, scenarios and the server answer OPF_ERR_INVALID_ARG). */
+enum { OPF_RES_PAPER = 0, OPF_RES_TEXTBOOK = 1 };
 enum { OPF_ENGINE_AUTO = 0, OPF_ENGINE_GRAPH = 1, OPF_ENGINE_HOSTLOOP = 2, OPF_ENGINE_PERSISTENT = 3 };
 
 /* Solve parameters.  criterion ABS: pres <= eps_abs_prim and dres <=
@@ -199,13 +209,30 @@ int32_t opf_problem_create(const opf_bus* buses, int32_t n_bus,
                            const opf_load* loads, int32_t n_load,
                            opf_problem** out);
 
+/* Decomposition into components (Eq. OurModel).  FINE: one component per
+ * bus, in-service line, load and generator.  PAPER: the decomposition of
+ * Section V-A -- one component per node of the feeder graph (a bus with its
+ * loads and generators) and one per in-service line, a leaf node (a bus
+ * with exactly one in-service line) being combined with that line, so S =
+ * nodes + lines - leaves (Table III).  Canonical orders under PAPER:
+ * components = non-leaf nodes (bus order), then in-service lines (line
+ * order); a node's locals = its bus locals, then each load's pd, qd (pb, qb
+ * and w are already there), generators adding none; a line with leaf ends =
+ * the line locals, then the from-end node's remaining locals if it is a
+ * leaf, then the to-end node's; rows stacked in the same order.
+ * opf_get_structure reports a node as kind 0 (bus) and a line component as
+ * kind 1, with the bus or line index.                                      */
+enum { OPF_DECOMP_FINE = 0, OPF_DECOMP_PAPER = 1 };
+
 /* Layout options for opf_problem_create_ex.  chunks = number of feeder
  * chunks (CTAs of the local update; 0 = automatic: about one per 4096 units
  * of n_s^2 + 4 n_s + 16, at most 296).  Batches give each instance a share
- * of the device so that all of them run co-resident.                      */
+ * of the device so that all of them run co-resident.  decomposition =
+ * OPF_DECOMP_FINE (default, 0) or OPF_DECOMP_PAPER.                        */
 typedef struct opf_create_options {
     int32_t chunks;
-    int32_t _reserved[7];
+    int32_t decomposition;
+    int32_t _reserved[6];
 } opf_create_options;
 
 /* opf_problem_create with layout options (NULL = defaults).                */

@@ -11,13 +11,20 @@ Follows Section II of the paper:
   VDLM-6..10 (three-phase delta).
 * Eq. (power_flow_eqns): powerloss-1/2 and voltage_mag_diff with M^p, M^q.
 * Eq. (LP_model): the global variable order [gens; w; loads; lines].
-* Eq. (OurModel) with the fine decomposition the hot path uses: one component
-  per bus, in-service line, load and generator.
+* Eq. (OurModel) with the fine decomposition the hot path uses by default:
+  one component per bus, in-service line, load and generator; or the
+  paper's decomposition of Section V-A ("paper"): one component per node of
+  the feeder graph (a bus together with its loads and generators) and one
+  per line, except that a leaf node is combined with the line that connects
+  it, so S = nodes + lines - leaves (Table III).
 
 Readings where the paper is silent: M^p/M^q of a line with fewer than three
 phases is the sub-block on its phases; delta loads must be three-phase (the
 paper writes VDLM-7..10 for phases 1, 2, 3 only); a variable counts as
-bounded only when both bounds are finite.
+bounded only when both bounds are finite.  Paper decomposition: a leaf is a
+bus with exactly one in-service line (graph degree one, the substation bus
+included when it has one line); when both ends of a line are leaves both
+are combined with it; a bus with no in-service line stays a node.
 
 Canonical orders (shared by contract with the library's state export):
 
@@ -25,12 +32,19 @@ Canonical orders (shared by contract with the library's state export):
   loads l: pb, qb, pd, qd (each over phases); in-service lines e:
   p_ij, q_ij, p_ji, q_ji (each over phases).
 * components: buses, in-service lines, loads, generators (input order).
+  Paper decomposition: nodes that are not leaves (bus order), then
+  in-service lines (line order), each combined with its leaf end(s).
 * bus i locals: w(P_i); for each in-service line touching i, in line order,
   the flow leaving i: p(P_e), q(P_e); loads at i: pb(P_l), qb(P_l);
   generators at i: pg(P_k), qg(P_k).
 * line locals: p_ij, q_ij, p_ji, q_ji (each over P_e), w_i(P_e), w_j(P_e).
 * load locals: pb, qb, pd, qd (each over P_l), w_i(P_l).
 * generator locals: pg(P_k), qg(P_k).
+* paper decomposition, combined parts: the locals of the parts concatenated
+  (node: bus, then its loads in load order, then its generators; line with
+  leaves: line, then the from-end node if a leaf, then the to-end node if a
+  leaf) keeping the first copy of a global that appears twice; rows of the
+  parts stacked in the same order.
 """
 from __future__ import annotations
 
@@ -320,8 +334,62 @@ def build(buses, lines, gens, loads) -> Model:
                  names, comps, tables)
 
 
-def build_feeder(f) -> Model:
-    return build(f.buses, f.lines, f.gens, f.loads)
+def combine(kind: int, index: int, parts) -> Component:
+    """One component from several (Section V-A): the union of their local
+    variables (first occurrence kept, so a global shared by two parts gets
+    one local copy) and all of their rows, stacked in order."""
+    gv = []
+    seen = {}
+    for c in parts:
+        for g in c.gvars:
+            if int(g) not in seen:
+                seen[int(g)] = len(gv)
+                gv.append(int(g))
+    rows, rhs = [], []
+    for c in parts:
+        for a in range(c.A.shape[0]):
+            r = np.zeros(len(gv))
+            for j, g in enumerate(c.gvars):
+                r[seen[int(g)]] += c.A[a, j]
+            rows.append(r)
+            rhs.append(c.b[a])
+    A = np.array(rows).reshape(len(rows), len(gv))
+    return Component(kind, index, np.array(gv, dtype=np.int64), A, np.array(rhs, dtype=np.float64))
+
+
+def paper_decomposition(model: Model, buses, lines, gens, loads) -> Model:
+    """Components of Section V-A from the fine ones: node = bus + its loads
+    + its generators; a leaf node (one in-service line) is combined with
+    that line; S = nodes + lines - leaves."""
+    fine = {(c.kind, c.index): c for c in model.comps}
+    nb = len(buses)
+    live = [e for e in range(len(lines)) if int(lines[e]["in_service"]) != 0]
+    degree = [0] * nb
+    for e in live:
+        degree[int(lines[e]["from_bus"])] += 1
+        degree[int(lines[e]["to_bus"])] += 1
+    node = {}
+    for i in range(nb):
+        parts = [fine[KIND_BUS, i]]
+        parts += [fine[KIND_LOAD, l] for l in range(len(loads)) if int(loads[l]["bus"]) == i]
+        parts += [fine[KIND_GEN, k] for k in range(len(gens)) if int(gens[k]["bus"]) == i]
+        node[i] = combine(KIND_BUS, i, parts)
+    leaf = [degree[i] == 1 for i in range(nb)]
+    comps = [node[i] for i in range(nb) if not leaf[i]]
+    for e in live:
+        i, j = int(lines[e]["from_bus"]), int(lines[e]["to_bus"])
+        parts = [fine[KIND_LINE, e]] + ([node[i]] if leaf[i] else []) + ([node[j]] if leaf[j] else [])
+        comps.append(combine(KIND_LINE, e, parts))
+    return dataclasses.replace(model, comps=comps)
+
+
+def build_feeder(f, decomposition: str = "fine") -> Model:
+    m = build(f.buses, f.lines, f.gens, f.loads)
+    if decomposition == "paper":
+        return paper_decomposition(m, f.buses, f.lines, f.gens, f.loads)
+    if decomposition != "fine":
+        raise ValueError(decomposition)
+    return m
 
 
 def stacked_A(model: Model):

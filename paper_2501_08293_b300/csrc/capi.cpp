@@ -132,10 +132,14 @@ int32_t opf_problem_create_ex(const opf_bus* buses, int32_t n_bus, const opf_lin
         if (!out) throw opf::Error(OPF_ERR_INVALID_ARG, "out is NULL");
         *out = nullptr;
         const int chunks = options ? options->chunks : 0;
+        const int decomp = options ? options->decomposition : OPF_DECOMP_FINE;
         if (chunks < 0 || chunks > 65536) throw opf::Error(OPF_ERR_INVALID_ARG, "chunks out of [0, 65536]");
+        if (decomp != OPF_DECOMP_FINE && decomp != OPF_DECOMP_PAPER)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "bad decomposition");
         opf_problem* p = new opf_problem();
         try {
             p->model = opf::build_model(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load);
+            if (decomp == OPF_DECOMP_PAPER) opf::paper_decomposition(p->model);
             p->ops.reserve(p->model.comps.size());
             p->canon_comp_ptr.assign(1, 0);
             for (const auto& c : p->model.comps) {
@@ -178,9 +182,24 @@ int32_t opf_update_lines(opf_problem* p, const int32_t* line_idx, const opf_line
             const int e = line_idx[k];
             if (e < 0 || e >= M.n_line || line_comp[e] < 0)
                 throw opf::Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": no in-service line there");
-            fresh.push_back(opf::line_update(M, records[k], e));
-            if (fresh.back().gvars != M.comps[line_comp[e]].gvars)
+            const opf::Component& cur = M.comps[line_comp[e]];
+            opf::Component nc = opf::line_update(M, records[k], e);
+            if (M.decomposition == OPF_DECOMP_PAPER) {
+                // a line with leaf ends: the line's locals and rows come first
+                // in its component; only those rows change
+                if (cur.n() < nc.n() || cur.m < nc.m || !std::equal(nc.gvars.begin(), nc.gvars.end(), cur.gvars.begin()))
+                    throw opf::Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": structure differs");
+                opf::Component merged = cur;
+                for (int r = 0; r < nc.m; ++r) {
+                    for (int c = 0; c < cur.n(); ++c)
+                        merged.A[(size_t)r * cur.n() + c] = c < nc.n() ? nc.A[(size_t)r * nc.n() + c] : 0.0;
+                    merged.b[r] = nc.b[r];
+                }
+                nc = std::move(merged);
+            } else if (nc.gvars != cur.gvars) {
                 throw opf::Error(OPF_ERR_INVALID_ARG, "line " + std::to_string(e) + ": structure differs");
+            }
+            fresh.push_back(std::move(nc));
         }
         if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "update before upload");
         std::vector<int> comps;
@@ -254,7 +273,8 @@ int32_t opf_admm_solve(opf_problem* p, const opf_params* prm, void* stream, opf_
         if (prm->max_iter < 0) throw opf::Error(OPF_ERR_INVALID_ARG, "max_iter < 0");
         if (prm->criterion < 0 || prm->criterion > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad criterion");
         if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
-        if (prm->residual_form != OPF_RES_PAPER) throw opf::Error(OPF_ERR_INVALID_ARG, "unsupported residual form");
+        if (prm->residual_form != OPF_RES_PAPER && prm->residual_form != OPF_RES_TEXTBOOK)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "bad residual form");
         if (prm->engine < 0 || prm->engine > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad engine");
         if (prm->adaptive_rho && !(prm->rb_mu > 1.0 && prm->rb_tau > 1.0))
             throw opf::Error(OPF_ERR_INVALID_ARG, "residual balancing needs rb_mu > 1 and rb_tau > 1");
@@ -496,7 +516,8 @@ int32_t opf_batch_solve(opf_batch* b, const opf_params* prm, int32_t n_params, v
             if (q.max_iter < 0 || q.criterion < 0 || q.criterion > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad max_iter or criterion");
             if (q.precision != prm[0].precision || (q.precision != OPF_FP64 && q.precision != OPF_FP32))
                 throw opf::Error(OPF_ERR_INVALID_ARG, "batch precision must be FP64 or FP32 for every instance");
-            if (q.residual_form != OPF_RES_PAPER) throw opf::Error(OPF_ERR_INVALID_ARG, "unsupported residual form");
+            if (q.residual_form != OPF_RES_PAPER)
+                throw opf::Error(OPF_ERR_INVALID_ARG, "batch: only the paper's residual form (OPF_RES_PAPER)");
             if (q.adaptive_rho && !(q.rb_mu > 1.0 && q.rb_tau > 1.0))
                 throw opf::Error(OPF_ERR_INVALID_ARG, "residual balancing needs rb_mu > 1 and rb_tau > 1");
         }
@@ -530,6 +551,8 @@ int32_t opf_scenarios_solve(opf_scenarios* sc, const opf_params* prm, void* stre
         if (!sc || !prm) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
         if (prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "scenarios: precision must be FP32");
         if (prm->adaptive_rho) throw opf::Error(OPF_ERR_INVALID_ARG, "scenarios: residual balancing not supported");
+        if (prm->residual_form != OPF_RES_PAPER)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "scenarios: only the paper's residual form (OPF_RES_PAPER)");
         if (!(prm->rho > 0.0) || prm->check_every < 1 || prm->max_iter < 0)
             throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
         opf::scenarios_solve(sc, *prm, (cudaStream_t)stream, infos);

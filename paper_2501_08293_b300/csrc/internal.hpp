@@ -42,6 +42,7 @@ struct Model {
     std::vector<int32_t> w_idx, pg_idx, qg_idx;                 // *3
     std::vector<int32_t> pij_idx, qij_idx, pji_idx, qji_idx;    // n_line*3
     std::vector<int32_t> pb_idx, qb_idx, pd_idx, qd_idx;        // n_load*3
+    int decomposition = OPF_DECOMP_FINE;
 };
 
 // Closed-form operator of one component (Eq. closed_2), P = -Abar.
@@ -113,6 +114,13 @@ struct Packed {
 
 Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
                   const opf_gen* gens, int ng, const opf_load* loads, int nd);
+// Section V-A: replace M's fine components by nodes (bus + its loads + its
+// generators) and lines, each leaf node (one in-service line) combined with
+// its line; canonical order: non-leaf nodes, then lines.
+void paper_decomposition(Model& M);
+// Rows and locals of the parts stacked into one component (first copy of a
+// global kept).
+Component combine_parts(int kind, int index, const std::vector<const Component*>& parts);
 Operator make_operator(const Component& c);
 // Line component of Eq. (power_flow_eqns) for in-service line e on the
 // global indices of M; line_update validates a new record for line e (same

@@ -10,6 +10,14 @@
 //   gen   no rows
 // The ordering of globals, components and locals is the canonical order
 // documented in opf_admm.h.
+//
+// Decomposition of Section V-A (OPF_DECOMP_PAPER): one component per node
+// of the feeder graph -- a bus together with its loads and generators --
+// and one per in-service line, except that a node with exactly one
+// in-service line (a leaf) is combined with that line, so S = nodes + lines
+// - leaves (Table III).  A combined component's locals are its parts'
+// locals in order, a global already present keeping its first local; its
+// rows are its parts' rows stacked in the same order.
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -391,6 +399,68 @@ Model build_model(const opf_bus* buses, int nb, const opf_line* lines, int nl,
         M.comps.push_back(std::move(C));
     }
     return M;
+}
+
+Component combine_parts(int kind, int index, const std::vector<const Component*>& parts) {
+    Component C;
+    C.kind = kind;
+    C.index = index;
+    std::map<int32_t, int> at;           // global -> local position in C
+    for (const Component* q : parts)
+        for (int32_t g : q->gvars)
+            if (at.emplace(g, (int)C.gvars.size()).second) C.gvars.push_back(g);
+    const int n = C.n();
+    for (const Component* q : parts) {
+        const int qn = q->n();
+        for (int r = 0; r < q->m; ++r) {
+            C.A.resize(C.A.size() + n, 0.0);
+            double* row = &C.A[(size_t)C.m * n];
+            for (int c = 0; c < qn; ++c) row[at[q->gvars[c]]] += q->A[(size_t)r * qn + c];
+            C.b.push_back(q->b[r]);
+            ++C.m;
+        }
+    }
+    return C;
+}
+
+void paper_decomposition(Model& M) {
+    const int nb = M.n_bus, nl = M.n_line;
+    std::vector<int> bus_comp(nb, -1), line_comp(nl, -1);
+    std::vector<std::vector<int>> parts_of(nb);     // loads, then generators, at each bus
+    for (int c = 0; c < (int)M.comps.size(); ++c) {
+        const Component& C = M.comps[c];
+        if (C.kind == COMP_BUS) bus_comp[C.index] = c;
+        else if (C.kind == COMP_LINE) line_comp[C.index] = c;
+    }
+    for (int c = 0; c < (int)M.comps.size(); ++c)
+        if (M.comps[c].kind == COMP_LOAD) parts_of[M.load_bus[M.comps[c].index]].push_back(c);
+    for (int c = 0; c < (int)M.comps.size(); ++c)
+        if (M.comps[c].kind == COMP_GEN) parts_of[M.gen_bus[M.comps[c].index]].push_back(c);
+    std::vector<int> degree(nb, 0);
+    for (int e = 0; e < nl; ++e)
+        if (line_comp[e] >= 0) {
+            ++degree[M.line_from[e]];
+            ++degree[M.line_to[e]];
+        }
+    std::vector<Component> node(nb);
+    for (int i = 0; i < nb; ++i) {
+        std::vector<const Component*> parts{&M.comps[bus_comp[i]]};
+        for (int c : parts_of[i]) parts.push_back(&M.comps[c]);
+        node[i] = combine_parts(COMP_BUS, i, parts);
+    }
+    std::vector<Component> out;
+    for (int i = 0; i < nb; ++i)
+        if (degree[i] != 1) out.push_back(std::move(node[i]));
+    for (int e = 0; e < nl; ++e) {
+        if (line_comp[e] < 0) continue;
+        const int i = M.line_from[e], j = M.line_to[e];
+        std::vector<const Component*> parts{&M.comps[line_comp[e]]};
+        if (degree[i] == 1) parts.push_back(&node[i]);
+        if (degree[j] == 1) parts.push_back(&node[j]);
+        out.push_back(combine_parts(COMP_LINE, e, parts));
+    }
+    M.comps = std::move(out);
+    M.decomposition = OPF_DECOMP_PAPER;
 }
 
 }  // namespace opf

@@ -2,7 +2,9 @@
 //
 // 1. Component order for locality: a depth-first walk over the feeder; each
 //    bus brings its own component, the in-service line that reaches it
-//    (emitted when its second end is visited), its loads and its generators.
+//    (emitted when its second end is visited), its loads and its generators
+//    (under the paper's decomposition a node already holds its loads and
+//    generators, and a leaf node travels with its line).
 // 2. The order is cut into `nblocks` contiguous chunks of about equal work
 //    (n_s^2 + 4 n_s + 16 per component); chunk b is processed by CTA b.
 // 3. Inside a chunk, components are sorted by decreasing n and packed into
@@ -60,7 +62,7 @@ std::vector<int> locality_order(const Model& M) {
             stack.pop_back();
             if (seen[u]) continue;
             seen[u] = 1;
-            order.push_back(bus_comp[u]);
+            if (bus_comp[u] >= 0) order.push_back(bus_comp[u]);   // a leaf combined with its line has none
             for (int e : lines_at[u]) {
                 const int v = M.line_from[e] == u ? M.line_to[e] : M.line_from[e];
                 if (seen[v] && !line_done[e]) {          // second end visited

@@ -35,6 +35,8 @@ struct Ctl {
     int32_t adaptive;             // residual balancing on
     int32_t rho_changes;
     double rb_mu, rb_tau;
+    int32_t res_form;             // OPF_RES_PAPER or OPF_RES_TEXTBOOK (graph / host-loop engines)
+    int32_t _pad_res;
 };
 enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_MAXITER = 2, CTL_NUMERIC = 3, CTL_TIMEOUT = 4 };
 
@@ -69,7 +71,9 @@ struct View {
     unsigned long long* phase;        // per CTA: interior, wait, boundary, release+check (ns)
     unsigned long long* mbox;         // tagged boundary values, 2 slots x nl x (1 f32 | 2 f64) words
     Ctl* ctl;
-    int32_t ng, nl, nblocks;
+    double* tdz;                      // textbook residual form: x_s - x_s(prev) per local on a check iteration
+    double* tpart;                    // textbook residual form: 2 partial sums per global-update block
+    int32_t ng, nl, nblocks, nzb;
 };
 
 struct DevPrec {            // one precision's arrays
@@ -130,6 +134,8 @@ struct opf_problem {
     int32_t* flags = nullptr;
     double* cost = nullptr;
     double* partials = nullptr;
+    double* tdz = nullptr;
+    double* tpart = nullptr;
     unsigned long long* phase = nullptr;
     unsigned long long* mbox = nullptr;
     opf::Ctl* ctl = nullptr;
@@ -140,5 +146,5 @@ struct opf_problem {
     int skip_block = -1;                              // test hook
     int force_variant = 0;                            // persistent kernel: 0 auto, 1 global, 2 shared
     int profile_phases = 0;
-    std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision, K)
+    std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision + 2 * residual form, K)
 };

@@ -286,8 +286,12 @@ int32_t opf_server_create(const opf_server_config* cfg, opf_server** out) {
         *out = nullptr;
         if (cfg->max_active < 1 || cfg->round_iters < 1 || cfg->device_budget_bytes < 1)
             throw opf::Error(OPF_ERR_INVALID_ARG, "bad server configuration");
+        if (cfg->params.check_every < 1 || cfg->params.check_every > 4096)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "params.check_every out of [1, 4096]");
         if (cfg->round_iters % cfg->params.check_every)
             throw opf::Error(OPF_ERR_INVALID_ARG, "round_iters must be a multiple of params.check_every");
+        if (cfg->params.residual_form != OPF_RES_PAPER)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "server: only the paper's residual form (OPF_RES_PAPER)");
         opf_server* S = new opf_server();
         S->cfg = *cfg;
         int32_t cap = 0;

@@ -281,10 +281,12 @@ __device__ __forceinline__ T global_value(const View<T>& v, int g, const T* xr, 
 
 // Local update + dual update of one tile (Eq. closed_2, Eq. ADMM-3).
 // getv(j, meta) returns the gathered global value (B_s x)_j for local j.
+// dzout (optional, check iterations only): x_s - x_s(prev) per local in
+// FP64, for the textbook residual form.
 template <typename T, typename GETV>
 __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int lane, T rho, T inv_rho,
                                             const T* xr, const T* lr, T* xw, T* lw, bool want, double* acc,
-                                            T* us, GETV getv) {
+                                            T* us, GETV getv, double* dzout = nullptr) {
     if (!tl.big) {
         const int L = tl.L, nmax = tl.nmax;
         const bool act = lane < L;
@@ -309,6 +311,7 @@ __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int
                 const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
                 acc[0] += pr * pr; acc[1] += dz * dz;
                 acc[2] += (double)vv * (double)vv; acc[3] += (double)xn * (double)xn; acc[4] += (double)ln * (double)ln;
+                if (dzout) dzout[j] = dz;
             }
         }
     } else {
@@ -333,6 +336,7 @@ __device__ __forceinline__ void tile_update(const View<T>& v, const Tile tl, int
                 const double pr = (double)vv - (double)xn, dz = (double)xn - (double)xo;
                 acc[0] += pr * pr; acc[1] += dz * dz;
                 acc[2] += (double)vv * (double)vv; acc[3] += (double)xn * (double)xn; acc[4] += (double)ln * (double)ln;
+                if (dzout) dzout[j] = dz;
             }
         }
         __syncwarp();
@@ -442,10 +446,11 @@ __device__ __forceinline__ void x_chunk(const View<T>& v, const int b, const int
     // boundary tiles first, then interior ones: the order of every engine
     // (the persistent kernel publishes boundary values early), so the
     // residual partial sums agree bit for bit
+    double* dzo = (want && ctl->res_form == OPF_RES_TEXTBOOK) ? v.tdz : nullptr;
     for (int t = bi.tileb + warp; t < bi.tile1; t += kXWarps)
-        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
+        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv, dzo);
     for (int t = bi.tile0 + warp; t < bi.tileb; t += kXWarps)
-        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv);
+        tile_update<T>(v, v.tiles[t], lane, rho, inv_rho, v.xl, v.lam, v.xl, v.lam, want, acc, us[warp], getv, dzo);
     if (!want) return;
     cta_partials(acc, red, v.partials + (size_t)b * 8);
 }
@@ -453,6 +458,41 @@ __device__ __forceinline__ void x_chunk(const View<T>& v, const int b, const int
 template <typename T>
 __global__ void __launch_bounds__(kXWarps * 32) x_kernel(View<T> v, int q) {
     x_chunk(v, blockIdx.x, q);
+}
+
+// Textbook residual form of Eq. (termination) (the sum over components
+// inside the norm): per global i, the copies' changes and duals summed in
+// CSR order, D_i = sum_j (x_j - x_j(prev)), L_i = sum_j lambda_j; each block
+// writes sum_i D_i^2 and sum_i L_i^2 over its globals (fixed-order tree), so
+// dres = rho sqrt(sum D^2) and eps_dual = eps_rel sqrt(sum L^2).
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) textbook_kernel(View<T> v) {
+    const Ctl* ctl = v.ctl;
+    __shared__ double sh[2][kZThreads];
+    if (ctl->iter >= ctl->max_iter) return;       // no iteration ran in this body
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double d = 0, l = 0;
+    if (i < v.ng) {
+        for (int q = v.gptr[i]; q < v.gptr[i + 1]; ++q) {
+            const int j = v.gcol[q];
+            d += v.tdz[j];
+            l += (double)v.lam[j];
+        }
+    }
+    sh[0][threadIdx.x] = d * d;
+    sh[1][threadIdx.x] = l * l;
+    __syncthreads();
+    for (int w = kZThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        v.tpart[2 * blockIdx.x] = sh[0][0];
+        v.tpart[2 * blockIdx.x + 1] = sh[1][0];
+    }
 }
 
 // Residual check after a graph body (fixed-order sum, Eq. termination);
@@ -466,6 +506,15 @@ __device__ __forceinline__ int finalize_body(const View<T>& v) {
     __shared__ double tot[5];
     static_assert(kFinThreads == kXWarps * 32, "finalize reduction layout");
     if (ndone > 0) sum_partials_small(v.partials, v.nblocks, red, tot);
+    if (ndone > 0 && ctl->res_form == OPF_RES_TEXTBOOK && threadIdx.x == 0) {
+        double d = 0, l = 0;
+        for (int b = 0; b < v.nzb; ++b) {
+            d += __ldcg(v.tpart + 2 * b);
+            l += __ldcg(v.tpart + 2 * b + 1);
+        }
+        tot[1] = d;
+        tot[4] = l;
+    }
     if (threadIdx.x != 0) return 0;
     const int it = iter + ndone;
     ctl->iter = it;
@@ -1396,6 +1445,7 @@ struct Arena {
 struct Layout {
     size_t lo, hi, invk, cik, zg, lo32, hi32, invk32, cik32, zg32;
     size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, phase, ctl, mbox;
+    size_t tdz, tpart;
     size_t xl, lam, xl2, lam2, bbar, xl0, xl32, lam32, xl2_32, lam2_32, bbar32, xl0_32, P64, P32;
     size_t total;
 };
@@ -1419,6 +1469,8 @@ Layout layout_of(const opf_problem* p) {
     L.partials = a.take<double>((size_t)k.nblocks * 16); L.ctl = a.take<Ctl>(1);   // two check slots
     L.phase = a.take<unsigned long long>((size_t)k.nblocks * 4);
     L.mbox = a.take<unsigned long long>((size_t)k.nl * 4);     // 2 slots x 2 words (f64)
+    L.tdz = a.take<double>(std::max(1, k.nl));
+    L.tpart = a.take<double>((size_t)2 * ((k.ng + kZThreads - 1) / kZThreads + 1));
     L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.xl2 = a.take<double>(k.nl); L.lam2 = a.take<double>(k.nl);
     L.bbar = a.take<double>(k.nl); L.xl0 = a.take<double>(k.nl);
     L.xl32 = a.take<float>(k.nl); L.lam32 = a.take<float>(k.nl); L.xl2_32 = a.take<float>(k.nl); L.lam2_32 = a.take<float>(k.nl);
@@ -1440,7 +1492,9 @@ View<T> view_of(const opf_problem* p, const DevPrec& d) {
     v.nbrs = p->nbrs; v.hcp = p->hcp; v.hci = p->hci; v.flags = p->flags;
     v.P = (const T*)d.P; v.cost = p->cost; v.partials = p->partials; v.phase = p->phase; v.ctl = p->ctl;
     v.mbox = p->mbox;
+    v.tdz = p->tdz; v.tpart = p->tpart;
     v.ng = p->pk.ng; v.nl = p->pk.nl; v.nblocks = p->pk.nblocks;
+    v.nzb = (p->pk.ng + kZThreads - 1) / kZThreads;
     return v;
 }
 
@@ -1467,21 +1521,22 @@ void enqueue_init(opf_problem* p, cudaStream_t s) {
 }
 
 template <typename T>
-void enqueue_iterations(opf_problem* p, int K, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+void enqueue_iterations(opf_problem* p, int K, int form, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
     View<T> v = view_of<T>(p, prec_of<T>(p));
     const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
     for (int q = 0; q < K; ++q) {
         z_kernel<T><<<zb, kZThreads, 0, s>>>(v, q);
         x_kernel<T><<<p->pk.nblocks, kXWarps * 32, 0, s>>>(v, q);
     }
+    if (form == OPF_RES_TEXTBOOK) textbook_kernel<T><<<zb, kZThreads, 0, s>>>(v);
     finalize_kernel<T><<<1, kFinThreads, 0, s>>>(v, h, use_cond);
     OPF_CUDA(cudaGetLastError());
 }
 
 template <typename T>
-GraphEntry& get_graph(opf_problem* p, int K) {
+GraphEntry& get_graph(opf_problem* p, int K, int form) {
     const int prec = sizeof(T) == 8 ? OPF_FP64 : OPF_FP32;
-    auto key = std::make_pair(prec, K);
+    auto key = std::make_pair(prec + 2 * form, K);
     auto it = p->graphs.find(key);
     if (it != p->graphs.end()) return it->second;
     GraphEntry g;
@@ -1500,7 +1555,7 @@ GraphEntry& get_graph(opf_problem* p, int K) {
     OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     OPF_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     try {
-        enqueue_iterations<T>(p, K, cs, h, 1);
+        enqueue_iterations<T>(p, K, form, cs, h, 1);
     } catch (...) {
         cudaGraph_t tmp;
         cudaStreamEndCapture(cs, &tmp);
@@ -1628,7 +1683,11 @@ void launch_persistent(opf_problem* p, cudaStream_t s) {
 template <typename T>
 void run_solve(opf_problem* p, const opf_params& prm, cudaStream_t s) {
     int engine = prm.engine;
-    if (engine == OPF_ENGINE_AUTO) engine = persistent_fits<T>(p) ? OPF_ENGINE_PERSISTENT : OPF_ENGINE_GRAPH;
+    const int form = prm.residual_form;
+    if (engine == OPF_ENGINE_AUTO)
+        engine = (form == OPF_RES_PAPER && persistent_fits<T>(p)) ? OPF_ENGINE_PERSISTENT : OPF_ENGINE_GRAPH;
+    if (engine == OPF_ENGINE_PERSISTENT && form != OPF_RES_PAPER)
+        throw Error(OPF_ERR_INVALID_ARG, "persistent engine: only the paper's residual form (OPF_RES_PAPER)");
     if (engine == OPF_ENGINE_PERSISTENT) {
         if (!persistent_fits<T>(p))
             throw Error(OPF_ERR_INVALID_ARG, "persistent engine: the chunks do not fit co-resident on this device");
@@ -1636,13 +1695,13 @@ void run_solve(opf_problem* p, const opf_params& prm, cudaStream_t s) {
         OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         OPF_CUDA(cudaStreamSynchronize(s));
     } else if (engine == OPF_ENGINE_GRAPH) {
-        GraphEntry& g = get_graph<T>(p, prm.check_every);
+        GraphEntry& g = get_graph<T>(p, prm.check_every, form);
         OPF_CUDA(cudaGraphLaunch(g.exec, s));
         OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         OPF_CUDA(cudaStreamSynchronize(s));
     } else {
         for (;;) {
-            enqueue_iterations<T>(p, prm.check_every, s, 0, 0);
+            enqueue_iterations<T>(p, prm.check_every, form, s, 0, 0);
             OPF_CUDA(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
             OPF_CUDA(cudaStreamSynchronize(s));
             if (p->ctl_host->stop) break;
@@ -1753,6 +1812,8 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     p->cost = (double*)(a + L.cost); p->partials = (double*)(a + L.partials);
     p->phase = (unsigned long long*)(a + L.phase);
     p->mbox = (unsigned long long*)(a + L.mbox);
+    p->tdz = (double*)(a + L.tdz);
+    p->tpart = (double*)(a + L.tpart);
     p->ctl = (Ctl*)(a + L.ctl);
     if (!p->ctl_host) OPF_CUDA(cudaMallocHost((void**)&p->ctl_host, sizeof(Ctl)));
     std::memset(p->ctl_host, 0, sizeof(Ctl));
@@ -1822,6 +1883,7 @@ int32_t device_solve(opf_problem* p, const opf_params& prm, cudaStream_t s, opf_
     c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
     c.adaptive = prm.adaptive_rho; c.rb_mu = prm.rb_mu; c.rb_tau = prm.rb_tau; c.rho_changes = 0;
     c.profile_phases = p->profile_phases;
+    c.res_form = prm.residual_form;
     *p->ctl_host = c;
     OPF_CUDA(cudaMemcpyAsync(p->ctl, p->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     if (prm.max_iter > 0) {
@@ -1945,6 +2007,7 @@ Ctl solve_ctl(const opf_problem* p, const opf_params& prm, const Ctl& cur) {
     c.arrive = 0; c.decided = 0; c.abort = 0; c.halt = 0; c.timeout_where = 0;
     c.timeout_ns = p->timeout_ns; c.skip_block = p->skip_block;
     c.adaptive = prm.adaptive_rho; c.rb_mu = prm.rb_mu; c.rb_tau = prm.rb_tau; c.rho_changes = 0;
+    c.res_form = OPF_RES_PAPER;
     return c;
 }
 

@@ -23,6 +23,8 @@ lib = C.CDLL(_LIB_PATH)
 OK, NOT_CONVERGED = 0, 1
 CRIT_ABS, CRIT_REL, CRIT_BOTH, CRIT_NEVER = 0, 1, 2, 3
 FP64, FP32 = 0, 1
+RES_PAPER, RES_TEXTBOOK = 0, 1
+DECOMP_FINE, DECOMP_PAPER = 0, 1
 ENGINE_AUTO, ENGINE_GRAPH, ENGINE_HOSTLOOP, ENGINE_PERSISTENT = 0, 1, 2, 3
 
 
@@ -35,7 +37,7 @@ class Params(C.Structure):
 
 
 class CreateOptions(C.Structure):
-    _fields_ = [("chunks", C.c_int32), ("_reserved", C.c_int32 * 7)]
+    _fields_ = [("chunks", C.c_int32), ("decomposition", C.c_int32), ("_reserved", C.c_int32 * 6)]
 
 
 class Info(C.Structure):
@@ -199,7 +201,8 @@ def component_operator(A, b):
 class Problem:
     """One feeder: host precompute at construction, device arena from torch."""
 
-    def __init__(self, buses, lines, gens, loads, *, device=None, stream=None, upload=True, chunks: int = 0):
+    def __init__(self, buses, lines, gens, loads, *, device=None, stream=None, upload=True, chunks: int = 0,
+                 decomposition: int = DECOMP_FINE):
         self._h = C.c_void_p()
         self._arrays = [np.ascontiguousarray(a) for a in (buses, lines, gens, loads)]
         for a, dt in zip(self._arrays, (_F.BUS_DTYPE, _F.LINE_DTYPE, _F.GEN_DTYPE, _F.LOAD_DTYPE)):
@@ -208,6 +211,7 @@ class Problem:
         b, l, g, d = self._arrays
         opts = CreateOptions()
         opts.chunks = int(chunks)
+        opts.decomposition = int(decomposition)
         _check(lib.opf_problem_create_ex(b.ctypes.data, len(b), l.ctypes.data, len(l), g.ctypes.data, len(g),
                                          d.ctypes.data, len(d), C.byref(opts), C.byref(self._h)),
                "opf_problem_create_ex")

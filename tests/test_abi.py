@@ -55,15 +55,18 @@ def test_record_layouts(opf):
     assert p.rho == 100.0 and p.eps_abs_prim == 1e-4 and p.eps_rel == 1e-3
 
 
+@pytest.mark.parametrize("decomp", ["fine", "paper"])
 @pytest.mark.parametrize("maker", [lambda: F.feeder_13(1), lambda: F.feeder_123(2),
                                    lambda: F.feeder_tiny(6, 3), lambda: F.feeder_8500(1, n_bus=1500)])
-def test_host_precompute_matches_oracle(opf, maker):
+def test_host_precompute_matches_oracle(opf, maker, decomp):
     """Independent C++ assembly + QR projector vs the oracle's rows + RREF +
-    Cholesky: same canonical structure, ranks and operators (P = -Abar)."""
+    Cholesky: same canonical structure, ranks and operators (P = -Abar), for
+    the fine decomposition and the paper's (Section V-A)."""
     from oracle import model as OM, precompute as OP
     f = maker()
-    p = opf.Problem.from_feeder(f, upload=False)
-    m = OM.build_feeder(f)
+    p = opf.Problem.from_feeder(f, upload=False,
+                                decomposition=opf.DECOMP_PAPER if decomp == "paper" else opf.DECOMP_FINE)
+    m = OM.build_feeder(f, decomp)
     pre = OP.precompute(m)
     st = p.structure()
     assert p.dims.n_global == m.n and p.dims.n_local == m.nl and p.dims.n_comp == m.S

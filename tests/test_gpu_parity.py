@@ -377,3 +377,97 @@ def test_nonblocking_checks_return_the_deciding_iterate(opf, prec):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
         assert ia.pres == ib.pres and ia.dres == ib.dres and ia.objective == ib.objective
+
+
+@pytest.mark.parametrize("engine", ["graph", "hostloop", "auto"])
+def test_textbook_residual_form_matches_oracle(opf, engine):
+    """residual_form TEXTBOOK (the sum over components inside the norm of
+    Eq. termination): the iterates are those of the paper form, the four
+    residual quantities equal the oracle's textbook values at 1e-9 at every
+    check, and a REL-criterion solve stops at the oracle's iteration.  The
+    persistent engine refuses the form."""
+    from oracle import admm as OA
+    eng = {"graph": opf.ENGINE_GRAPH, "hostloop": opf.ENGINE_HOSTLOOP, "auto": opf.ENGINE_AUTO}[engine]
+    f = F.feeder_123(1)
+    p = opf.Problem.from_feeder(f)
+    m, pre, s = oracle_solver(f, 100.0)
+    done = 0
+    for t in (1, 7, 60, 400):
+        info = p.solve(opf.default_params(criterion=opf.CRIT_NEVER, max_iter=t - done, check_every=t - done,
+                                          warm_start=int(done > 0), residual_form=opf.RES_TEXTBOOK, engine=eng))
+        for _ in range(t - done):
+            r = s.step(form=OA.RES_TEXTBOOK)
+        done = t
+        xg, xl, lam = p.state()
+        assert rel(xg, s.x) <= TOL and rel(xl, s.z) <= TOL and rel(lam, s.lam) <= TOL
+        for k in ("pres", "dres", "eps_prim", "eps_dual"):
+            assert abs(getattr(info, k) - getattr(r, k)) <= TOL * abs(getattr(r, k)), (t, k, getattr(info, k),
+                                                                                     getattr(r, k))
+    # the two forms differ (a copy's change is spread over its siblings)
+    rp = s.residuals(s.B @ s.x, s.z, s.z, s.lam, form=OA.RES_PAPER)
+    assert abs(rp.eps_dual - r.eps_dual) > 1e-6 * r.eps_dual
+    # stopping on the paper's relative criterion with the textbook norms
+    m, pre, s2 = oracle_solver(f, 100.0)
+    o = s2.run(200000, criterion=OA.CRIT_REL, form=OA.RES_TEXTBOOK, check_every=10)
+    info = p.solve(opf.default_params(criterion=opf.CRIT_REL, max_iter=200000, check_every=10,
+                                      residual_form=opf.RES_TEXTBOOK, engine=eng))
+    assert info.status == opf.OK and info.iters == o["iters"] and info.first_rel_iter == o["first_rel"]
+    if engine == "graph":
+        with pytest.raises(opf.OpfError) as ei:
+            p.solve(opf.default_params(residual_form=opf.RES_TEXTBOOK, engine=opf.ENGINE_PERSISTENT))
+        assert ei.value.status == -1
+    p.close()
+
+
+@pytest.mark.parametrize("engine", ["graph", "persistent"])
+@pytest.mark.parametrize("maker,rho", [(lambda: F.feeder_13(1), 100.0), (lambda: F.feeder_123(1), 10.0)])
+def test_paper_decomposition_parity(opf, engine, maker, rho):
+    """The paper's decomposition (Section V-A: nodes with their loads and
+    generators, leaf nodes combined with their lines) through the C ABI
+    against the oracle's, per iterate at 1e-9 (normwise and element-wise)."""
+    from oracle import admm as OA, model as OM, precompute as OP
+    eng = opf.ENGINE_GRAPH if engine == "graph" else opf.ENGINE_PERSISTENT
+    f = maker()
+    p = opf.Problem.from_feeder(f, decomposition=opf.DECOMP_PAPER)
+    m = OM.build_feeder(f, "paper")
+    s = OA.ADMM(m, OP.precompute(m), rho)
+    assert p.dims.n_comp == m.S and p.dims.n_local == m.nl
+    done = 0
+    for t in (1, 2, 10, 300, 1001):
+        info = p.solve(opf.default_params(rho=rho, criterion=opf.CRIT_NEVER, max_iter=t - done,
+                                          check_every=min(50, t - done), warm_start=int(done > 0), engine=eng))
+        for _ in range(t - done):
+            r = s.step()
+        done = t
+        xg, xl, lam = p.state()
+        assert rel(xg, s.x) <= TOL and rel(xl, s.z) <= TOL and rel(lam, s.lam) <= TOL, t
+        assert abs(info.pres - r.pres) <= TOL * max(r.pres, 1e-6)
+        assert abs(info.dres - r.dres) <= TOL * max(r.dres, 1e-6)
+    p.close()
+
+
+def test_paper_decomposition_8500_class(opf):
+    """Full-size feeder under the paper's decomposition: 200 FP64 iterations
+    against the oracle, and an FP32 solve of the 123-bus feeder to ABS 1e-4
+    whose objective is within 1e-4 of the fine decomposition's."""
+    from oracle import admm as OA, model as OM, precompute as OP
+    f = F.feeder_8500(1)
+    p = opf.Problem.from_feeder(f, decomposition=opf.DECOMP_PAPER)
+    m = OM.build_feeder(f, "paper")
+    s = OA.ADMM(m, OP.precompute(m), 100.0)
+    info = p.solve(opf.default_params(criterion=opf.CRIT_NEVER, max_iter=200, check_every=50))
+    for _ in range(200):
+        r = s.step()
+    xg, xl, lam = p.state()
+    assert rel(xg, s.x) <= TOL and rel(xl, s.z) <= TOL and rel(lam, s.lam) <= TOL
+    assert abs(info.pres - r.pres) <= TOL * r.pres
+    p.close()
+    g = F.feeder_123(1)
+    objs = []
+    for d in (opf.DECOMP_FINE, opf.DECOMP_PAPER):
+        q = opf.Problem.from_feeder(g, decomposition=d)
+        inf = q.solve(opf.default_params(rho=10.0, precision=opf.FP32, max_iter=400000))
+        assert inf.status == opf.OK
+        objs.append(inf.objective)
+        q.close()
+    assert abs(objs[1] - objs[0]) <= 1e-4 * abs(objs[0])

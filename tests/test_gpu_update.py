@@ -47,16 +47,19 @@ def changed_lines(f, rng, count):
     return idx, rec
 
 
+@pytest.mark.parametrize("decomp", [0, 1])
 @pytest.mark.parametrize("maker", [lambda: F.feeder_123(1), lambda: F.feeder_8500(2, n_bus=1500)])
-def test_device_operators_match_host_precompute(opf, maker):
+def test_device_operators_match_host_precompute(opf, maker, decomp):
+    """Fine decomposition (line components) and the paper's (a line may be
+    combined with its leaf node: only the line's rows change)."""
     f = maker()
     rng = np.random.default_rng(5)
     idx, rec = changed_lines(f, rng, 12)
-    p = opf.Problem.from_feeder(f)
+    p = opf.Problem.from_feeder(f, decomposition=decomp)
     p.update_lines(idx, rec)
     g = f.copy()
     g.lines[idx] = rec
-    q = opf.Problem.from_feeder(g, upload=False)
+    q = opf.Problem.from_feeder(g, upload=False, decomposition=decomp)
     st = p.structure()
     line_comp = {int(e): s for s, (k, e) in enumerate(zip(st["kind"], st["index"])) if k == 1}
     for e in idx:
@@ -99,3 +102,32 @@ def test_warm_solve_after_update_follows_fresh_problem(opf, prec):
     assert abs(ia.objective - ib.objective) <= 1e-6 * abs(ib.objective)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("decomp", [0, 1])
+def test_warm_solve_after_update_matches_oracle(opf, decomp):
+    """After opf_update_lines the warm solve is Algorithm 1 on the updated
+    model continued from the same local iterate and duals: compared per
+    iterate with the FP64 oracle built from the new records (1e-9)."""
+    from oracle import admm as OA, model as OM, precompute as OP
+    f = F.feeder_123(1)
+    rng = np.random.default_rng(11)
+    idx, rec = changed_lines(f, rng, 10)
+    prm = opf.default_params(rho=10.0, criterion=opf.CRIT_NEVER, max_iter=200, check_every=50)
+    a = opf.Problem.from_feeder(f, decomposition=decomp)
+    a.solve(prm)
+    _, xl, lam = a.state()
+    a.update_lines(idx, rec)
+    prm.warm_start = 1
+    info = a.solve(prm)
+    g = f.copy()
+    g.lines[idx] = rec
+    m = OM.build_feeder(g, "paper" if decomp else "fine")
+    s = OA.ADMM(m, OP.precompute(m), 10.0)
+    s.z, s.lam = xl.copy(), lam.copy()
+    for _ in range(200):
+        r = s.step()
+    xg2, xl2, lam2 = a.state()
+    assert rel(xg2, s.x) <= 1e-9 and rel(xl2, s.z) <= 1e-9 and rel(lam2, s.lam) <= 1e-9
+    assert abs(info.pres - r.pres) <= 1e-9 * r.pres
+    a.close()

@@ -556,3 +556,71 @@ def test_residual_balancing_equals_restart_at_new_rho():
             b.step()
     assert b.t == a.t == T and b.rho == ref["rho"]
     assert np.array_equal(b.x, a.x) and np.array_equal(b.z, a.z) and np.array_equal(b.lam, a.lam)
+
+
+def _leaves_and_nodes(f):
+    live = np.flatnonzero(f.lines["in_service"] == 1)
+    deg = np.zeros(f.n_bus, dtype=int)
+    for e in live:
+        deg[int(f.lines["from_bus"][e])] += 1
+        deg[int(f.lines["to_bus"][e])] += 1
+    return live, deg
+
+
+@pytest.mark.parametrize("maker", [lambda: F.feeder_13(1), lambda: F.feeder_123(2), lambda: F.feeder_tiny(6, 3),
+                                   lambda: F.feeder_8500(1, n_bus=2000)])
+def test_paper_decomposition_counts(maker):
+    """Section V-A / Table III: with the paper's decomposition S = nodes +
+    lines - leaves (a leaf = a node with one in-service line); rows are
+    neither lost nor added (sum m_s equal to the fine decomposition's); and
+    every local copy that the combination removes is one that two parts
+    shared: a load shares pb, qb, w with its bus (3 |P_l|), a generator pg,
+    qg (2 |P_k|), a leaf node the flows leaving it and its w with its line
+    (3 |P_e|), so sum n_s drops by exactly that."""
+    f = maker()
+    fine = OM.build_feeder(f)
+    paper = OM.build_feeder(f, "paper")
+    live, deg = _leaves_and_nodes(f)
+    leaves = int(np.sum(deg == 1))
+    assert paper.S == f.n_bus + len(live) - leaves
+    assert sum(c.A.shape[0] for c in paper.comps) == sum(c.A.shape[0] for c in fine.comps)
+    npl = lambda mask: bin(int(mask)).count("1")
+    drop = sum(3 * npl(d["phases"]) for d in f.loads) + sum(2 * npl(g["phases"]) for g in f.gens)
+    for e in live:
+        for end in ("from_bus", "to_bus"):
+            if deg[int(f.lines[end][e])] == 1:
+                drop += 3 * npl(f.lines["phases"][e])
+    assert paper.nl == fine.nl - drop
+    # every global keeps at least one copy, and no component copies a global twice
+    for c in paper.comps:
+        assert len(set(c.gvars.tolist())) == len(c.gvars)
+    assert set(np.concatenate([c.gvars for c in paper.comps]).tolist()) == set(range(paper.n))
+
+
+@pytest.mark.parametrize("maker", [lambda: F.feeder_13(1), lambda: F.feeder_123(2)])
+def test_paper_decomposition_is_the_same_lp(maker):
+    """Both decompositions split the same centralized rows of Eq. (LP_model):
+    the stacked rows A_s B_s (mapped to global columns) are the same set of
+    rows, with the same right-hand sides."""
+    f = maker()
+    A1, b1 = OM.stacked_A(OM.build_feeder(f))
+    A2, b2 = OM.stacked_A(OM.build_feeder(f, "paper"))
+    key = lambda A, b: sorted((tuple(sorted(zip(A.getrow(r).indices.tolist(), A.getrow(r).data.tolist()))), b[r])
+                              for r in range(A.shape[0]))
+    assert key(A1.tocsr(), b1) == key(A2.tocsr(), b2)
+
+
+@pytest.mark.parametrize("maker", [lambda: F.feeder_tiny(5, 1), lambda: F.feeder_13(1)])
+def test_paper_decomposition_fixed_point_matches_highs(maker):
+    """Algorithm 1 on the paper's decomposition reaches the same LP optimum
+    (HiGHS) and its duality gap closes."""
+    f = maker()
+    m = OM.build_feeder(f, "paper")
+    pre = OP.precompute(m)
+    lp = OL.solve_lp(OM.build_feeder(f))
+    s = OA.ADMM(m, pre, 100.0)
+    out = s.run(400000, eps_abs_prim=1e-8, eps_abs_dual=1e-8, criterion=OA.CRIT_ABS)
+    assert out["converged"]
+    assert abs(out["objective"] - lp.fun) <= 1e-6 * max(1.0, abs(lp.fun))
+    cert = OA.dual_certificate(m, pre, s)
+    assert abs(cert["primal"] - cert["dual"]) <= 1e-5 * max(1.0, abs(lp.fun))
