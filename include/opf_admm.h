@@ -258,6 +258,31 @@ int32_t opf_get_dims(const opf_problem* p, opf_dims* dims);
 int32_t opf_update_lines(opf_problem* p, const int32_t* line_idx, const opf_line* records, int32_t count,
                          void* stream);
 
+/* Switch line `line` (index in the input records) in (in_service = 1) or
+ * out of service (0): the paper's dynamically changing topology
+ * (Section I; the model of Section II-A leaves out lines that are out of
+ * service).  The line's flows appear in or leave the global vector and the
+ * rows of the components at its ends change, so the model is assembled
+ * again from the records the problem was built from (with every earlier
+ * opf_update_lines / opf_set_line_status applied) and the operators of
+ * Eq. (closed_2) are recomputed for the components whose rows changed only
+ * (*n_recomputed, may be NULL, gets their number; every other component
+ * keeps its operator).  Same decomposition and chunk option as at create.
+ * On an uploaded problem the new layout is uploaded to the problem's
+ * device (the handle then allocates its own arena with cudaMallocAsync on
+ * `stream`; an arena the caller passed to opf_problem_upload is no longer
+ * used once the call returns) and the iterate and duals are carried over
+ * on the device for every local copy whose component (kind, element) and
+ * global variable (element, phase) exist before and after; new copies start
+ * from the initial point of Section V-A.  The next solve with warm_start =
+ * 1 continues from there; the iteration counter restarts at 0.  The call
+ * synchronizes `stream`.  Batches that include the problem must be created
+ * again.  No change when the line already has that state.  Closing a line
+ * may close a loop (the model does not require a radial feeder); opening
+ * one may leave buses without supply (the LP is then infeasible and the
+ * solve does not converge).  Errors: INVALID_ARG (index, state).          */
+int32_t opf_set_line_status(opf_problem* p, int32_t line, int32_t in_service, void* stream, int32_t* n_recomputed);
+
 /* Copy the packed problem to the current CUDA device on `stream`.  With
  * device_arena != NULL the handle carves all its device buffers out of that
  * caller-owned region (>= dims.device_bytes bytes, 256-byte aligned; it must

@@ -140,16 +140,12 @@ int32_t opf_problem_create_ex(const opf_bus* buses, int32_t n_bus, const opf_lin
         try {
             p->model = opf::build_model(buses, n_bus, lines, n_line, gens, n_gen, loads, n_load);
             if (decomp == OPF_DECOMP_PAPER) opf::paper_decomposition(p->model);
-            p->ops.reserve(p->model.comps.size());
-            p->canon_comp_ptr.assign(1, 0);
-            for (const auto& c : p->model.comps) {
-                p->ops.push_back(opf::make_operator(c));
-                p->m_reduced.push_back(p->ops.back().m_reduced);
-                p->canon_comp_ptr.push_back(p->canon_comp_ptr.back() + c.n());
-                p->n_rows += c.m;
-                p->n_rows_reduced += p->ops.back().m_reduced;
-            }
-            p->pk = opf::pack(p->model, p->ops, chunks);
+            p->create_chunks = chunks;
+            opf::finish_host(p, nullptr, nullptr, nullptr);
+            p->rec_bus.assign(buses, buses + n_bus);
+            p->rec_line.assign(lines, lines + n_line);
+            p->rec_gen.assign(gens, gens + n_gen);
+            p->rec_load.assign(loads, loads + n_load);
         } catch (...) {
             delete p;
             throw;
@@ -230,6 +226,18 @@ int32_t opf_update_lines(opf_problem* p, const int32_t* line_idx, const opf_line
         }
         opf::device_update_bounds(p, ranges, (cudaStream_t)stream);
         opf::device_reprecompute(p, comps, (cudaStream_t)stream);
+        for (int k = 0; k < count; ++k) p->rec_line[line_idx[k]] = records[k];
+        return OPF_OK;
+    });
+}
+
+int32_t opf_set_line_status(opf_problem* p, int32_t line, int32_t in_service, void* stream, int32_t* n_recomputed) {
+    return guarded([&]() -> int32_t {
+        if (!p) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL problem");
+        if (in_service != 0 && in_service != 1) throw opf::Error(OPF_ERR_INVALID_ARG, "in_service must be 0 or 1");
+        int rec = 0;
+        opf::set_line_status(p, line, in_service != 0, (cudaStream_t)stream, &rec);
+        if (n_recomputed) *n_recomputed = rec;
         return OPF_OK;
     });
 }

@@ -106,6 +106,12 @@ struct opf_batch {
 };
 
 struct opf_problem {
+    // the records the problem was built from (kept for topology changes)
+    std::vector<opf_bus> rec_bus;
+    std::vector<opf_line> rec_line;
+    std::vector<opf_gen> rec_gen;
+    std::vector<opf_load> rec_load;
+    int create_chunks = 0;              // chunk option of the create call
     opf::Model model;
     std::vector<opf::Operator> ops;
     opf::Packed pk;
@@ -148,3 +154,11 @@ struct opf_problem {
     int profile_phases = 0;
     std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision + 2 * residual form, K)
 };
+
+namespace opf {
+// Operators (reusing those of old_model's components with unchanged rows),
+// canonical offsets, ranks and the device layout of p->model.
+void finish_host(opf_problem* p, const Model* old_model, const std::vector<Operator>* old_ops, int* recomputed);
+void set_line_status(opf_problem* p, int line, bool in_service, cudaStream_t s, int* recomputed);
+std::vector<int32_t> warm_map(const opf_problem* dst, const opf_problem* src);
+}  // namespace opf

@@ -43,6 +43,7 @@ size_t device_bytes(const opf_problem* p);
 void device_warm_transfer(opf_problem* dst, const opf_problem* src, const std::vector<int32_t>& map, cudaStream_t s);
 void device_free(opf_problem* p);
 void set_last_error(const std::string& m);
+std::vector<int32_t> warm_map(const opf_problem* dst, const opf_problem* src);
 }  // namespace opf
 
 namespace {
@@ -66,44 +67,6 @@ struct Request {
     int chunks = 0;
     uint64_t last_use = 0;
 };
-
-// Identity of a global variable independent of the numbering: kind, element, phase.
-std::vector<int64_t> global_keys(const opf::Model& M) {
-    std::vector<int64_t> key(M.n, -1);
-    auto put = [&](const std::vector<int32_t>& idx, int64_t kind) {
-        for (size_t q = 0; q < idx.size(); ++q)
-            if (idx[q] >= 0) key[idx[q]] = (kind << 40) | ((int64_t)(q / 3) << 4) | (int64_t)(q % 3);
-    };
-    put(M.w_idx, 1); put(M.pg_idx, 2); put(M.qg_idx, 3);
-    put(M.pij_idx, 4); put(M.qij_idx, 5); put(M.pji_idx, 6); put(M.qji_idx, 7);
-    put(M.pb_idx, 8); put(M.qb_idx, 9); put(M.pd_idx, 10); put(M.qd_idx, 11);
-    return key;
-}
-
-// New device local -> old device local for copies of the same global
-// variable in the same component (kind, element); -1 elsewhere.
-std::vector<int32_t> warm_map(const opf_problem* dst, const opf_problem* src) {
-    const std::vector<int64_t> kd = global_keys(dst->model), ks = global_keys(src->model);
-    std::map<std::pair<int, int>, int> src_comp;
-    for (int s = 0; s < (int)src->model.comps.size(); ++s)
-        src_comp[{src->model.comps[s].kind, src->model.comps[s].index}] = s;
-    std::vector<int32_t> map(dst->pk.nl, -1);
-    for (int s = 0; s < (int)dst->model.comps.size(); ++s) {
-        const opf::Component& C = dst->model.comps[s];
-        auto it = src_comp.find({C.kind, C.index});
-        if (it == src_comp.end()) continue;
-        const opf::Component& D = src->model.comps[it->second];
-        std::unordered_map<int64_t, int> pos;
-        for (int r = 0; r < D.n(); ++r) pos[ks[D.gvars[r]]] = r;
-        for (int r = 0; r < C.n(); ++r) {
-            auto f = pos.find(kd[C.gvars[r]]);
-            if (f == pos.end()) continue;
-            map[dst->pk.dev_of_canon[dst->canon_comp_ptr[s] + r]] =
-                src->pk.dev_of_canon[src->canon_comp_ptr[it->second] + f->second];
-        }
-    }
-    return map;
-}
 
 }  // namespace
 
@@ -198,7 +161,7 @@ bool admit(opf_server* S, Request& r) {
     if (r.warm_from >= 0) {
         auto it = S->reqs.find(r.warm_from);
         if (it != S->reqs.end() && it->second.resident && it->second.state == REQ_DONE && it->second.p) {
-            opf::device_warm_transfer(r.p, it->second.p, warm_map(r.p, it->second.p), S->upload);
+            opf::device_warm_transfer(r.p, it->second.p, opf::warm_map(r.p, it->second.p), S->upload);
             it->second.last_use = ++S->tick;
             S->stats.warm_started += 1;
         } else {

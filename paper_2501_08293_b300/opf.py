@@ -88,6 +88,7 @@ EXPORTS = {
                                           C.POINTER(CreateOptions), C.POINTER(C.c_void_p)]),
     "opf_get_dims": (C.c_int32, [_P, C.POINTER(Dims)]),
     "opf_update_lines": (C.c_int32, [_P, _I, _P, C.c_int32, _P]),
+    "opf_set_line_status": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _I]),
     "opf_problem_upload": (C.c_int32, [_P, _P, C.c_size_t, _P]),
     "opf_admm_solve": (C.c_int32, [_P, C.POINTER(Params), _P, C.POINTER(Info)]),
     "opf_get_state": (C.c_int32, [_P, _D, _D, _D, _P]),
@@ -204,7 +205,9 @@ class Problem:
     def __init__(self, buses, lines, gens, loads, *, device=None, stream=None, upload=True, chunks: int = 0,
                  decomposition: int = DECOMP_FINE):
         self._h = C.c_void_p()
-        self._arrays = [np.ascontiguousarray(a) for a in (buses, lines, gens, loads)]
+        # private copies: later record updates (update_lines, set_line_status)
+        # must not write into the caller's arrays
+        self._arrays = [np.array(a, copy=True, order="C") for a in (buses, lines, gens, loads)]
         for a, dt in zip(self._arrays, (_F.BUS_DTYPE, _F.LINE_DTYPE, _F.GEN_DTYPE, _F.LOAD_DTYPE)):
             if a.dtype != dt:
                 raise TypeError(f"record array has dtype {a.dtype}, expected {dt}")
@@ -219,6 +222,7 @@ class Problem:
         _check(lib.opf_get_dims(self._h, C.byref(self.dims)), "opf_get_dims")
         self.n_bus, self.n_line, self.n_gen, self.n_load = len(b), len(l), len(g), len(d)
         self._arena = None
+        self._device_owned = False
         if upload:
             self.upload(device=device, stream=stream)
 
@@ -236,6 +240,7 @@ class Problem:
         _check(lib.opf_get_dims(p._h, C.byref(p.dims)), "opf_get_dims")
         p.n_bus, p.n_line, p.n_gen, p.n_load = n_bus, n_line, n_gen, n_load
         p._arena = None
+        p._device_owned = False
         p._borrowed = True
         return p
 
@@ -305,6 +310,23 @@ class Problem:
                                     _stream_handle(stream)), "opf_update_lines")
         for k, e in enumerate(idx):
             self._arrays[1][e] = rec[k]
+
+    def set_line_status(self, line: int, in_service: bool, stream=None) -> int:
+        """Switch a line in or out of service (opf_set_line_status): the
+        problem is rebuilt on the host (operators recomputed only for the
+        touched components, whose count is returned) and, when uploaded, the
+        iterate is carried over on the device; the library then owns its
+        device arena.  Continue with solve(..., warm_start=1)."""
+        n = C.c_int32()
+        _check(lib.opf_set_line_status(self._h, int(line), int(bool(in_service)), _stream_handle(stream)
+                                       if self._arena is not None or self._device_owned else None, C.byref(n)),
+               "opf_set_line_status")
+        self._arrays[1]["in_service"][int(line)] = int(bool(in_service))
+        _check(lib.opf_get_dims(self._h, C.byref(self.dims)), "opf_get_dims")
+        if self._arena is not None:
+            self._device_owned = True       # the library allocated a new arena; torch's is free again
+            self._arena = None
+        return n.value
 
     def persistent_ok(self, params: Params) -> bool:
         e = C.c_int32()

@@ -236,3 +236,52 @@ def test_component_operator_matches_oracle_row_reduction(opf):
         np.testing.assert_allclose(bb, bbar, atol=1e-9 * max(1.0, np.abs(bbar).max()))
     P, bb, mr = opf.component_operator(np.zeros((0, 4)), np.zeros(0))
     assert mr == 0 and np.array_equal(P, np.eye(4)) and np.array_equal(bb, np.zeros(4))
+
+
+@pytest.mark.parametrize("decomp", ["fine", "paper"])
+def test_set_line_status_host_rebuild(opf, decomp):
+    """opf_set_line_status on a problem that is not uploaded: the rebuilt
+    host problem equals one created from the new records (structure and
+    operators bit for bit); only the components whose rows changed are
+    re-precomputed, counted independently from the oracle's models; and
+    switching back restores the original problem."""
+    from oracle import model as OM
+    d = opf.DECOMP_PAPER if decomp == "paper" else opf.DECOMP_FINE
+    f = F.feeder_123(1)
+    rng = np.random.default_rng(3)
+    g = F.reconfigure(f, rng)
+    changed = np.flatnonzero(g.lines["in_service"] != f.lines["in_service"])
+    assert len(changed) == 2
+    p = opf.Problem.from_feeder(f, upload=False, decomposition=d)
+    base = [p.operator(s) for s in range(p.dims.n_comp)]
+    cur = f.copy()
+    for e in changed:
+        old_m = OM.build_feeder(cur, decomp)
+        cur.lines["in_service"][e] = g.lines["in_service"][e]
+        new_m = OM.build_feeder(cur, decomp)
+        before = {(c.kind, c.index): c for c in old_m.comps}
+        touched = sum(1 for c in new_m.comps
+                      if (c.kind, c.index) not in before
+                      or not (np.array_equal(before[c.kind, c.index].A, c.A)
+                              and np.array_equal(before[c.kind, c.index].b, c.b)))
+        n = p.set_line_status(int(e), bool(g.lines["in_service"][e]))
+        assert n == touched and 1 <= n <= 6, (n, touched)
+        q = opf.Problem.from_feeder(cur, upload=False, decomposition=d)
+        sp, sq = p.structure(), q.structure()
+        for k in sp:
+            assert np.array_equal(sp[k], sq[k]), k
+        assert p.dims.n_global == q.dims.n_global and p.dims.n_blocks == q.dims.n_blocks
+        for s in range(q.dims.n_comp):
+            a, b = p.operator(s), q.operator(s)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        q.close()
+    assert p.set_line_status(int(changed[0]), bool(g.lines["in_service"][changed[0]])) == 0   # no change
+    for e in changed[::-1]:
+        p.set_line_status(int(e), bool(f.lines["in_service"][e]))
+    assert p.dims.n_comp == len(base)
+    for s in range(p.dims.n_comp):
+        a = p.operator(s)
+        assert np.array_equal(a[0], base[s][0]) and np.array_equal(a[1], base[s][1])
+    with pytest.raises(opf.OpfError):
+        p.set_line_status(len(f.lines), True)
+    p.close()

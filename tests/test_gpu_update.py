@@ -131,3 +131,62 @@ def test_warm_solve_after_update_matches_oracle(opf, decomp):
     assert rel(xg2, s.x) <= 1e-9 and rel(xl2, s.z) <= 1e-9 and rel(lam2, s.lam) <= 1e-9
     assert abs(info.pres - r.pres) <= 1e-9 * r.pres
     a.close()
+
+
+@pytest.mark.parametrize("decomp", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_set_line_status_carries_state_and_follows_oracle(opf, decomp, prec):
+    """A topology switch (close a tie, open a line on the loop it closes)
+    through opf_set_line_status on an uploaded, partly solved problem:
+    every local copy whose component and global variable exist before and
+    after keeps its value and dual; new copies start at the initial point of
+    Section V-A with lambda = 0; the warm solve that follows is Algorithm 1
+    on the new model from that state (FP64: 1e-9 per iterate against the
+    oracle; FP32 sweeps: 1e-5) and converges."""
+    from oracle import admm as OA, model as OM, precompute as OP
+    dname = "paper" if decomp else "fine"
+    f = F.feeder_123(1)
+    g = F.reconfigure(f, np.random.default_rng(3))
+    changed = np.flatnonzero(g.lines["in_service"] != f.lines["in_service"])
+    p = opf.Problem.from_feeder(f, decomposition=decomp)
+    p.solve(opf.default_params(rho=10.0, criterion=opf.CRIT_NEVER, max_iter=300, check_every=50, precision=prec))
+    _, xl0, lam0 = p.state()
+    m0, m1 = OM.build_feeder(f, dname), OM.build_feeder(g, dname)
+    where0 = {}
+    k = 0
+    for c in m0.comps:
+        for gv in c.gvars:
+            where0[c.kind, c.index, m0.names[gv]] = k
+            k += 1
+    total = 0
+    for e in changed:
+        total += p.set_line_status(int(e), bool(g.lines["in_service"][e]))
+    assert total >= 4
+    _, xl1, lam1 = p.state()
+    assert p.dims.n_local == m1.nl and p.dims.n_global == m1.n
+    s = OA.ADMM(m1, OP.precompute(m1), 10.0)
+    init = s.initial_local()
+    k = 0
+    carried = fresh = 0
+    for c in m1.comps:
+        for gv in c.gvars:
+            j = where0.get((c.kind, c.index, m1.names[gv]))
+            if j is not None:
+                assert xl1[k] == xl0[j] and lam1[k] == lam0[j]
+                carried += 1
+            else:
+                assert abs(xl1[k] - init[k]) <= (0 if prec == 0 else 1e-7) * max(1.0, abs(init[k])) and lam1[k] == 0
+                fresh += 1
+            k += 1
+    assert carried > 0.9 * m1.nl and fresh > 0
+    s.z, s.lam = xl1.copy(), lam1.copy()
+    info = p.solve(opf.default_params(rho=10.0, criterion=opf.CRIT_NEVER, max_iter=200, check_every=50,
+                                      precision=prec, warm_start=1))
+    for _ in range(200):
+        r = s.step()
+    tol = 1e-9 if prec == 0 else 1e-5
+    xg2, xl2, lam2 = p.state()
+    assert rel(xg2, s.x) <= tol and rel(xl2, s.z) <= tol and rel(lam2, s.lam) <= tol
+    info = p.solve(opf.default_params(rho=10.0, max_iter=400000, precision=prec, warm_start=1))
+    assert info.status == opf.OK
+    p.close()
