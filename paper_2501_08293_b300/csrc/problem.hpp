@@ -103,6 +103,13 @@ struct opf_batch {
     cudaGraphExec_t gexec = nullptr;
     const void* g_buf = nullptr;
     int g_n = 0, g_nz = 0, g_nx = 0, g_K = 0, g_prec = -1;
+    // persistent engine: the flag clear, the cooperative launch and the
+    // finish kernel captured once as a graph, and what it was captured for
+    cudaGraph_t pgraph = nullptr;
+    cudaGraphExec_t pexec = nullptr;
+    const void* p_buf = nullptr;
+    int p_n = 0, p_nx = 0, p_nz = 0, p_prec = -1, p_var = 0;
+    unsigned char p_plan[128] = {};
 };
 
 struct opf_problem {

@@ -2143,25 +2143,82 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     int32_t* dclaim = reinterpret_cast<int32_t*>(d + claim_off);
     Ctl* dctl = reinterpret_cast<Ctl*>(d + ctl_off);
     const bool smem_var = engine == OPF_ENGINE_PERSISTENT && coop_fits(batch_smem_kernel<T>, (size_t)sp.total, nctas);
-    batch_clear_flags<T><<<std::min(n, 1024), 256, 0, s>>>(dviews, n, smem_var ? 1 : 0);
-    OPF_CUDA(cudaGetLastError());
     if (running > 0 && engine == OPF_ENGINE_PERSISTENT) {
-        if (smem_var) {
-            int per = resident_per_sm(batch_smem_kernel<T>, (size_t)sp.total);
-            void* args[] = {&dviews, &dmap, &sp, &dclaim, &per};
-            OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_smem_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
-                                                 args, (size_t)sp.total, s));
-        } else if (coop_fits(batch_global_kernel<T>, gsmem, nctas)) {
-            int per = resident_per_sm(batch_global_kernel<T>, gsmem);
-            void* args[] = {&dviews, &dmap, &dclaim, &per};
-            OPF_CUDA(cudaLaunchCooperativeKernel((const void*)batch_global_kernel<T>, dim3(nctas), dim3(kXWarps * 32),
-                                                 args, gsmem, s));
-        } else {
+        // One persistent launch for the whole batch, captured once into a
+        // CUDA graph (flag clear, cooperative kernel, per-instance finish)
+        // and launched again while the batch layout, precision and kernel
+        // plan are unchanged; the per-solve control blocks and descriptors
+        // are copied in before it (same device addresses).
+        const int variant = smem_var ? 2 : (coop_fits(batch_global_kernel<T>, gsmem, nctas) ? 1 : 0);
+        if (!variant)
             throw Error(OPF_ERR_INVALID_ARG, "batch: " + std::to_string(nctas) +
                                                  " chunks do not fit co-resident; create the problems with fewer"
                                                  " chunks or use the graph engine");
+        static_assert(sizeof(SmemPlan) <= sizeof(B->p_plan), "plan key");
+        unsigned char plan[sizeof(B->p_plan)] = {};
+        std::memcpy(plan, &sp, sizeof(SmemPlan));
+        if (!B->pexec || B->p_buf != B->dev_buf || B->p_n != n || B->p_nx != nctas || B->p_nz != nz || B->p_prec != prec ||
+            B->p_var != variant || std::memcmp(plan, B->p_plan, sizeof(plan)) != 0) {
+            if (B->pexec) cudaGraphExecDestroy(B->pexec);
+            if (B->pgraph) cudaGraphDestroy(B->pgraph);
+            B->pexec = nullptr;
+            B->pgraph = nullptr;
+            cudaStream_t cs;
+            OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            OPF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaSuccess;
+            batch_clear_flags<T><<<std::min(n, 1024), 256, 0, cs>>>(dviews, n, smem_var ? 1 : 0);
+            cudaLaunchConfig_t lc = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeCooperative;
+            at[0].val.cooperative = 1;
+            lc.gridDim = dim3(nctas);
+            lc.blockDim = dim3(kXWarps * 32);
+            lc.stream = cs;
+            lc.attrs = at;
+            lc.numAttrs = 1;
+            if (variant == 2) {
+                int per = resident_per_sm(batch_smem_kernel<T>, (size_t)sp.total);
+                void* args[] = {&dviews, &dmap, &sp, &dclaim, &per};
+                lc.dynamicSmemBytes = (size_t)sp.total;
+                ce = cudaLaunchKernelExC(&lc, (const void*)batch_smem_kernel<T>, args);
+            } else {
+                int per = resident_per_sm(batch_global_kernel<T>, gsmem);
+                void* args[] = {&dviews, &dmap, &dclaim, &per};
+                lc.dynamicSmemBytes = gsmem;
+                ce = cudaLaunchKernelExC(&lc, (const void*)batch_global_kernel<T>, args);
+            }
+            batch_finish_kernel<T><<<n, 256, 0, cs>>>(dviews, dctl);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+            cudaStreamDestroy(cs);
+            if (ce != cudaSuccess || ee != cudaSuccess || !g) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                throw Error(OPF_ERR_CUDA, std::string("batch: capturing the persistent launch failed: ") +
+                                              cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+            }
+            cudaGraphExec_t ge = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(g);
+                throw Error(OPF_ERR_CUDA, std::string("batch: instantiating the persistent launch: ") +
+                                              cudaGetErrorString(ie));
+            }
+            B->pgraph = g;
+            B->pexec = ge;
+            B->p_buf = B->dev_buf; B->p_n = n; B->p_nx = nctas; B->p_nz = nz; B->p_prec = prec; B->p_var = variant;
+            std::memcpy(B->p_plan, plan, sizeof(plan));
         }
-    } else if (running > 0) {
+        OPF_CUDA(cudaGraphLaunch(B->pexec, s));
+        OPF_CUDA(cudaMemcpyAsync(hctl, dctl, (size_t)n * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        OPF_CUDA(cudaEventRecord(B->done, s));
+        B->n_launched = n;
+        return;
+    }
+    batch_clear_flags<T><<<std::min(n, 1024), 256, 0, s>>>(dviews, n, smem_var ? 1 : 0);
+    OPF_CUDA(cudaGetLastError());
+    if (running > 0) {
         const int K = prm[0].check_every;
         if (!B->gexec || B->g_buf != B->dev_buf || B->g_n != n || B->g_nz != nz || B->g_nx != nctas || B->g_K != K ||
             B->g_prec != prec) {
@@ -2252,6 +2309,10 @@ void device_batch_free(opf_batch* B) {
     if (B->graph) cudaGraphDestroy(B->graph);
     B->gexec = nullptr;
     B->graph = nullptr;
+    if (B->pexec) cudaGraphExecDestroy(B->pexec);
+    if (B->pgraph) cudaGraphDestroy(B->pgraph);
+    B->pexec = nullptr;
+    B->pgraph = nullptr;
     if (B->done) cudaEventDestroy(B->done);
     B->done = nullptr;
     if (B->dev_buf) cudaFree(B->dev_buf);

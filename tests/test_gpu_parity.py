@@ -163,17 +163,28 @@ def test_full_size_8500_class_parity(opf):
 # errors add up at most linearly over iterations and, being of random sign,
 # typically as the square root: sqrt(t * mean n_s) u ~ sqrt(200 * 7) * 6e-8
 # ~ 2e-6 at t = 200, plus the one-time rounding of the operators to FP32 (u
-# per entry).  The bound below keeps a factor of ~5 over that estimate.
+# per entry).  The bound below keeps a factor of ~2-5 over that estimate
+# (measured on B300: 2.4e-6 to 4.9e-6 for x and z).  The dual update
+# lambda += rho (B x - x_s) multiplies the local rounding errors by rho, so
+# lambda is compared in the variable in which ADMM is non-expansive, the
+# scaled dual lambda / rho, against the scale of the local iterate:
+# |dlambda_i| / rho <= TOL (|lambda_i| / rho + max |lambda| / rho + max |z|).
 TOL_FP32_T200 = 1e-5
+
+
+def rel_scaled_dual(lam, lam_ref, z_ref, rho):
+    d = (lam - lam_ref) / rho
+    scale = np.abs(lam_ref) / rho + float(np.max(np.abs(lam_ref))) / rho + float(np.max(np.abs(z_ref)))
+    nrm = float(np.linalg.norm(lam_ref)) / rho + float(np.linalg.norm(z_ref))
+    return max(float(np.linalg.norm(d)) / nrm, float(np.max(np.abs(d) / scale)))
 
 
 @pytest.mark.parametrize("rho", [10.0, 100.0])
 def test_fp32_per_iterate_parity_8500_class(opf, rho):
     """The headline configuration (8500-class feeder, FP32 sweeps with FP64
     residual sums, default engine and chunking, check every 50) against the
-    FP64 oracle at t = 200: x, z and lambda within TOL_FP32_T200 normwise and
-    element by element (scale |oracle_i| + max |oracle|), residuals within
-    1e-3 relative."""
+    FP64 oracle at t = 200: x, z and lambda / rho within TOL_FP32_T200
+    normwise and element by element, residuals within 1e-3 relative."""
     f = F.feeder_8500(1)
     p = opf.Problem.from_feeder(f)
     m, pre, s = oracle_solver(f, rho)
@@ -182,7 +193,7 @@ def test_fp32_per_iterate_parity_8500_class(opf, rho):
     for _ in range(200):
         r = s.step()
     xg, xl, lam = p.state()
-    errs = {"x": rel(xg, s.x), "z": rel(xl, s.z), "lam": rel(lam, s.lam)}
+    errs = {"x": rel(xg, s.x), "z": rel(xl, s.z), "lam/rho": rel_scaled_dual(lam, s.lam, s.z, rho)}
     assert max(errs.values()) <= TOL_FP32_T200, errs
     assert abs(info.pres - r.pres) <= 1e-3 * r.pres and abs(info.dres - r.dres) <= 1e-3 * r.dres
     assert abs(info.eps_prim - r.eps_prim) <= 1e-5 * r.eps_prim
