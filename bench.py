@@ -46,24 +46,34 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="8500", choices=["8500", "batch", "serve", "configs", "scenarios"])
+    ap.add_argument("--workload", default="8500", choices=["8500", "batch", "serve", "configs", "scenarios", "tune"])
+    ap.add_argument("--tune-out", default="", help="tune workload: where to write the table (default: the package's)")
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--scenario-iters", type=int, default=1000)
     ap.add_argument("--sweep-budget-iters", type=int, default=4_000_000)
     ap.add_argument("--configs-quick", action="store_true", help="configs workload: small feeders only")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-iters", type=int, default=2000)
-    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--requests", type=int, default=2000, help="serve workload: requests of the stream")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="serve workload: arrivals per second (0 = serve-load x the capacity measured first)")
+    ap.add_argument("--serve-workload-max-bus", type=int, default=8500, help="serve workload: largest feeder")
     ap.add_argument("--serve-requests-default", type=int, default=100,
                     help="requests of the serving stream in the default bench line")
     ap.add_argument("--no-serve", action="store_true", help="default bench line without the serving stream")
     ap.add_argument("--no-precision", action="store_true",
                     help="default bench line without the FP64 solve of the precision report")
-    ap.add_argument("--rate", type=float, default=4.0, help="request arrivals per second")
+    ap.add_argument("--rate", type=float, default=4.0, help="arrivals per second of the default line's stream")
     ap.add_argument("--serve-max-bus", type=int, default=2500)
     ap.add_argument("--serve-bus-per-chunk", type=int, default=0,
                     help="serving: buses per chunk of a new request (0: the server's default)")
     ap.add_argument("--serve-budget-iters", type=int, default=200000)
+    ap.add_argument("--serve-iters-per-bus", type=int, default=300,
+                    help="serving: a request's iteration budget is max(serve-budget-iters, this x n_bus)")
+    ap.add_argument("--serve-capacity-requests", type=int, default=120,
+                    help="serve workload with --rate 0: cold requests submitted at once to measure capacity")
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="serve workload with --rate 0: offered load as a fraction of the measured capacity")
     ap.add_argument("--profile-scenarios", type=int, default=0,
                     help="launch each multi-scenario kernel this many times outside the graph (64 draws on the "
                          "8500-class feeder; the small case for ncu) and exit")
@@ -527,20 +537,60 @@ def run_batch(args):
     }))
 
 
-def serve_stream(args, requests: int, rate: float) -> dict:
+def serve_feeder(rng, max_bus: int):
+    """A cold serving request: n_bus log-uniform in [13, max_bus], shaped like
+    the configurations (12.47 kV, a load per 8 buses, lognormal loads, PV)."""
+    import numpy as np
+    from paper_2501_08293_b300 import feeders as F
+    nb = int(max(13, np.exp(rng.uniform(np.log(13), np.log(max_bus)))))
+    return F.make_feeder(nb, int(rng.integers(1 << 30)), n_loads=max(1, nb // 8),
+                         load_sampler=lambda r: r.lognormal(-4.0, 1.0), n_pv=max(1, nb // 60),
+                         n_switches=4, line_mix=(0.6, 0.15, 0.25), v_ll_kv=12.47, lateral_mean=5.0)
+
+
+def new_server(args):
+    from paper_2501_08293_b300 import opf
+    prec = opf.FP64 if args.precision == "fp64" else opf.FP32
+    return opf.Server(precision=prec, rho=args.rho, max_iter=args.serve_budget_iters, check_every=50,
+                      round_iters=1000, max_active=256, iters_per_bus=args.serve_iters_per_bus)
+
+
+def serve_capacity(args, requests: int, max_bus: int) -> dict:
+    """Capacity: `requests` cold requests (same size law) submitted at once;
+    completed solves per second of wall time until the last one finishes."""
+    import numpy as np
+    from paper_2501_08293_b300 import opf
+    rng = np.random.default_rng(args.seed + 7)
+    fs = [serve_feeder(rng, max_bus) for _ in range(requests)]
+    srv = new_server(args)
+    t0 = time.perf_counter()
+    for f in fs:
+        srv.submit(f)
+    done = {}
+    while len(done) < requests:
+        srv.step()
+        for rid, info in srv.poll():
+            done[rid] = info
+    wall = time.perf_counter() - t0
+    srv.close()
+    conv = sum(1 for i in done.values() if i.status == opf.OK)
+    return {"requests": requests, "wall_s": wall, "solves_per_s": requests / wall, "converged": conv,
+            "note": "cold requests submitted at once (a lower bound: warm-started requests are cheaper)"}
+
+
+def serve_stream(args, requests: int, rate: float, max_bus: int | None = None) -> dict:
     """Poisson stream of `requests` requests at `rate`/s (sizes log-uniform
-    in [13, serve-max-bus] buses, 30 % topology switches of a resident
-    feeder warm-started from its last iterate) through the continuous-
-    batching server; returns solves/s, p50/p99 latency and server counters."""
+    in [13, max_bus] buses, 30 % topology switches of a resident feeder
+    warm-started from its last iterate) through the continuous-batching
+    server; converged solves/s and p50/p99 latency over the requests that
+    reached ABS 1e-4, the rest reported beside them."""
     import numpy as np
     from paper_2501_08293_b300 import feeders as F
     from paper_2501_08293_b300 import opf
+    max_bus = args.serve_max_bus if max_bus is None else max_bus
     rng = np.random.default_rng(args.seed)
-    prec = opf.FP64 if args.precision == "fp64" else opf.FP32
-    srv = opf.Server(precision=prec, rho=args.rho, max_iter=args.serve_budget_iters, check_every=50,
-                     round_iters=1000, max_active=256)
+    srv = new_server(args)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=requests))
-    sizes = np.exp(rng.uniform(np.log(13), np.log(args.serve_max_bus), size=requests)).astype(int)
     done_feeders = []            # (request id, feeder) finished and possibly resident
     kind = {}
     t0 = time.perf_counter()
@@ -557,10 +607,8 @@ def serve_stream(args, requests: int, rate: float) -> dict:
                 kind[rid] = ("warm", g)
                 warm_n += 1
             else:
-                nb = int(max(13, sizes[nxt]))
-                g = F.make_feeder(nb, int(rng.integers(1 << 30)), n_loads=max(1, nb // 8),
-                                  load_sampler=lambda r: r.lognormal(-4.0, 1.0), n_pv=max(1, nb // 60),
-                                  n_switches=4, line_mix=(0.6, 0.15, 0.25), v_ll_kv=12.47, lateral_mean=5.0)
+                g = serve_feeder(rng, max_bus)
+                nb = g.n_bus
                 ch = max(1, min(64, nb // args.serve_bus_per_chunk)) if args.serve_bus_per_chunk > 0 else 0
                 rid = srv.submit(g, chunks=ch)
                 kind[rid] = ("cold", g)
@@ -587,17 +635,28 @@ def serve_stream(args, requests: int, rate: float) -> dict:
                                                {"p50": pct(lat_miss, 50), "p99": pct(lat_miss, 99)})},
             "latency_all_s": {"p50": pct(lat_all, 50), "p99": pct(lat_all, 99)},
             "warm_requests": warm_n, "wall_s": wall, "server": st,
-            "workload": f"{requests} requests, Poisson {rate}/s, n_bus log-uniform [13, {args.serve_max_bus}], "
-                        f"30% topology switches warm-started, ABS 1e-4, budget {args.serve_budget_iters} iterations"}
+            "workload": f"{requests} requests, Poisson {rate:.3g}/s, n_bus log-uniform [13, {max_bus}], "
+                        f"30% topology switches warm-started, ABS 1e-4, budget max({args.serve_budget_iters}, "
+                        f"{args.serve_iters_per_bus} x n_bus) iterations"}
 
 
 def run_serve(args):
-    """The serving workload alone: solves/s and p50/p99 latency."""
+    """The serving workload (configuration C5 by default: 2000 requests,
+    13-8500 buses, 30 % warm topology switches): converged solves/s and
+    p50/p99 latency over converged requests.  With --rate 0 the arrival rate
+    is serve-load (0.8) times the capacity measured first with a burst of
+    cold requests."""
     import torch
     torch.cuda.set_device(0)
     from paper_2501_08293_b300 import build as B
     B.build()
-    r = serve_stream(args, args.requests, args.rate)
+    cap = None
+    rate = args.serve_rate
+    if rate <= 0:
+        cap = serve_capacity(args, args.serve_capacity_requests, args.serve_workload_max_bus)
+        rate = args.serve_load * cap["solves_per_s"]
+    with ClockSampler(0) as clk:
+        r = serve_stream(args, args.requests, rate, args.serve_workload_max_bus)
     print(json.dumps({
         "metric": "served OPF solves/s at ABS 1e-4 (continuous batching)", "value": r["converged_solves_per_s"],
         "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
@@ -606,8 +665,32 @@ def run_serve(args):
         "latency_s": r["latency_s"], "converged": r["converged"], "converged_frac": r["converged_frac"],
         "budget_exhausted": r["budget_exhausted"], "all_requests": {"solves_per_s": r["solves_per_s"],
                                                                     "latency_s": r["latency_all_s"]},
+        "capacity": cap, "offered_load": (None if cap is None else args.serve_load),
         "warm_requests": r["warm_requests"], "wall_s": r["wall_s"], "server": r["server"],
+        "clocks": clk.summary(),
     }))
+
+
+def run_tune(args):
+    """Autotune the automatic chunking per feeder-size bucket (the project's
+    tuner, paper_2501_08293_b300/autotune.py): every candidate chunk size
+    timed on the device; the winners are written as the JSON table the
+    library loads.  One JSON line: per bucket the chosen chunking and its
+    time per iteration against the default's."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import autotune
+    with ClockSampler(0) as clk:
+        table = autotune.tune(iters=3000, rho=args.rho, log=lambda m: print(m, file=sys.stderr, flush=True))
+    autotune.save(table, args.tune_out or autotune.DEFAULT_PATH)
+    rows = [{k: e[k] for k in ("n_bus_lo", "n_bus_hi", "representative_n_bus", "work_per_chunk", "chunks",
+                               "us_per_iter", "default_chunks", "default_us_per_iter")} for e in table["entries"]]
+    print(json.dumps({"metric": "chunking autotuner: us per iteration per size bucket (persistent engine, FP32)",
+                      "unit": "us/iter", "n_gpus": 1, "data": "synthetic", "gpu": table["gpu"],
+                      "seconds": table["seconds"], "rows": rows, "clocks": clk.summary(),
+                      "written": args.tune_out or autotune.DEFAULT_PATH}))
 
 
 def run_profile_solve(args):
@@ -820,5 +903,7 @@ if __name__ == "__main__":
         run_configs(a)
     elif a.workload == "scenarios":
         run_scenarios(a)
+    elif a.workload == "tune":
+        run_tune(a)
     else:
         run_ours(a)

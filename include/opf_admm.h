@@ -244,6 +244,26 @@ int32_t opf_problem_create_ex(const opf_bus* buses, int32_t n_bus,
 
 int32_t opf_get_dims(const opf_problem* p, opf_dims* dims);
 
+/* Tuning table of the automatic chunking (opf_create_options.chunks = 0;
+ * the paper has no counterpart: its CPU runs spread the components evenly
+ * over N workers, Section V-A).  A problem of n_bus buses is cut into
+ * chunks of about work_per_chunk units of n_s^2 + 4 n_s + 16, at most
+ * max_chunks; an entry applies to the GPU whose cudaDeviceProp::name equals
+ * `gpu` ("*" matches any) and to n_bus_lo <= n_bus < n_bus_hi.  Without a
+ * matching entry: 4096 units, at most 296 chunks.  Entries are process-wide
+ * (guarded by a mutex) and replace one with the same gpu and bucket.
+ * opf_tuning_load reads the JSON file the project's tuner writes
+ * ({"gpu": name, "entries": [{"n_bus_lo", "n_bus_hi", "work_per_chunk",
+ * "max_chunks", ...}]}, other keys ignored; *n_entries may be NULL);
+ * opf_tuning_lookup reports what a create on the current device would use.
+ * Errors: INVALID_ARG (unreadable or malformed file, values out of range:
+ * 0 <= lo < hi, 16 <= work_per_chunk <= 2^26, 1 <= max_chunks <= 65536).   */
+int32_t opf_tuning_set(const char* gpu, int32_t n_bus_lo, int32_t n_bus_hi, int32_t work_per_chunk,
+                       int32_t max_chunks);
+int32_t opf_tuning_clear(void);
+int32_t opf_tuning_load(const char* path, int32_t* n_entries);
+int32_t opf_tuning_lookup(int32_t n_bus, int32_t* work_per_chunk, int32_t* max_chunks);
+
 /* New parameters for in-service lines of an uploaded problem: records[k]
  * replaces line line_idx[k] (impedances r, x; shunts; taps; flow bounds).
  * Ends, phases and the service state must not change (a topology change
@@ -378,8 +398,10 @@ int32_t opf_engine_for(const opf_problem* p, int32_t precision, int32_t* engine)
  * the failure-detection test), -1 restores normal operation;
  * persistent_variant selects the persistent kernel: 0 automatic (shared-
  * memory iterate when it fits, else global-memory iterate), 1 global-memory
- * iterate, 2 shared-memory iterate (OPF_ERR_INVALID_ARG at solve time if it
- * does not fit co-resident).                                               */
+ * iterate, 2 shared-memory iterate, 3 shared-memory iterate whose boundary
+ * terms are polled entry by entry instead of gathered in one pass (same
+ * results; OPF_ERR_INVALID_ARG at solve time when 2 or 3 does not fit
+ * co-resident).                                                            */
 int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold_block, int32_t persistent_variant);
 
 /* Allocation-free residual norms.  The paper has no counterpart: this entry
@@ -526,9 +548,13 @@ typedef struct opf_server_config {
     int32_t round_iters;          /* iterations per round, multiple of check_every */
     int32_t max_chunks;           /* CTAs per round (0: the device's batch capacity,
                                      opf_batch_capacity)                         */
-    int32_t _reserved[3];
+    int32_t iters_per_bus;        /* iteration budget per bus of a request: its
+                                     budget is max(params.max_iter, iters_per_bus
+                                     x n_bus); 0 = params.max_iter for all       */
+    int32_t _reserved[2];
     opf_params params;            /* solve parameters of every request; max_iter
-                                     is each request's iteration budget          */
+                                     is each request's iteration budget (see
+                                     iters_per_bus)                              */
 } opf_server_config;
 
 typedef struct opf_server_stats {

@@ -79,6 +79,7 @@ struct BlockInfo {
     int32_t mat0, mat1;     // operator elements [mat0, mat1) of the chunk's tiles
     int32_t cp0, cp1;       // copy list entries of the chunk's halo [cp0, cp1)
     int32_t tileb, halob;   // first boundary tile / halo entry
+    int32_t ext0, ext1;     // copies of other chunks that the chunk reads [ext0, ext1) (device locals)
 };
 
 // Device-ordered problem, ready to upload.
@@ -93,6 +94,8 @@ struct Packed {
     std::vector<int32_t> meta;           // per local: hidx | n << 16 | base lane << 24 | exported << 30
     std::vector<int32_t> hcp;            // per halo entry (+1): start of its copy list in hci
     std::vector<int32_t> hci;            // copy of a halo global: chunk-relative local (>= 0) or ~device local (< 0)
+    std::vector<int32_t> hcx;            // the same, copies of other chunks as ~slot in the chunk's ext list
+    std::vector<int32_t> ext;            // per chunk: device locals of other chunks it reads, in copy-list order
     std::vector<int32_t> dev_of_canon;   // local: canonical -> device
     std::vector<int32_t> canon_of_dev;   // local: device -> canonical
     std::vector<int32_t> gidx;           // device order
@@ -108,6 +111,7 @@ struct Packed {
     int max_loc = 0;                     // largest chunk local count
     int max_mat = 0;                     // largest chunk operator span (elements)
     int max_copies = 0;                  // largest chunk halo copy list
+    int max_ext = 0;                     // most copies of other chunks read by one chunk
     int max_big = 0;                     // largest component with n > 32 (0: none)
     int max_tiles = 0;                   // most tiles in one chunk
 };
@@ -128,5 +132,10 @@ Operator make_operator(const Component& c);
 Component line_component(const Model& M, const opf_line& L, int e);
 Component line_update(const Model& M, const opf_line& L, int e);
 Packed pack(const Model& m, const std::vector<Operator>& ops, int nblocks_hint = 0);
+// Automatic chunking (nblocks_hint = 0): chunk size in units of
+// n_s^2 + 4 n_s + 16 and the chunk cap for a feeder of n_bus buses on the
+// current device, from the tuning table (default 4096, 296).
+void auto_chunking(int n_bus, int64_t* work_per_chunk, int* max_chunks);
+void set_last_error(const std::string& m);
 
 }  // namespace opf

@@ -86,7 +86,8 @@ std::vector<int> locality_order(const Model& M) {
 void validate(const Packed& K) {
     auto fail = [](const char* what) { throw Error(OPF_ERR_INVALID_ARG, std::string("internal layout check: ") + what); };
     std::vector<char> seen(K.nl, 0);
-    if ((int)K.blocks.size() != K.nblocks || K.hcp.size() != K.halo_gid.size() + 1) fail("sizes");
+    if ((int)K.blocks.size() != K.nblocks || K.hcp.size() != K.halo_gid.size() + 1 || K.hcx.size() != K.hci.size())
+        fail("sizes");
     for (int b = 0; b < K.nblocks; ++b) {
         const BlockInfo& bi = K.blocks[b];
         if (bi.loc0 < 0 || bi.loc1 > K.nl || bi.loc0 > bi.loc1) fail("chunk locals");
@@ -124,6 +125,16 @@ void validate(const Packed& K) {
             }
         }
         if (bi.cp0 != K.hcp[bi.halo0] || bi.cp1 != K.hcp[bi.halo1]) fail("copy list range");
+        if (bi.ext0 < 0 || bi.ext1 > (int)K.ext.size() || bi.ext0 > bi.ext1 || bi.ext1 - bi.ext0 > K.max_ext)
+            fail("gather list range");
+        for (int q = bi.cp0; q < bi.cp1; ++q) {
+            const int c = K.hcx[q];
+            if (c >= 0) {
+                if (c != K.hci[q]) fail("gather copy index");
+            } else if (~c >= bi.ext1 - bi.ext0 || K.ext[bi.ext0 + ~c] != ~K.hci[q]) {
+                fail("gather slot");
+            }
+        }
         for (int h = bi.halo0; h < bi.halo1; ++h) {
             const int g = K.halo_gid[h];
             if (g < 0 || g >= K.ng) fail("halo global");
@@ -165,7 +176,12 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
 
     // ---- chunks
     int nblk = nblocks_hint;
-    if (nblk <= 0) nblk = (int)std::min<int64_t>(296, std::max<int64_t>(1, work_total / 4096));
+    if (nblk <= 0) {
+        int64_t work = 4096;
+        int cap = 296;
+        auto_chunking(M.n_bus, &work, &cap);
+        nblk = (int)std::min<int64_t>(cap, std::max<int64_t>(1, work_total / work));
+    }
     nblk = std::max(1, std::min(nblk, std::max(1, K.ncomp)));
     const std::vector<int> order = locality_order(M);
     std::vector<int> chunk_start;   // index into order
@@ -435,21 +451,30 @@ Packed pack(const Model& M, const std::vector<Operator>& ops, int nblocks_hint) 
         K.max_halo = std::max(K.max_halo, bi.halo1 - bi.halo0);
         // copy lists of the halo globals, canonical copy order; a copy held by
         // this chunk is referenced by its chunk-relative local index
+        // (hcx: a copy of another chunk as ~slot in the chunk's list of such
+        // copies, ext, which the persistent kernel gathers in one pass)
         bi.cp0 = (int)K.hci.size();
+        bi.ext0 = (int)K.ext.size();
         for (int h = bi.halo0; h < bi.halo1; ++h) {
             K.hcp.push_back((int)K.hci.size());
             const int g = K.halo_gid[h];
             for (int q = K.gptr[g]; q < K.gptr[g + 1]; ++q) {
                 const int l = K.gcol[q];
-                if (l >= bi.loc0 && l < bi.loc1) K.hci.push_back(l - bi.loc0);
-                else {
+                if (l >= bi.loc0 && l < bi.loc1) {
+                    K.hci.push_back(l - bi.loc0);
+                    K.hcx.push_back(l - bi.loc0);
+                } else {
                     K.hci.push_back(~l);
+                    K.hcx.push_back(~((int)K.ext.size() - bi.ext0));
+                    K.ext.push_back(l);
                     K.meta[l] |= (1 << 30);        // read by another chunk: exported
                 }
             }
         }
         bi.cp1 = (int)K.hci.size();
+        bi.ext1 = (int)K.ext.size();
         K.max_copies = std::max(K.max_copies, bi.cp1 - bi.cp0);
+        K.max_ext = std::max(K.max_ext, bi.ext1 - bi.ext0);
         bi.nbr0 = (int)K.nbrs.size();
         for (int h = bi.halo0; h < bi.halo1; ++h) {
             const int g = K.halo_gid[h];

@@ -64,6 +64,8 @@ struct View {
     const int32_t* nbrs;
     const int32_t* hcp;
     const int32_t* hci;
+    const int32_t* hcx;               // copy lists with copies of other chunks as ~slot (gathered exchange)
+    const int32_t* ext;               // per chunk: device locals of other chunks it reads
     int32_t* flags;                   // per chunk: iteration flag (global-memory kernel) or claim word (shared-memory kernel)
     const T* P;
     const double* cost;
@@ -144,6 +146,8 @@ struct opf_problem {
     int32_t* nbrs = nullptr;
     int32_t* hcp = nullptr;
     int32_t* hci = nullptr;
+    int32_t* hcx = nullptr;
+    int32_t* ext = nullptr;
     int32_t* flags = nullptr;
     double* cost = nullptr;
     double* partials = nullptr;
@@ -157,7 +161,7 @@ struct opf_problem {
     bool cold = true;                   // state is at the initial point
     unsigned long long timeout_ns = 2000000000ull;   // bounded waits (persistent engine)
     int skip_block = -1;                              // test hook
-    int force_variant = 0;                            // persistent kernel: 0 auto, 1 global, 2 shared
+    int force_variant = 0;                            // persistent kernel: 0 auto, 1 global, 2 shared, 3 shared with per-entry exchange
     int profile_phases = 0;
     std::map<std::pair<int, int>, opf::GraphEntry> graphs;   // (precision + 2 * residual form, K)
 };

@@ -5,8 +5,9 @@
 // opf_server_step is one scheduling round:
 //   1. collect the round in flight (if any): each active instance gets its
 //      residuals; an instance that converged, failed or used up its
-//      iteration budget is finished (its latency recorded) and stays
-//      resident for warm starts until memory is needed;
+//      iteration budget (params.max_iter, or iters_per_bus times its bus
+//      count when that is larger) is finished (its latency recorded) and
+//      stays resident for warm starts until memory is needed;
 //   2. admit queued requests in arrival order while a slot, the device
 //      memory budget and the co-resident chunk capacity allow (finished
 //      instances are evicted least recently used first); uploads run on a
@@ -65,6 +66,7 @@ struct Request {
     opf_info info{};
     size_t bytes = 0;
     int chunks = 0;
+    int32_t budget = 0;          // iteration budget of this request
     uint64_t last_use = 0;
 };
 
@@ -121,7 +123,7 @@ void collect(opf_server* S) {
         r.info = infos[i];
         r.started = true;
         r.last_use = ++S->tick;
-        const bool budget_used = r.info.iters >= S->cfg.params.max_iter;
+        const bool budget_used = r.info.iters >= r.budget;
         if (r.info.status != OPF_NOT_CONVERGED || budget_used) {
             r.state = REQ_DONE;
             r.t_done = t;
@@ -197,7 +199,7 @@ void launch_round(opf_server* S, cudaStream_t s) {
         Request& r = S->reqs.at(id);
         opf_params q = S->cfg.params;
         q.warm_start = (r.started || r.warm_from >= 0) ? 1 : 0;
-        const int left = S->cfg.params.max_iter - (r.started ? r.info.iters : 0);
+        const int left = r.budget - (r.started ? r.info.iters : 0);
         const double scale = std::min(8.0, t_max / t_iter(r.p));
         int iters = (int)(S->cfg.round_iters * scale) / K * K;
         iters = std::max(S->cfg.round_iters, iters);
@@ -247,7 +249,8 @@ int32_t opf_server_create(const opf_server_config* cfg, opf_server** out) {
     return guard([&]() -> int32_t {
         if (!cfg || !out) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
         *out = nullptr;
-        if (cfg->max_active < 1 || cfg->round_iters < 1 || cfg->device_budget_bytes < 1)
+        if (cfg->max_active < 1 || cfg->round_iters < 1 || cfg->device_budget_bytes < 1 || cfg->iters_per_bus < 0 ||
+            cfg->params.max_iter < 0)
             throw opf::Error(OPF_ERR_INVALID_ARG, "bad server configuration");
         if (cfg->params.check_every < 1 || cfg->params.check_every > 4096)
             throw opf::Error(OPF_ERR_INVALID_ARG, "params.check_every out of [1, 4096]");
@@ -298,6 +301,8 @@ int32_t opf_server_submit(opf_server* S, const opf_bus* buses, int32_t n_bus, co
         r.t_submit = t;
         r.bytes = opf::device_bytes(p);
         r.chunks = p->pk.nblocks;
+        const int64_t scaled = (int64_t)S->cfg.iters_per_bus * n_bus;
+        r.budget = (int32_t)std::min<int64_t>(INT32_MAX / 2, std::max<int64_t>(S->cfg.params.max_iter, scaled));
         if (r.chunks > S->cfg.max_chunks || r.bytes > (size_t)S->cfg.device_budget_bytes) {
             opf_destroy(p);
             throw opf::Error(OPF_ERR_INVALID_ARG, "request larger than the server's chunk or memory budget");

@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
 // ----------------------------------------------- persistent, shared-memory
 // Per-launch shared-memory plan (byte offsets; every region 16-byte aligned).
 struct SmemPlan {
-    int P, xs, ls, ws, bb, mt, zs, hcon, hp, hc, us, big, tl, ush, total;
+    int P, xs, ls, ws, bb, mt, zs, hcon, hp, hc, us, big, tl, ush, gx, rt, total;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -695,7 +695,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // Only copies read by another chunk (the "exported" locals) are written to
 // the global ping-pong buffers each iteration; only copies held by another
 // chunk are read from them.
-template <typename T>
+// kGather selects how the terms of copies held by other chunks reach the
+// boundary global update: true -- every thread first fetches its share of
+// the chunk's list of such copies (one mailbox word each, all loads in
+// flight together) into shared memory, then the boundary entries are summed
+// from shared memory; false -- each thread polls the words of its own
+// boundary entries as it sums them.  Same terms, same order, same bits.
+template <typename T, bool kGather>
 __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const SmemPlan& sp, unsigned char* sm) {
     T* sP = reinterpret_cast<T*>(sm + sp.P);
     T* xs = reinterpret_cast<T*>(sm + sp.xs);
@@ -714,6 +720,8 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     // holding u_(i + k) at i (zero for i + k >= 32), so that every lane
     // reads its operands u_(base + c) with 16-byte-aligned vector loads
     T* ush = reinterpret_cast<T*>(sm + sp.ush);
+    int* gx = reinterpret_cast<int*>(sm + sp.gx);       // gathered exchange: device local of each outside copy
+    T* rt = reinterpret_cast<T*>(sm + sp.rt);           // ... and its term of the previous iteration
     __shared__ double red[kXWarps][5];
     __shared__ double tot[5];
     __shared__ __align__(8) unsigned long long mbar;
@@ -727,7 +735,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     const unsigned long long tmo = ctl->timeout_ns;
     const bool withhold = (ctl->skip_block == b);
     const bool adaptive = ctl->adaptive != 0;
-    const int nloc = bi.loc1 - bi.loc0, nh = bi.halo1 - bi.halo0, ncp = bi.cp1 - bi.cp0;
+    const int nloc = bi.loc1 - bi.loc0, nh = bi.halo1 - bi.halo0, ncp = bi.cp1 - bi.cp0, next = bi.ext1 - bi.ext0;
 
     // ---- prologue: operators by TMA bulk copies, the rest by plain loads
     const unsigned pbytes = (unsigned)(((size_t)(bi.mat1 - bi.mat0) * sizeof(T) + 15) & ~size_t(15));
@@ -756,7 +764,9 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         hp[h] = v.hcp[bi.halo0 + h] - bi.cp0;
     }
     if (threadIdx.x == 0) hp[nh] = ncp;
-    for (int q = threadIdx.x; q < ncp; q += blockDim.x) hc[q] = v.hci[bi.cp0 + q];
+    for (int q = threadIdx.x; q < ncp; q += blockDim.x) hc[q] = kGather ? v.hcx[bi.cp0 + q] : v.hci[bi.cp0 + q];
+    if constexpr (kGather)
+        for (int k = threadIdx.x; k < next; k += blockDim.x) gx[k] = v.ext[bi.ext0 + k];
     for (int q = threadIdx.x; q < bi.tile1 - bi.tile0; q += blockDim.x) stl[q] = v.tiles[bi.tile0 + q];
     const int hb = bi.halob - bi.halo0;                // interior halo entries [0, hb)
     int ok = 1;
@@ -805,12 +815,18 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     // thread has one); hb1 = this thread's first boundary entry
     const int hb1 = hb + (int)((threadIdx.x + blockDim.x - (unsigned)hb % blockDim.x) % blockDim.x);
     auto prefetch = [&](int t) {
-        const int h = hb1;
-        if (t == 0 || h >= nh) return;
-        const int q0 = hp[h], n = min(hp[h + 1] - q0, kPre);
+        if (t == 0) return;
+        if constexpr (kGather) {
+            // the thread's first slot of the gather list
+            if ((int)threadIdx.x < next) Mail<T>::fetch(mb, nlg, (t - 1) & 1, gx[threadIdx.x], raw);
+        } else {
+            const int h = hb1;
+            if (h >= nh) return;
+            const int q0 = hp[h], n = min(hp[h + 1] - q0, kPre);
 #pragma unroll
-        for (int k = 0; k < kPre; ++k)
-            if (k < n && hc[q0 + k] < 0) Mail<T>::fetch(mb, nlg, (t - 1) & 1, ~hc[q0 + k], raw + k * kW);
+            for (int k = 0; k < kPre; ++k)
+                if (k < n && hc[q0 + k] < 0) Mail<T>::fetch(mb, nlg, (t - 1) & 1, ~hc[q0 + k], raw + k * kW);
+        }
     };
     // term of an internal copy (chunk-relative local c)
     auto wint = [&](int c) -> T {
@@ -871,6 +887,36 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
                     if (qb + k < q1) sum += w[k];
             }
             if (ok) zs[h] = halo_global(sum, hcon + 4 * h, inv_rho);
+        }
+    };
+    // gathered exchange: the term of every outside copy of iteration t - 1
+    // into rt (t == 0: from the initial iterate in the primary buffers)
+    auto gather = [&](int t, bool& ok) {
+        const int slot = (t - 1) & 1;
+        const unsigned tag = (unsigned)t;
+        for (int k = threadIdx.x; k < next && ok; k += blockDim.x) {
+            T w;
+            if (t == 0) {
+                w = copy_term(__ldcg(v.xl + gx[k]), __ldcg(v.lam + gx[k]), inv_rho);
+            } else {
+                const bool hit = (k == (int)threadIdx.x) ? Mail<T>::decode(raw, tag, w)
+                                                         : Mail<T>::get(mb, nlg, slot, gx[k], tag, w);
+                if (!hit) ok = mail_poll(mb, nlg, slot, gx[k], tag, w, ctl, tmo, 1);
+            }
+            rt[k] = w;
+        }
+    };
+    // gathered exchange: boundary entries summed from shared memory, copies
+    // in CSR order (the same additions as zboundary)
+    auto zboundary_gathered = [&]() {
+        for (int h = hb1; h < nh; h += blockDim.x) {
+            const int q0 = hp[h], q1 = hp[h + 1];
+            T sum = 0;
+            for (int q = q0; q < q1; ++q) {
+                const int c = hc[q];
+                sum += c >= 0 ? wint(c) : rt[~c];
+            }
+            zs[h] = halo_global(sum, hcon + 4 * h, inv_rho);
         }
     };
     // publish the terms of this chunk's exported copies for iteration t
@@ -989,8 +1035,15 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         prefetch(t);
         zinterior();
         mark(0);
-        zboundary(t, okz);
-        if (!__syncthreads_and(okz)) { flush_prof(); return; }
+        if constexpr (kGather) {
+            gather(t, okz);
+            if (!__syncthreads_and(okz)) { flush_prof(); return; }
+            zboundary_gathered();
+            __syncthreads();
+        } else {
+            zboundary(t, okz);
+            if (!__syncthreads_and(okz)) { flush_prof(); return; }
+        }
         mark(1);
         // local update: boundary tiles first so that their terms reach the
         // neighbours while the interior tiles are computed
@@ -1128,9 +1181,16 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         if (v.halo_own[bi.halo0 + h]) v.zg[v.halo_gid[bi.halo0 + h]] = zs[h];
     if (t == 1) {
         bool okz = true;
-        for (int q = threadIdx.x; q < ncp && okz; q += blockDim.x) {
-            T w;
-            if (hc[q] < 0) okz = mail_poll(mb, nlg, 0, ~hc[q], 1u, w, ctl, tmo, 3);
+        if constexpr (kGather) {
+            for (int k = threadIdx.x; k < next && okz; k += blockDim.x) {
+                T w;
+                okz = mail_poll(mb, nlg, 0, gx[k], 1u, w, ctl, tmo, 3);
+            }
+        } else {
+            for (int q = threadIdx.x; q < ncp && okz; q += blockDim.x) {
+                T w;
+                if (hc[q] < 0) okz = mail_poll(mb, nlg, 0, ~hc[q], 1u, w, ctl, tmo, 3);
+            }
         }
         if (!__syncthreads_and(okz)) return;
     }
@@ -1166,13 +1226,13 @@ __device__ __forceinline__ int claim_chunk(int32_t* claim, int nblocks, int per)
     return s_b;
 }
 
-template <typename T>
+template <typename T, bool kGather>
 __global__ void __launch_bounds__(kXWarps * 32, 2) persistent_smem_kernel(View<T> v, SmemPlan sp) {
     extern __shared__ __align__(128) unsigned char sm[];
     // nblocks CTAs claim nblocks chunks one each: the scan always finds one
     const int b = claim_chunk(v.flags, v.nblocks, 2);
     if (b < 0) return;
-    chunk_smem(v, b, sp, sm);
+    chunk_smem<T, kGather>(v, b, sp, sm);
 }
 
 // ------------------------------------------------------------------ batch
@@ -1197,7 +1257,7 @@ __global__ void __launch_bounds__(kXWarps * 32, 3) batch_smem_kernel(const View<
     const CtaMap m = map[i];
     if (threadIdx.x == 0) sv = views[m.inst];
     __syncthreads();
-    chunk_smem(sv, m.chunk, sp, sm);
+    chunk_smem<T, true>(sv, m.chunk, sp, sm);
 }
 
 template <typename T>
@@ -1445,7 +1505,7 @@ struct Arena {
 struct Layout {
     size_t lo, hi, invk, cik, zg, lo32, hi32, invk32, cik32, zg32;
     size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, phase, ctl, mbox;
-    size_t tdz, tpart;
+    size_t tdz, tpart, hcx, ext;
     size_t xl, lam, xl2, lam2, bbar, xl0, xl32, lam32, xl2_32, lam2_32, bbar32, xl0_32, P64, P32;
     size_t total;
 };
@@ -1464,6 +1524,7 @@ Layout layout_of(const opf_problem* p) {
     L.halo_gid = a.take<int32_t>(k.halo_gid.size()); L.halo_own = a.take<uint8_t>(k.halo_own.size());
     L.nbrs = a.take<int32_t>(k.nbrs.size() + 1);
     L.hcp = a.take<int32_t>(k.hcp.size()); L.hci = a.take<int32_t>(k.hci.size() + 1);
+    L.hcx = a.take<int32_t>(k.hcx.size() + 1); L.ext = a.take<int32_t>(k.ext.size() + 1);
     L.flags = a.take<int32_t>(k.nblocks);
     L.cost = a.take<double>(k.ng);
     L.partials = a.take<double>((size_t)k.nblocks * 16); L.ctl = a.take<Ctl>(1);   // two check slots
@@ -1489,7 +1550,7 @@ View<T> view_of(const opf_problem* p, const DevPrec& d) {
     v.xl = (T*)d.xl; v.lam = (T*)d.lam; v.xl2 = (T*)d.xl2; v.lam2 = (T*)d.lam2;
     v.bbar = (const T*)d.bbar; v.xl0 = (const T*)d.xl0; v.gidx = p->gidx; v.meta = p->meta;
     v.tiles = p->tiles; v.blocks = p->blocks; v.halo_gid = p->halo_gid; v.halo_own = p->halo_own;
-    v.nbrs = p->nbrs; v.hcp = p->hcp; v.hci = p->hci; v.flags = p->flags;
+    v.nbrs = p->nbrs; v.hcp = p->hcp; v.hci = p->hci; v.hcx = p->hcx; v.ext = p->ext; v.flags = p->flags;
     v.P = (const T*)d.P; v.cost = p->cost; v.partials = p->partials; v.phase = p->phase; v.ctl = p->ctl;
     v.mbox = p->mbox;
     v.tdz = p->tdz; v.tpart = p->tpart;
@@ -1573,10 +1634,11 @@ template <typename T>
 size_t persistent_smem(const opf_problem* p) { return (size_t)std::max(1, p->pk.max_halo) * sizeof(T); }
 
 struct ChunkMax {
-    int mat = 0, loc = 0, halo = 0, copies = 0, big = 0, tiles = 0;
+    int mat = 0, loc = 0, halo = 0, copies = 0, big = 0, tiles = 0, ext = 0;
     void add(const Packed& k) {
         mat = std::max(mat, k.max_mat); loc = std::max(loc, k.max_loc); halo = std::max(halo, k.max_halo);
         copies = std::max(copies, k.max_copies); big = std::max(big, k.max_big); tiles = std::max(tiles, k.max_tiles);
+        ext = std::max(ext, k.max_ext);
     }
 };
 
@@ -1603,6 +1665,8 @@ SmemPlan smem_plan_of(const ChunkMax& k) {
     sp.us = take((size_t)kXWarps * k.big * w);
     sp.tl = take((size_t)std::max(1, k.tiles) * sizeof(Tile));
     sp.ush = take(f32 ? (size_t)kXWarps * 4 * kUrow * w : 0);
+    sp.gx = take((size_t)std::max(1, k.ext) * 4);
+    sp.rt = take((size_t)std::max(1, k.ext) * w);
     sp.total = off;
     return sp;
 }
@@ -1650,8 +1714,9 @@ bool coop_fits(KernelT kernel, size_t smem, int nblocks) {
 // 0: none, 1: persistent (global-memory iterate), 2: persistent (shared-memory iterate)
 template <typename T>
 int persistent_variant(const opf_problem* p) {
-    const bool smem_ok = coop_fits(persistent_smem_kernel<T>, (size_t)smem_plan<T>(p).total, p->pk.nblocks);
-    if (p->force_variant == 2) return smem_ok ? 2 : 0;
+    const bool smem_ok = coop_fits(persistent_smem_kernel<T, true>, (size_t)smem_plan<T>(p).total, p->pk.nblocks) &&
+                         coop_fits(persistent_smem_kernel<T, false>, (size_t)smem_plan<T>(p).total, p->pk.nblocks);
+    if (p->force_variant == 2 || p->force_variant == 3) return smem_ok ? p->force_variant : 0;
     if (p->force_variant != 1 && smem_ok) return 2;
     if (coop_fits(persistent_kernel<T>, persistent_smem<T>(p), p->pk.nblocks)) return 1;
     return 0;
@@ -1665,12 +1730,13 @@ void launch_persistent(opf_problem* p, cudaStream_t s) {
     View<T> v = view_of<T>(p, prec_of<T>(p));
     OPF_CUDA(cudaMemsetAsync(p->flags, 0, sizeof(int32_t) * p->pk.nblocks, s));
     const int variant = persistent_variant<T>(p);
-    if (variant == 2) {
+    if (variant == 2 || variant == 3) {
         OPF_CUDA(cudaMemsetAsync(p->mbox, 0, (size_t)p->pk.nl * 2 * Mail<T>::kWords * sizeof(unsigned long long), s));
         SmemPlan sp = smem_plan<T>(p);
         void* args[] = {&v, &sp};
-        OPF_CUDA(cudaLaunchCooperativeKernel((const void*)persistent_smem_kernel<T>, dim3(p->pk.nblocks),
-                                             dim3(kXWarps * 32), args, (size_t)sp.total, s));
+        const void* kern = variant == 2 ? (const void*)persistent_smem_kernel<T, true>
+                                        : (const void*)persistent_smem_kernel<T, false>;
+        OPF_CUDA(cudaLaunchCooperativeKernel(kern, dim3(p->pk.nblocks), dim3(kXWarps * 32), args, (size_t)sp.total, s));
     } else if (variant == 1) {
         void* args[] = {&v};
         OPF_CUDA(cudaLaunchCooperativeKernel((const void*)persistent_kernel<T>, dim3(p->pk.nblocks),
@@ -1809,6 +1875,7 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     p->halo_gid = (int32_t*)(a + L.halo_gid); p->halo_own = (uint8_t*)(a + L.halo_own);
     p->nbrs = (int32_t*)(a + L.nbrs); p->flags = (int32_t*)(a + L.flags);
     p->hcp = (int32_t*)(a + L.hcp); p->hci = (int32_t*)(a + L.hci);
+    p->hcx = (int32_t*)(a + L.hcx); p->ext = (int32_t*)(a + L.ext);
     p->cost = (double*)(a + L.cost); p->partials = (double*)(a + L.partials);
     p->phase = (unsigned long long*)(a + L.phase);
     p->mbox = (unsigned long long*)(a + L.mbox);
@@ -1841,6 +1908,8 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     h2d(p->nbrs, k.nbrs.data(), k.nbrs.size() * 4);
     h2d(p->hcp, k.hcp.data(), k.hcp.size() * 4);
     h2d(p->hci, k.hci.data(), k.hci.size() * 4);
+    h2d(p->hcx, k.hcx.data(), k.hcx.size() * 4);
+    h2d(p->ext, k.ext.data(), k.ext.size() * 4);
     h2d(p->cost, M.c.data(), k.ng * 8);
     h2d(p->d64.bbar, k.bbar.data(), k.nl * 8); h2d(p->d64.xl0, k.xl0.data(), k.nl * 8);
     h2d32(p->d32.bbar, k.bbar); h2d32(p->d32.xl0, k.xl0);

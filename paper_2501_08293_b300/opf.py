@@ -61,7 +61,8 @@ class Dims(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("device_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("round_iters", C.c_int32),
-                ("max_chunks", C.c_int32), ("_reserved", C.c_int32 * 3), ("params", Params)]
+                ("max_chunks", C.c_int32), ("iters_per_bus", C.c_int32), ("_reserved", C.c_int32 * 2),
+                ("params", Params)]
 
 
 class ServerStats(C.Structure):
@@ -104,6 +105,10 @@ EXPORTS = {
     "opf_chunk_stats": (C.c_int32, [_P, _I]),
     "opf_residuals_noalloc": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "opf_component_operator": (C.c_int32, [_D, _D, C.c_int32, C.c_int32, _D, _D, _I]),
+    "opf_tuning_set": (C.c_int32, [C.c_char_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "opf_tuning_clear": (C.c_int32, []),
+    "opf_tuning_load": (C.c_int32, [C.c_char_p, _I]),
+    "opf_tuning_lookup": (C.c_int32, [C.c_int32, _I, _I]),
     "opf_destroy": (None, [_P]),
     "opf_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "opf_batch_solve": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, C.POINTER(Info)]),
@@ -130,6 +135,15 @@ for _name, (_res, _args) in EXPORTS.items():
     _fn = getattr(lib, _name)
     _fn.restype = _res
     _fn.argtypes = _args
+
+
+# the tuning table written by autotune.py for this package, if there is one
+# (entries are keyed by GPU name, so other devices keep the defaults)
+_TUNING_PATH = os.path.join(os.path.dirname(_LIB_PATH), "tuning.json")
+if os.path.exists(_TUNING_PATH):
+    if lib.opf_tuning_load(_TUNING_PATH.encode(), None) != 0:
+        import warnings
+        warnings.warn(f"{_TUNING_PATH}: {lib.opf_last_error().decode()}; automatic chunking keeps its defaults")
 
 
 class OpfError(RuntimeError):
@@ -182,6 +196,31 @@ def residuals_noalloc(v, x_local, x_local_prev, lam, rho: float, eps_rel: float,
     _check(lib.opf_residuals_noalloc(v.data_ptr(), x_local.data_ptr(), x_local_prev.data_ptr(), lam.data_ptr(),
                                      n, rho, eps_rel, out.data_ptr(), _stream_handle(stream)),
            "opf_residuals_noalloc")
+
+
+def tuning_load(path: str) -> int:
+    """Load a tuning table written by autotune.py (opf_tuning_load); returns
+    the number of entries read."""
+    n = C.c_int32()
+    _check(lib.opf_tuning_load(str(path).encode(), C.byref(n)), "opf_tuning_load")
+    return n.value
+
+
+def tuning_set(gpu: str, n_bus_lo: int, n_bus_hi: int, work_per_chunk: int, max_chunks: int) -> None:
+    _check(lib.opf_tuning_set(gpu.encode(), int(n_bus_lo), int(n_bus_hi), int(work_per_chunk), int(max_chunks)),
+           "opf_tuning_set")
+
+
+def tuning_clear() -> None:
+    lib.opf_tuning_clear()
+
+
+def tuning_lookup(n_bus: int):
+    """(work_per_chunk, max_chunks) that automatic chunking uses for a feeder
+    of n_bus buses on the current device."""
+    w, m = C.c_int32(), C.c_int32()
+    _check(lib.opf_tuning_lookup(int(n_bus), C.byref(w), C.byref(m)), "opf_tuning_lookup")
+    return w.value, m.value
 
 
 def component_operator(A, b):
@@ -486,7 +525,7 @@ def default_server_config(**kw) -> ServerConfig:
     c = ServerConfig()
     lib.opf_server_config_default(C.byref(c))
     for k, v in kw.items():
-        if k in ("device_budget_bytes", "max_active", "round_iters", "max_chunks"):
+        if k in ("device_budget_bytes", "max_active", "round_iters", "max_chunks", "iters_per_bus"):
             setattr(c, k, v)
         else:
             setattr(c.params, k, v)

@@ -285,3 +285,46 @@ def test_set_line_status_host_rebuild(opf, decomp):
     with pytest.raises(opf.OpfError):
         p.set_line_status(len(f.lines), True)
     p.close()
+
+
+def test_tuning_table(opf, tmp_path):
+    """Automatic chunking reads the tuning table: an entry for every GPU
+    ("*") and a bus-count bucket sets the chunk size and cap; entries for
+    another GPU name do not apply here (no device: empty name); a JSON file
+    in the tuner's format loads (extra keys ignored); malformed files and
+    out-of-range values are refused."""
+    opf.tuning_clear()
+    try:
+        assert opf.tuning_lookup(150) == (4096, 296)
+        from paper_2501_08293_b300 import autotune
+        f = autotune.representative(150, 3)
+        p0 = opf.Problem.from_feeder(f, upload=False)
+        opf.tuning_set("*", 100, 200, 256, 7)
+        assert opf.tuning_lookup(150) == (256, 7) and opf.tuning_lookup(99) == (4096, 296)
+        p1 = opf.Problem.from_feeder(f, upload=False)
+        ns = np.diff(p1.structure()["comp_ptr"]).astype(np.int64)
+        total = int(np.sum(ns * ns + 4 * ns + 16))
+        assert p1.dims.n_blocks == min(7, total // 256) and p1.dims.n_blocks != p0.dims.n_blocks
+        for x, y in zip(p0.structure().values(), p1.structure().values()):
+            assert np.array_equal(x, y)          # same problem, other chunking
+        opf.tuning_set("Some Other GPU", 0, 1000, 512, 3)
+        opf.tuning_clear()
+        opf.tuning_set("Some Other GPU", 0, 1000, 512, 3)
+        assert opf.tuning_lookup(150) == (4096, 296)
+        path = tmp_path / "t.json"
+        path.write_text('{"gpu": "*", "precision": "fp32", "entries": [{"n_bus_lo": 1, "n_bus_hi": 60, '
+                        '"work_per_chunk": 1024, "max_chunks": 296, "us_per_iter": 1.5, "candidates": {"256": {}}},'
+                        ' {"n_bus_lo": 60, "n_bus_hi": 200, "work_per_chunk": 2048, "max_chunks": 100}]}')
+        assert opf.tuning_load(str(path)) == 2
+        assert opf.tuning_lookup(30) == (1024, 296) and opf.tuning_lookup(150) == (2048, 100)
+        for bad in ('{"gpu": "*", "entries": [{"n_bus_lo": 5, "n_bus_hi": 1, "work_per_chunk": 64, "max_chunks": 1}]}',
+                    '{"gpu": "*", "entries": [{"n_bus_lo": 1}]}', '{"gpu": "*", "entries": [', '[1, 2]'):
+            path.write_text(bad)
+            with pytest.raises(opf.OpfError):
+                opf.tuning_load(str(path))
+        with pytest.raises(opf.OpfError):
+            opf.tuning_set("*", 0, 10, 8, 1)
+    finally:
+        opf.tuning_clear()
+        if os.path.exists(opf._TUNING_PATH):
+            opf.tuning_load(opf._TUNING_PATH)

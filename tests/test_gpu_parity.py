@@ -169,7 +169,13 @@ def test_full_size_8500_class_parity(opf):
 # lambda is compared in the variable in which ADMM is non-expansive, the
 # scaled dual lambda / rho, against the scale of the local iterate:
 # |dlambda_i| / rho <= TOL (|lambda_i| / rho + max |lambda| / rho + max |z|).
+# The scaled dual is a running sum of the primal residuals B x - x_s of all
+# iterations so far, so its rounding errors add up linearly in t rather than
+# as a square root: t * 4u ~ 200 * 4 * 6e-8 = 4.8e-5 at t = 200 (two
+# roundings in the residual, one in the sum, one in the division by rho);
+# measured on B300: 1.7e-5 (rho = 100) and 2.8e-5 (rho = 10).
 TOL_FP32_T200 = 1e-5
+TOL_FP32_DUAL_T200 = 5e-5
 
 
 def rel_scaled_dual(lam, lam_ref, z_ref, rho):
@@ -183,8 +189,9 @@ def rel_scaled_dual(lam, lam_ref, z_ref, rho):
 def test_fp32_per_iterate_parity_8500_class(opf, rho):
     """The headline configuration (8500-class feeder, FP32 sweeps with FP64
     residual sums, default engine and chunking, check every 50) against the
-    FP64 oracle at t = 200: x, z and lambda / rho within TOL_FP32_T200
-    normwise and element by element, residuals within 1e-3 relative."""
+    FP64 oracle at t = 200: x and z within TOL_FP32_T200, lambda / rho
+    within TOL_FP32_DUAL_T200, normwise and element by element; residuals
+    within 1e-3 relative."""
     f = F.feeder_8500(1)
     p = opf.Problem.from_feeder(f)
     m, pre, s = oracle_solver(f, rho)
@@ -194,7 +201,8 @@ def test_fp32_per_iterate_parity_8500_class(opf, rho):
         r = s.step()
     xg, xl, lam = p.state()
     errs = {"x": rel(xg, s.x), "z": rel(xl, s.z), "lam/rho": rel_scaled_dual(lam, s.lam, s.z, rho)}
-    assert max(errs.values()) <= TOL_FP32_T200, errs
+    assert errs["x"] <= TOL_FP32_T200 and errs["z"] <= TOL_FP32_T200, errs
+    assert errs["lam/rho"] <= TOL_FP32_DUAL_T200, errs
     assert abs(info.pres - r.pres) <= 1e-3 * r.pres and abs(info.dres - r.dres) <= 1e-3 * r.dres
     assert abs(info.eps_prim - r.eps_prim) <= 1e-5 * r.eps_prim
     p.close()
@@ -459,8 +467,9 @@ def test_paper_decomposition_parity(opf, engine, maker, rho):
 
 def test_paper_decomposition_8500_class(opf):
     """Full-size feeder under the paper's decomposition: 200 FP64 iterations
-    against the oracle, and an FP32 solve of the 123-bus feeder to ABS 1e-4
-    whose objective is within 1e-4 of the fine decomposition's."""
+    against the oracle; and both decompositions of the 13-bus feeder solved
+    tightly (FP64, ABS 1e-8) reach the LP optimum (stored HiGHS objective)
+    to 1e-6, while FP32 solves of the 123-bus feeder converge to ABS 1e-4."""
     from oracle import admm as OA, model as OM, precompute as OP
     f = F.feeder_8500(1)
     p = opf.Problem.from_feeder(f, decomposition=opf.DECOMP_PAPER)
@@ -473,12 +482,15 @@ def test_paper_decomposition_8500_class(opf):
     assert rel(xg, s.x) <= TOL and rel(xl, s.z) <= TOL and rel(lam, s.lam) <= TOL
     assert abs(info.pres - r.pres) <= TOL * r.pres
     p.close()
-    g = F.feeder_123(1)
-    objs = []
+    import json, os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "lp_objectives.json")) as fh:
+        lp13 = json.load(fh)["feeders"]["13"]["objective"]
     for d in (opf.DECOMP_FINE, opf.DECOMP_PAPER):
-        q = opf.Problem.from_feeder(g, decomposition=d)
+        q = opf.Problem.from_feeder(F.feeder_13(1), decomposition=d)
+        inf = q.solve(opf.default_params(rho=100.0, max_iter=2000000, eps_abs_prim=1e-8, eps_abs_dual=1e-8))
+        assert inf.status == opf.OK and abs(inf.objective - lp13) <= 1e-6 * abs(lp13), (d, inf.objective, lp13)
+        q.close()
+        q = opf.Problem.from_feeder(F.feeder_123(1), decomposition=d)
         inf = q.solve(opf.default_params(rho=10.0, precision=opf.FP32, max_iter=400000))
         assert inf.status == opf.OK
-        objs.append(inf.objective)
         q.close()
-    assert abs(objs[1] - objs[0]) <= 1e-4 * abs(objs[0])
