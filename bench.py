@@ -732,8 +732,11 @@ def run_scenarios(args):
     """64 load draws on the 8500-class topology (each load's a, b scaled by its
     own factor ~ U[0.5, 1]) iterated together by the multi-scenario engine,
     FP32: one step = scenario-iters iterations of every scenario; value =
-    scenario-iterations per second.  Also the 123-bus feeder's 64 scenarios
-    solved to ABS 1e-4 (solves/s), and the per-kernel times."""
+    scenario-iterations per second.  Both x-update kinds are timed (small
+    shared-operator components on CUDA cores, bit-identical to single-
+    instance FP32, or on tensor cores in 3xTF32); the line's value is the
+    faster one, the other is reported beside it.  Also the 123-bus feeder's
+    64 scenarios solved to ABS 1e-4 (solves/s), and the per-kernel times."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
@@ -744,28 +747,38 @@ def run_scenarios(args):
     S = args.scenarios
     f = F.feeder_8500(args.seed)
     loads = F.load_scenarios(f, S, seed=args.seed + 100)
-    t0 = time.perf_counter()
-    sc = opf.Scenarios.from_feeder(f, loads)
-    t_create = time.perf_counter() - t0
     prm = opf.default_params(rho=args.rho, precision=opf.FP32, criterion=opf.CRIT_NEVER,
                              max_iter=args.scenario_iters, check_every=50)
-    kt = sc.profile(prm, reps=20)
-    for _ in range(args.warmup):
-        sc.solve(prm)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    times = []
+    kinds = {"cuda_cores": opf.SC_XUPDATE_CUDA_CORES, "tensor_3xtf32": opf.SC_XUPDATE_TENSOR}
+    per_kind = {}
+    t_create = None
     with ClockSampler(0) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sc.solve(prm)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-    tot = sum(times)
+        for name, kind in kinds.items():
+            t0 = time.perf_counter()
+            sc = opf.Scenarios.from_feeder(f, loads)
+            t_create = time.perf_counter() - t0 if t_create is None else t_create
+            sc.set_xupdate(kind)
+            kt = sc.profile(prm, reps=20)
+            for _ in range(args.warmup):
+                sc.solve(prm)
+            times = []
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sc.solve(prm)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            sc.close()
+            per_kind[name] = {"seconds": sum(times), "value": args.steps * args.scenario_iters * S / sum(times),
+                              "us_per_iteration_all_scenarios": 1e6 * sum(times) / (args.steps * args.scenario_iters),
+                              "kernel_us": kt}
+    best = max(per_kind, key=lambda k: per_kind[k]["value"])
+    tot = per_kind[best]["seconds"]
     iters = args.steps * args.scenario_iters * S
     p1 = opf.Problem.from_feeder(f, upload=False)
     d = p1.dims
@@ -775,11 +788,11 @@ def run_scenarios(args):
     bytes_iter = S * (d.n_local * 20 + d.n_global * 4) + 4 * d.sum_n2 + d.n_global * 24 + d.n_local * 8
     peaks, kind = measured_peaks()
     achieved = bytes_iter * args.steps * args.scenario_iters / tot / 1e9
-    sc.close()
-    # to tolerance on the 123-bus feeder: 64 scenarios at once
+    # to tolerance on the 123-bus feeder: 64 scenarios at once, the chosen kind
     f2 = F.feeder_123(args.seed)
     l2 = F.load_scenarios(f2, S, seed=args.seed + 100)
     sc2 = opf.Scenarios.from_feeder(f2, l2)
+    sc2.set_xupdate(kinds[best])
     tt = opf.default_params(rho=args.rho, precision=opf.FP32, max_iter=200000, check_every=50)
     sc2.solve(tt)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -798,14 +811,17 @@ def run_scenarios(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{S} load draws on the 8500-class feeder (11,932 buses), a, b x U[0.5, 1] per load",
                    "rho": args.rho, "iters_per_step": args.scenario_iters, "create_s": t_create,
-                   "l2": "flushed before each step"},
+                   "xupdate": best, "l2": "flushed before each step"},
+        "xupdate_kinds": per_kind,
         "roofline": {"kernel": "scenario sweep (global update + local updates, all kernels)", "bound": "hbm",
                      "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": SC_TRAFFIC_PER_ITER_B if (S == 64 and args.seed == 1) else None,
+                     "traffic": (SC_TRAFFIC_PER_ITER_B if (S == 64 and args.seed == 1 and best == "cuda_cores")
+                                 else None),
                      "traffic_note": "DRAM bytes per iteration of all scenarios (sum of the three kernels, one "
-                                     "cold-cache ncu capture); the unit of achieved is one iteration as well",
-                     "peak_kind": kind, "bytes_per_iter": bytes_iter, "kernel_us": kt},
+                                     "cold-cache ncu capture of the CUDA-core kernels); the unit of achieved is one "
+                                     "iteration as well",
+                     "peak_kind": kind, "bytes_per_iter": bytes_iter},
         "to_tolerance_123bus": {"scenarios": S, "converged": conv, "seconds": t2,
                                 "iters_max": max(i.iters for i in inf2), "iters_min": min(i.iters for i in inf2),
                                 "solves_per_s": conv / t2},

@@ -523,6 +523,22 @@ int32_t opf_scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* 
  * per-scenario check.  Uses params->rho; leaves the scenarios at a cold
  * start.                                                                   */
 int32_t opf_scenarios_profile(opf_scenarios* sc, const opf_params* params, int32_t reps, void* stream, double* us);
+/* Arithmetic of the local update of Eq. (closed_2) for the components with
+ * at most 8 locals whose operator P_s is shared by every scenario (buses,
+ * lines, generators, constant-power loads): for 64 scenarios at a time it
+ * is the small matrix product X_s = P_s U_s + bbar_s.
+ *   OPF_SC_XUPDATE_CUDA_CORES (default): packed FP32 fmas, the operation
+ *     order of the single-instance engines, so each scenario's iterates are
+ *     bit-identical to solving it alone in FP32;
+ *   OPF_SC_XUPDATE_TENSOR: tensor cores (mma.sync m16n8k8, TF32 inputs,
+ *     FP32 accumulation) with each operand split into two TF32 parts and
+ *     three products (hi*hi + hi*lo + lo*hi), about FP32 accuracy but not
+ *     the same bits; used on the iterations between residual checks (a
+ *     check iteration and the per-scenario operators of voltage-dependent
+ *     loads keep the CUDA-core path).
+ * Takes effect at the next opf_scenarios_solve.  INVALID_ARG otherwise.   */
+enum { OPF_SC_XUPDATE_CUDA_CORES = 0, OPF_SC_XUPDATE_TENSOR = 1 };
+int32_t opf_scenarios_set_xupdate(opf_scenarios* sc, int32_t kind);
 void opf_scenarios_destroy(opf_scenarios* sc);
 
 /* ----------------------------------------------------------------- serving

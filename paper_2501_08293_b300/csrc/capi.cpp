@@ -37,6 +37,7 @@ void scenarios_solve(opf_scenarios* sc, const opf_params& prm, cudaStream_t s, o
 void scenarios_get_state(const opf_scenarios* sc, int k, double* xg, double* xl, double* lam, cudaStream_t s);
 void scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* n_local, int64_t* device_bytes);
 void scenarios_profile(opf_scenarios* sc, const opf_params& prm, int reps, cudaStream_t s, double* us);
+void scenarios_set_xupdate(opf_scenarios* sc, int kind);
 void device_reprecompute(opf_problem* p, const std::vector<int>& comps, cudaStream_t s);
 void device_update_bounds(opf_problem* p, const std::vector<std::pair<int, int>>& ranges, cudaStream_t s);
 }  // namespace opf
@@ -590,6 +591,14 @@ int32_t opf_scenarios_profile(opf_scenarios* sc, const opf_params* prm, int32_t 
         if (!sc || !prm || !us) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
         if (reps < 1 || !(prm->rho > 0.0)) throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
         opf::scenarios_profile(sc, *prm, reps, (cudaStream_t)stream, us);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_scenarios_set_xupdate(opf_scenarios* sc, int32_t kind) {
+    return guarded([&]() -> int32_t {
+        if (!sc) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        opf::scenarios_set_xupdate(sc, kind);
         return OPF_OK;
     });
 }

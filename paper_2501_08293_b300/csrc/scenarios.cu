@@ -307,7 +307,90 @@ __device__ __forceinline__ void sc_small_rows(const ScView& v, const ScComp& cd,
     }
 }
 
-template <bool check>
+// ---- tensor-core (3xTF32) local update of small shared-operator components
+// x -> (hi, lo), both TF32 (hi = x rounded to TF32, lo = the remainder
+// rounded to TF32): about 21 significant bits of x.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+// D += A B, A 16 x 8 (row-major), B 8 x 8 (column-major), TF32 in, FP32
+// accumulate; fragment of lane l (g = l / 4, t = l % 4): a = {A[g][t],
+// A[g+8][t], A[g][t+4], A[g+8][t+4]}, b = {B[t][g], B[t+4][g]},
+// d = {D[g][2t], D[g][2t+1], D[g+8][2t], D[g+8][2t+1]}.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+                 "{%0, %1, %2, %3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One small component with a shared operator, the warp's 64 scenarios of
+// this pass [base, base + 64) on tensor cores: for each block of 16
+// scenarios, D (16 scenarios x 8 rows) = U^T (16 x 8 columns) P^T (8 x 8),
+// i.e. D[s][r] = sum_c P[r][c] u_c(s), in three TF32 products (lo*hi +
+// hi*lo + hi*hi, FP32 accumulation), then x = D + bbar, the dual update
+// and the copy term for the next global update.  Columns and rows past n
+// are zero in the padded operator (and u is zero there).
+__device__ __forceinline__ void sc_small_tc(const ScView& v, const ScComp& cd, int gl, int base, int lane, bool keepx,
+                                            float rho, float inv_rho) {
+    const int n = cd.nf & 0xFFFF, j0 = cd.loc0, Sp = v.Sp;
+    const int g = lane >> 2, t = lane & 3;
+    const float* Ps = v.Ps + cd.poff;              // P[r][c] at c * 8 + r
+    uint32_t bh0, bl0, bh1, bl1;
+    split_tf32(Ps[t * 8 + g], bh0, bl0);           // B[t][g] = P[g][t]
+    split_tf32(Ps[(t + 4) * 8 + g], bh1, bl1);     // B[t+4][g] = P[g][t+4]
+    const int gc0 = __shfl_sync(0xffffffffu, gl, t), gc1 = __shfl_sync(0xffffffffu, gl, t + 4);
+    const int gr0 = __shfl_sync(0xffffffffu, gl, 2 * t), gr1 = __shfl_sync(0xffffffffu, gl, 2 * t + 1);
+    const bool c0 = t < n, c1 = t + 4 < n;
+    const int rr[2] = {2 * t, 2 * t + 1};
+    const int gr[2] = {gr0, gr1};
+    const bool var_b = (cd.nf & kVarB) != 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int sa = base + 16 * m + g, sb = sa + 8;
+        auto uval = [&](bool live, int gc, int c, int sc) -> float {
+            if (!live) return 0.f;
+            return u_of(v.Z[(size_t)gc * Sp + sc], v.L[(size_t)(j0 + c) * Sp + sc], inv_rho);
+        };
+        uint32_t ah[4], al[4];
+        split_tf32(uval(c0, gc0, t, sa), ah[0], al[0]);
+        split_tf32(uval(c0, gc0, t, sb), ah[1], al[1]);
+        split_tf32(uval(c1, gc1, t + 4, sa), ah[2], al[2]);
+        split_tf32(uval(c1, gc1, t + 4, sb), ah[3], al[3]);
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_tf32(d, al, bh0, bh1);
+        mma_tf32(d, ah, bl0, bl1);
+        mma_tf32(d, ah, bh0, bh1);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int r = rr[h & 1];
+            const int sc = (h < 2) ? sa : sb;
+            if (r >= n) continue;
+            const size_t e = (size_t)(j0 + r) * Sp + sc;
+            const float z = v.Z[(size_t)gr[h & 1] * Sp + sc];
+            const float l = v.L[e];
+            const float bb = var_b ? v.bv[(size_t)(cd.boff + r) * Sp + sc] : v.bs[cd.boff + r];
+            const float xn = d[h] + bb;
+            const float ln = dual_of(l, rho, z, xn);
+            if ((v.amask[sc >> 5] >> (sc & 31)) & 1u) {
+                v.L[e] = ln;
+                v.W[e] = copy_term(xn, ln, inv_rho);
+                if (keepx) v.X[e] = xn;
+            }
+        }
+    }
+}
+
+// kTC (plain iterations only): components with a shared operator go to the
+// tensor-core path above, those with per-scenario operators keep the
+// CUDA-core rows.
+template <bool check, bool kTC = false>
 __global__ void __launch_bounds__(kXsWarps * 32, check ? 2 : 4) sc_xs_kernel(ScView v, int q) {
     __shared__ double red[check ? kXsWarps : 1][5][64];
     const ScCtl* ctl = v.ctl;
@@ -329,6 +412,16 @@ __global__ void __launch_bounds__(kXsWarps * 32, check ? 2 : 4) sc_xs_kernel(ScV
             const int gl = ngl;
             const int n = cd.nf & 0xFFFF;
             const int j0 = cd.loc0;
+            if constexpr (kTC) {
+                if (!(cd.nf & kVarP)) {
+                    if (s + nw < v.nsmall) {
+                        ncd = v.comps[s + nw];
+                        ngl = lane < (ncd.nf & 0xFFFF) ? v.gidx[ncd.loc0 + lane] : 0;
+                    }
+                    sc_small_tc(v, cd, gl, k0 - 2 * lane, lane, keepx, rho, inv_rho);
+                    continue;
+                }
+            }
             float2 u[kSmallN];
 #pragma unroll
             for (int c = 0; c < kSmallN; ++c) {
@@ -564,6 +657,8 @@ struct opf_scenarios {
     uint32_t* am_host = nullptr;     // pinned, Sp / 32 words
     bool cold = true;
     int graph_K = -1;
+    int xupdate = 0;                 // OPF_SC_XUPDATE_*: small-component local update of plain iterations
+    int graph_xupdate = -1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
@@ -572,6 +667,12 @@ struct opf_scenarios {
 namespace opf {
 
 void scenarios_destroy(opf_scenarios* sc);
+
+void scenarios_set_xupdate(opf_scenarios* sc, int kind) {
+    if (kind != OPF_SC_XUPDATE_CUDA_CORES && kind != OPF_SC_XUPDATE_TENSOR)
+        throw Error(OPF_ERR_INVALID_ARG, "bad x-update kind");
+    sc->xupdate = kind;
+}
 
 namespace {
 
@@ -649,6 +750,7 @@ void build_graph(opf_scenarios* sc, int K) {
         else sc_x_kernel<false><<<v.nctas - v.nctas_s, kScWarps * 32, sc_x_smem(sc->maxn), cs2>>>(v, q);
         cudaEventRecord(ev_x, cs2);
         if (q == K - 1) sc_xs_kernel<true><<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
+        else if (sc->xupdate == OPF_SC_XUPDATE_TENSOR) sc_xs_kernel<false, true><<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
         else sc_xs_kernel<false><<<v.nctas_s, kXsWarps * 32, 0, cs>>>(v, q);
         cudaStreamWaitEvent(cs, ev_x, 0);
     }
@@ -665,6 +767,7 @@ void build_graph(opf_scenarios* sc, int K) {
         throw Error(OPF_ERR_CUDA, std::string("scenario graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ee));
     SC_CUDA(cudaGraphInstantiate(&sc->exec, sc->graph, 0));
     sc->graph_K = K;
+    sc->graph_xupdate = sc->xupdate;
 }
 
 }  // namespace
@@ -916,7 +1019,7 @@ void scenarios_solve(opf_scenarios* sc, const opf_params& prm, cudaStream_t s, o
         sc->cold = false;
     }
     if (prm.max_iter > 0) {
-        if (sc->graph_K != prm.check_every) build_graph(sc, prm.check_every);
+        if (sc->graph_K != prm.check_every || sc->graph_xupdate != sc->xupdate) build_graph(sc, prm.check_every);
         SC_CUDA(cudaGraphLaunch(sc->exec, s));
     }
     sc_objective_kernel<<<S, 256, 0, s>>>(sc->view, S);
@@ -981,7 +1084,10 @@ void scenarios_profile(opf_scenarios* sc, const opf_params& prm, int reps, cudaS
     };
     // q = 0 with K = 2^20: a plain iteration; q = K - 1: a check iteration
     us[0] = timeit([&] { sc_z_kernel<<<zblocks, 256, 0, s>>>(v, 0); });
-    us[1] = timeit([&] { sc_xs_kernel<false><<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, 0); });
+    us[1] = timeit([&] {
+        if (sc->xupdate == OPF_SC_XUPDATE_TENSOR) sc_xs_kernel<false, true><<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, 0);
+        else sc_xs_kernel<false><<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, 0);
+    });
     us[2] = timeit([&] { sc_x_kernel<false><<<v.nctas - v.nctas_s, kScWarps * 32, xsm, s>>>(v, 0); });
     us[3] = timeit([&] {
         sc_xs_kernel<true><<<v.nctas_s, kXsWarps * 32, 0, s>>>(v, (1 << 20) - 1);

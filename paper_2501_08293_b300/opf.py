@@ -25,6 +25,7 @@ CRIT_ABS, CRIT_REL, CRIT_BOTH, CRIT_NEVER = 0, 1, 2, 3
 FP64, FP32 = 0, 1
 RES_PAPER, RES_TEXTBOOK = 0, 1
 DECOMP_FINE, DECOMP_PAPER = 0, 1
+SC_XUPDATE_CUDA_CORES, SC_XUPDATE_TENSOR = 0, 1
 ENGINE_AUTO, ENGINE_GRAPH, ENGINE_HOSTLOOP, ENGINE_PERSISTENT = 0, 1, 2, 3
 
 
@@ -120,6 +121,7 @@ EXPORTS = {
     "opf_scenarios_get_state": (C.c_int32, [_P, C.c_int32, _D, _D, _D, _P]),
     "opf_scenarios_dims": (C.c_int32, [_P, _I, _I, C.POINTER(C.c_int64)]),
     "opf_scenarios_profile": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
+    "opf_scenarios_set_xupdate": (C.c_int32, [_P, C.c_int32]),
     "opf_scenarios_destroy": (None, [_P]),
     "opf_server_config_default": (None, [C.POINTER(ServerConfig)]),
     "opf_server_create": (C.c_int32, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
@@ -493,6 +495,11 @@ class Scenarios:
         _check(lib.opf_scenarios_solve(self._h, C.byref(params), _stream_handle(stream), infos),
                "opf_scenarios_solve")
         return list(infos)
+
+    def set_xupdate(self, kind: int) -> None:
+        """Small shared-operator local update on CUDA cores (bit-identical to
+        single-instance FP32) or on tensor cores (3xTF32)."""
+        _check(lib.opf_scenarios_set_xupdate(self._h, int(kind)), "opf_scenarios_set_xupdate")
 
     def profile(self, params: Params, reps: int = 50, stream=None) -> dict:
         """Per-kernel microseconds of one iteration (opf_scenarios_profile)."""

@@ -119,3 +119,74 @@ def test_scenarios_reject_bad_input(opf):
     with pytest.raises(opf.OpfError):
         sc.state(3)
     sc.close()
+
+
+# Tolerances at t = 200 (derivation as in test_gpu_parity.py: sqrt(t n) u for
+# x and z, t 4 u for the scaled dual).  CUDA cores: FP32, u = 2^-24.  Tensor
+# cores: operands carried as two TF32 parts, about 22 significant bits, so
+# u_eff = 2^-22 (4x) and the bounds are 4x larger.
+TOLS = {0: (1e-5, 5e-5), 1: (4e-5, 2e-4)}
+
+
+@pytest.mark.parametrize("xupdate", [0, 1])
+@pytest.mark.parametrize("name,maker,picks", [("123", lambda: F.feeder_123(1), (0, 5, 63)),
+                                              ("8500", lambda: F.feeder_8500(1), (0, 40))])
+def test_scenarios_match_fp64_oracle(opf, name, maker, picks, xupdate):
+    """Each scenario of the multi-scenario engine (FP32 sweeps; the small
+    shared-operator local update on CUDA cores or on tensor cores in 3xTF32)
+    against the FP64 oracle built from that scenario's loads, at t = 200
+    (rho = 10): x, z and the scaled dual lambda / rho within TOLS."""
+    from oracle import admm as OA, model as OM, precompute as OP
+    f = maker()
+    loads = F.load_scenarios(f, 64, seed=11)
+    sc = opf.Scenarios.from_feeder(f, loads)
+    sc.set_xupdate(xupdate)
+    tol_x, tol_d = TOLS[xupdate]
+    sc.solve(opf.default_params(precision=opf.FP32, rho=10.0, criterion=opf.CRIT_NEVER, max_iter=200, check_every=50))
+    for k in picks:
+        g = f.copy()
+        g.loads = loads[k].copy()
+        m = OM.build_feeder(g)
+        s = OA.ADMM(m, OP.precompute(m), 10.0)
+        for _ in range(200):
+            s.step()
+        xg, xl, lam = sc.state(k)
+        rel = lambda a, b: max(np.linalg.norm(a - b) / np.linalg.norm(b),
+                               np.max(np.abs(a - b) / (np.abs(b) + np.max(np.abs(b)))))
+        d = (lam - s.lam) / 10.0
+        sd = np.max(np.abs(d) / (np.abs(s.lam) / 10.0 + np.max(np.abs(s.lam)) / 10.0 + np.max(np.abs(s.z))))
+        assert rel(xg, s.x) <= tol_x and rel(xl, s.z) <= tol_x and sd <= tol_d, (k, rel(xg, s.x), rel(xl, s.z), sd)
+    sc.close()
+
+
+def test_tensor_core_scenarios_converge(opf):
+    """The tensor-core x-update solves all 64 draws of the 123-bus feeder to
+    ABS 1e-4 (rho = 10), each within 1e-3 relative of the CUDA-core result's
+    objective and in a similar number of iterations; a fixed-length run on
+    the CUDA cores after switching back is bit-identical to a fresh one."""
+    f = F.feeder_123(1)
+    loads = F.load_scenarios(f, 64, seed=3)
+    prm = opf.default_params(precision=opf.FP32, rho=10.0, max_iter=300000, check_every=50)
+    res = {}
+    for kind in (0, 1):
+        sc = opf.Scenarios.from_feeder(f, loads)
+        sc.set_xupdate(kind)
+        res[kind] = sc.solve(prm)
+        sc.close()
+    for a, b in zip(res[0], res[1]):
+        assert a.status == b.status == opf.OK
+        assert abs(a.objective - b.objective) <= 1e-3 * abs(a.objective)
+        assert abs(a.iters - b.iters) <= 0.1 * a.iters + 100
+    sc = opf.Scenarios.from_feeder(f, loads)
+    short = opf.default_params(precision=opf.FP32, rho=10.0, criterion=opf.CRIT_NEVER, max_iter=150, check_every=50)
+    sc.set_xupdate(1)
+    sc.solve(short)
+    sc.set_xupdate(0)
+    sc.solve(short)          # cold start again, CUDA cores
+    x0 = sc.state(7)
+    sc.close()
+    sc = opf.Scenarios.from_feeder(f, loads)
+    sc.solve(short)
+    for x, y in zip(x0, sc.state(7)):
+        assert np.array_equal(x, y)
+    sc.close()
