@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(kXWarps * 32) persistent_kernel(View<T> v) {
 // ----------------------------------------------- persistent, shared-memory
 // Per-launch shared-memory plan (byte offsets; every region 16-byte aligned).
 struct SmemPlan {
-    int P, xs, ls, ws, bb, mt, zs, hcon, hp, hc, us, big, tl, ush, gx, rt, total;
+    int P, xs, ls, ws, bb, mt, zs, hcon, hp, hc, us, big, tl, ush, rt, total;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -720,8 +720,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     // holding u_(i + k) at i (zero for i + k >= 32), so that every lane
     // reads its operands u_(base + c) with 16-byte-aligned vector loads
     T* ush = reinterpret_cast<T*>(sm + sp.ush);
-    int* gx = reinterpret_cast<int*>(sm + sp.gx);       // gathered exchange: device local of each outside copy
-    T* rt = reinterpret_cast<T*>(sm + sp.rt);           // ... and its term of the previous iteration
+    T* rt = reinterpret_cast<T*>(sm + sp.rt);           // gathered exchange: term of each outside copy (aliases usw)
     __shared__ double red[kXWarps][5];
     __shared__ double tot[5];
     __shared__ __align__(8) unsigned long long mbar;
@@ -765,8 +764,10 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
     }
     if (threadIdx.x == 0) hp[nh] = ncp;
     for (int q = threadIdx.x; q < ncp; q += blockDim.x) hc[q] = kGather ? v.hcx[bi.cp0 + q] : v.hci[bi.cp0 + q];
-    if constexpr (kGather)
-        for (int k = threadIdx.x; k < next; k += blockDim.x) gx[k] = v.ext[bi.ext0 + k];
+    // gathered exchange: device local of the thread's first outside copy (in
+    // a register for the whole solve); further slots are read from global
+    const int32_t* gxg = v.ext + bi.ext0;
+    const int gx0 = (kGather && (int)threadIdx.x < next) ? gxg[threadIdx.x] : 0;
     for (int q = threadIdx.x; q < bi.tile1 - bi.tile0; q += blockDim.x) stl[q] = v.tiles[bi.tile0 + q];
     const int hb = bi.halob - bi.halo0;                // interior halo entries [0, hb)
     int ok = 1;
@@ -818,7 +819,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         if (t == 0) return;
         if constexpr (kGather) {
             // the thread's first slot of the gather list
-            if ((int)threadIdx.x < next) Mail<T>::fetch(mb, nlg, (t - 1) & 1, gx[threadIdx.x], raw);
+            if ((int)threadIdx.x < next) Mail<T>::fetch(mb, nlg, (t - 1) & 1, gx0, raw);
         } else {
             const int h = hb1;
             if (h >= nh) return;
@@ -896,12 +897,13 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         const unsigned tag = (unsigned)t;
         for (int k = threadIdx.x; k < next && ok; k += blockDim.x) {
             T w;
+            const int l = (k == (int)threadIdx.x) ? gx0 : gxg[k];
             if (t == 0) {
-                w = copy_term(__ldcg(v.xl + gx[k]), __ldcg(v.lam + gx[k]), inv_rho);
+                w = copy_term(__ldcg(v.xl + l), __ldcg(v.lam + l), inv_rho);
             } else {
                 const bool hit = (k == (int)threadIdx.x) ? Mail<T>::decode(raw, tag, w)
-                                                         : Mail<T>::get(mb, nlg, slot, gx[k], tag, w);
-                if (!hit) ok = mail_poll(mb, nlg, slot, gx[k], tag, w, ctl, tmo, 1);
+                                                         : Mail<T>::get(mb, nlg, slot, l, tag, w);
+                if (!hit) ok = mail_poll(mb, nlg, slot, l, tag, w, ctl, tmo, 1);
             }
             rt[k] = w;
         }
@@ -1184,7 +1186,7 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         if constexpr (kGather) {
             for (int k = threadIdx.x; k < next && okz; k += blockDim.x) {
                 T w;
-                okz = mail_poll(mb, nlg, 0, gx[k], 1u, w, ctl, tmo, 3);
+                okz = mail_poll(mb, nlg, 0, gxg[k], 1u, w, ctl, tmo, 3);
             }
         } else {
             for (int q = threadIdx.x; q < ncp && okz; q += blockDim.x) {
@@ -1662,11 +1664,12 @@ SmemPlan smem_plan_of(const ChunkMax& k) {
     sp.zs = take((size_t)k.halo * w); sp.hcon = take((size_t)k.halo * 4 * w);
     sp.hp = take((size_t)(k.halo + 1) * 4); sp.hc = take((size_t)std::max(1, k.copies) * 4);
     sp.big = k.big;
-    sp.us = take((size_t)kXWarps * k.big * w);
+    // big-tile staging (tile phase) and the gathered outside terms (global
+    // update phase) are never live at the same time: one region
+    sp.us = take(std::max((size_t)kXWarps * k.big * w, (size_t)std::max(1, k.ext) * w));
+    sp.rt = sp.us;
     sp.tl = take((size_t)std::max(1, k.tiles) * sizeof(Tile));
     sp.ush = take(f32 ? (size_t)kXWarps * 4 * kUrow * w : 0);
-    sp.gx = take((size_t)std::max(1, k.ext) * 4);
-    sp.rt = take((size_t)std::max(1, k.ext) * w);
     sp.total = off;
     return sp;
 }
