@@ -233,10 +233,11 @@ def kernel_times(prob, params, stream):
 
 
 # persistent_smem_kernel<float> on the 8500-class feeder (seed 1, default
-# chunking): DRAM traffic per launch from ncu (dram__bytes_read + write)
+# chunking): DRAM traffic per launch from ncu (dram__bytes_read + write) of
+# the current kernel; None until it has been captured
 PROFILED_BLOCKS = 296
-TRAFFIC_STAGING_B = 14_697_000
-TRAFFIC_PER_ITER_B = 41.7
+TRAFFIC_STAGING_B = None
+TRAFFIC_PER_ITER_B = None
 # the multi-scenario sweep (64 draws on the same feeder): DRAM bytes of one
 # plain iteration (global update + both local updates) from one cold-cache
 # ncu capture of the three kernels
@@ -354,7 +355,8 @@ def run_ours(args):
 
     peaks, kind = measured_peaks()
     traffic, traffic_note = None, None
-    if persistent and prec == opf.FP32 and args.seed == 1 and d.n_blocks == PROFILED_BLOCKS:
+    if (persistent and prec == opf.FP32 and args.seed == 1 and d.n_blocks == PROFILED_BLOCKS
+            and TRAFFIC_STAGING_B is not None):
         # DRAM bytes of persistent_smem_kernel<float> on this workload from two
         # ncu captures (2000 and 20000 iterations): one-time staging plus a
         # small per-iteration term, extrapolated to this launch's iterations

@@ -40,12 +40,18 @@
 // same fused multiply-adds), so its iterates are bit-identical to solving
 // that scenario alone in FP32; only the order of the residual sums differs.
 //
-// Why CUDA cores and not tensor cores: per component and iteration the
-// product reads u and writes x for every scenario (8 bytes per element and
-// scenario) against 2 n flops per element, about n/4 flop per byte with
-// n ~ 7 on the 8500-class feeder -- far below the FP32 CUDA-core ridge
-// point, let alone the tensor-core one, and TF32 would need a three-way split
-// to keep FP32 accuracy.  The sweep is bound by memory traffic.
+// Tensor cores (opf_scenarios_set_xupdate): for the small components whose
+// operator is shared by every scenario, the product X = P U over 64
+// scenarios is D (16 scenarios x 8 rows) = U^T P^T per block of 16
+// scenarios on mma.sync m16n8k8 with TF32 inputs, each operand split in two
+// TF32 parts and three products (hi*hi + hi*lo + lo*hi) with FP32
+// accumulation -- about FP32 accuracy, not the same bits.  It runs on the
+// iterations between checks; check iterations and the per-scenario
+// operators keep the CUDA-core path.  Per element and scenario the product
+// reads u and writes x (8 bytes) against 2 n flops, about n/4 flop per byte
+// with n ~ 7: far below either ridge point, so what the tensor-core path can
+// change is the instruction count (no operator broadcast by shuffles) and
+// the latency chain of the GEMV, not the bytes moved.
 #include <cuda_runtime.h>
 
 #include <algorithm>
