@@ -430,7 +430,7 @@ int32_t opf_debug_config(opf_problem* p, int64_t wait_limit_ns, int32_t withhold
             throw opf::Error(OPF_ERR_INVALID_ARG, "wait limit out of [1 us, 600 s]");
         if (withhold_block < -1 || withhold_block >= p->pk.nblocks)
             throw opf::Error(OPF_ERR_INVALID_ARG, "withhold_block out of range");
-        if (persistent_variant < 0 || persistent_variant > 4) throw opf::Error(OPF_ERR_INVALID_ARG, "bad persistent variant");
+        if (persistent_variant < 0 || persistent_variant > 3) throw opf::Error(OPF_ERR_INVALID_ARG, "bad persistent variant");
         p->timeout_ns = (unsigned long long)wait_limit_ns;
         p->skip_block = withhold_block;
         p->force_variant = persistent_variant;

@@ -701,11 +701,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // flight together) into shared memory, then the boundary entries are summed
 // from shared memory; false -- each thread polls the words of its own
 // boundary entries as it sums them.  Same terms, same order, same bits.
-// kIF (with kGather): interior tiles first -- the interior global update,
-// then the interior tiles (they read interior globals only) while the
-// outside terms are in flight, then the boundary globals and the boundary
-// tiles, which publish; the exchange latency overlaps the interior work.
-template <typename T, bool kGather, bool kIF = false>
+template <typename T, bool kGather>
 __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const SmemPlan& sp, unsigned char* sm) {
     T* sP = reinterpret_cast<T*>(sm + sp.P);
     T* xs = reinterpret_cast<T*>(sm + sp.xs);
@@ -1038,42 +1034,25 @@ __device__ __forceinline__ void chunk_smem(const View<T>& v, const int b, const 
         bool okz = true;
         // global update: interior halo entries (copies all in this chunk),
         // then boundary ones (the neighbours' terms of iteration t - 1)
-        if constexpr (kIF) {
-            zinterior();
-            __syncthreads();
-            prefetch(t);                 // outside words in flight during the interior tiles
-            mark(0);
-            xphase(0, ntb, t, false, check, acc);
-            mark(3);
+        prefetch(t);
+        zinterior();
+        mark(0);
+        if constexpr (kGather) {
             gather(t, okz);
             if (!__syncthreads_and(okz)) { flush_prof(); return; }
             zboundary_gathered();
             __syncthreads();
-            mark(1);
-            xphase(ntb, ntl, t, !defer, check, acc);
-            mark(2);
-            __syncthreads();
         } else {
-            prefetch(t);
-            zinterior();
-            mark(0);
-            if constexpr (kGather) {
-                gather(t, okz);
-                if (!__syncthreads_and(okz)) { flush_prof(); return; }
-                zboundary_gathered();
-                __syncthreads();
-            } else {
-                zboundary(t, okz);
-                if (!__syncthreads_and(okz)) { flush_prof(); return; }
-            }
-            mark(1);
-            // local update: boundary tiles first so that their terms reach the
-            // neighbours while the interior tiles are computed
-            xphase(ntb, ntl, t, !defer, check, acc);
-            mark(2);
-            xphase(0, ntb, t, !defer, check, acc);
-            __syncthreads();
+            zboundary(t, okz);
+            if (!__syncthreads_and(okz)) { flush_prof(); return; }
         }
+        mark(1);
+        // local update: boundary tiles first so that their terms reach the
+        // neighbours while the interior tiles are computed
+        xphase(ntb, ntl, t, !defer, check, acc);
+        mark(2);
+        xphase(0, ntb, t, !defer, check, acc);
+        __syncthreads();
         ++t;
         snap = false;
         if (__builtin_expect(check, 0) && !adaptive && t >= 2) {
@@ -1249,13 +1228,13 @@ __device__ __forceinline__ int claim_chunk(int32_t* claim, int nblocks, int per)
     return s_b;
 }
 
-template <typename T, bool kGather, bool kIF = false>
+template <typename T, bool kGather>
 __global__ void __launch_bounds__(kXWarps * 32, 2) persistent_smem_kernel(View<T> v, SmemPlan sp) {
     extern __shared__ __align__(128) unsigned char sm[];
     // nblocks CTAs claim nblocks chunks one each: the scan always finds one
     const int b = claim_chunk(v.flags, v.nblocks, 2);
     if (b < 0) return;
-    chunk_smem<T, kGather, kIF>(v, b, sp, sm);
+    chunk_smem<T, kGather>(v, b, sp, sm);
 }
 
 // ------------------------------------------------------------------ batch
@@ -1740,8 +1719,7 @@ template <typename T>
 int persistent_variant(const opf_problem* p) {
     const size_t sm = (size_t)smem_plan<T>(p).total;
     const bool smem_ok = coop_fits(persistent_smem_kernel<T, true>, sm, p->pk.nblocks) &&
-                         coop_fits(persistent_smem_kernel<T, false>, sm, p->pk.nblocks) &&
-                         coop_fits(persistent_smem_kernel<T, true, true>, sm, p->pk.nblocks);
+                         coop_fits(persistent_smem_kernel<T, false>, sm, p->pk.nblocks);
     if (p->force_variant >= 2) return smem_ok ? p->force_variant : 0;
     if (p->force_variant != 1 && smem_ok) return 2;
     if (coop_fits(persistent_kernel<T>, persistent_smem<T>(p), p->pk.nblocks)) return 1;
@@ -1760,9 +1738,8 @@ void launch_persistent(opf_problem* p, cudaStream_t s) {
         OPF_CUDA(cudaMemsetAsync(p->mbox, 0, (size_t)p->pk.nl * 2 * Mail<T>::kWords * sizeof(unsigned long long), s));
         SmemPlan sp = smem_plan<T>(p);
         void* args[] = {&v, &sp};
-        const void* kern = variant == 2   ? (const void*)persistent_smem_kernel<T, true>
-                           : variant == 3 ? (const void*)persistent_smem_kernel<T, false>
-                                          : (const void*)persistent_smem_kernel<T, true, true>;
+        const void* kern = variant == 2 ? (const void*)persistent_smem_kernel<T, true>
+                                        : (const void*)persistent_smem_kernel<T, false>;
         OPF_CUDA(cudaLaunchCooperativeKernel(kern, dim3(p->pk.nblocks), dim3(kXWarps * 32), args, (size_t)sp.total, s));
     } else if (variant == 1) {
         void* args[] = {&v};
