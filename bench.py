@@ -847,20 +847,27 @@ def run_configs(args):
     from paper_2501_08293_b300 import feeders as F
     from paper_2501_08293_b300 import opf
     lp = golden_lp()
-    runs = [("13-bus", F.feeder_13(1), opf.FP64, 100.0, "13"), ("123-bus", F.feeder_123(1), opf.FP64, 10.0, "123"),
-            ("123-bus", F.feeder_123(1), opf.FP32, 10.0, "123")]
+    # (name, feeder, precision, rho, golden key, residual balancing)
+    runs = [("13-bus", F.feeder_13(1), opf.FP64, 100.0, "13", False),
+            ("123-bus", F.feeder_123(1), opf.FP64, 10.0, "123", False),
+            ("123-bus", F.feeder_123(1), opf.FP32, 10.0, "123", False)]
     for rho in (10.0, 100.0, 1000.0):
-        runs.append(("8500-class (11932 buses)", F.feeder_8500(1), opf.FP32, rho, "8500"))
-    runs.append(("8500-bus literal", F.feeder_8500(1, n_bus=8500), opf.FP32, 10.0, None))
+        runs.append(("8500-class (11932 buses)", F.feeder_8500(1), opf.FP32, rho, "8500", False))
+    # the same rho sweep in FP64 (is a missed 1e-4 the FP32 floor or ADMM?)
+    # and in FP32 with residual balancing (checks every 1000 iterations)
+    for rho in (100.0, 1000.0):
+        runs.append(("8500-class (11932 buses)", F.feeder_8500(1), opf.FP64, rho, "8500", False))
+        runs.append(("8500-class (11932 buses)", F.feeder_8500(1), opf.FP32, rho, "8500", True))
+    runs.append(("8500-bus literal", F.feeder_8500(1, n_bus=8500), opf.FP32, 10.0, None, False))
     if args.configs_quick:
         runs = runs[:3]
     rows = []
     stream = torch.cuda.current_stream()
     with ClockSampler(0) as clk:
-        for name, f, prec, rho, key in runs:
+        for name, f, prec, rho, key, rb in runs:
             p = opf.Problem.from_feeder(f)
-            prm = opf.default_params(rho=rho, precision=prec, check_every=args.check_every,
-                                     max_iter=args.sweep_budget_iters)
+            prm = opf.default_params(rho=rho, precision=prec, check_every=1000 if rb else args.check_every,
+                                     max_iter=args.sweep_budget_iters, adaptive_rho=int(rb))
             p.solve(opf.default_params(rho=rho, precision=prec, check_every=args.check_every, max_iter=1000))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -871,7 +878,9 @@ def run_configs(args):
             sec = e0.elapsed_time(e1) / 1e3
             d = p.dims
             rows.append({"config": name, "n_bus": f.n_bus, "precision": "fp64" if prec == opf.FP64 else "fp32",
-                         "rho": rho, "status": info.status, "iters": info.iters, "seconds": sec,
+                         "rho": rho, "residual_balancing": rb, "rho_final": info.rho,
+                         "first_rel_iter": info.first_rel_iter,
+                         "status": info.status, "iters": info.iters, "seconds": sec,
                          "iters_per_s": info.iters / sec, "us_per_iter": 1e6 * sec / max(1, info.iters),
                          "pres": info.pres, "dres": info.dres, "objective": info.objective,
                          "objective_rel_err_vs_lp": (abs(info.objective - lp[key]) / abs(lp[key])

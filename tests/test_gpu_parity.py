@@ -279,10 +279,13 @@ def test_persistent_matches_graph_engine_8500(opf, prec):
     """Engines and persistent kernels on the 8500-class feeder (hundreds of
     CTAs): every engine runs the same arithmetic (explicit fused
     multiply-adds, same summation orders), so after 500 iterations the
-    iterates and residuals are bit-identical in FP64 and in FP32."""
+    iterates and residuals are bit-identical in FP64 and in FP32 -- the
+    graph engine, the global-memory persistent kernel and the shared-memory
+    one with the gathered (2) and the per-entry (3) boundary exchange."""
     f = F.feeder_8500(1)
     res = []
-    for engine, variant in ((opf.ENGINE_GRAPH, 0), (opf.ENGINE_PERSISTENT, 1), (opf.ENGINE_PERSISTENT, 2)):
+    for engine, variant in ((opf.ENGINE_GRAPH, 0), (opf.ENGINE_PERSISTENT, 1), (opf.ENGINE_PERSISTENT, 2),
+                            (opf.ENGINE_PERSISTENT, 3)):
         p = opf.Problem.from_feeder(f)
         assert p.dims.n_blocks > 100
         p.debug_config(variant=variant)
