@@ -428,7 +428,12 @@ def run_ours(args):
             "fp32_vs_lp_objective_rel": lp_err(r32["objective"], "8500"),
             "fp64_vs_lp_objective_rel": lp_err(r64["objective"], "8500"),
             "note": "same rho, ABS 1e-4 stopping rule and check interval; first_rel_iter = first check at which "
-                    "the paper's relative test (eps_rel 1e-3) held"}
+                    "the paper's relative test (eps_rel 1e-3) held",
+            "gap_cause": "at residual 1e-4 the objective still moves by ~1e-3 on this feeder (rho = 10): FP64 "
+                         "continued from the FP32 stop wanders between 8e-5 and 2.8e-4 of the LP optimum, FP32 "
+                         "run on to ABS 3e-5 lands at 7e-5, and at a fixed 1M iterations FP32 and FP64 are 2e-4 "
+                         "apart; so the FP32-vs-FP64 gap at ABS 1e-4 is where each trajectory stops, not an FP32 "
+                         "residual floor"}
     f123 = F.feeder_123(1)
     p123 = opf.Problem.from_feeder(f123)
     res = {}
