@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--tune-out", default="", help="tune workload: where to write the table (default: the package's)")
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--scenario-iters", type=int, default=1000)
+    ap.add_argument("--scenario-xupdate", default="cuda", choices=["cuda", "tensor"],
+                    help="profile-scenarios: small-component local update on CUDA cores or tensor cores")
     ap.add_argument("--sweep-budget-iters", type=int, default=4_000_000)
     ap.add_argument("--configs-quick", action="store_true", help="configs workload: small feeders only")
     ap.add_argument("--batch", type=int, default=256)
@@ -58,6 +60,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="serve workload: arrivals per second (0 = serve-load x the capacity measured first)")
     ap.add_argument("--serve-workload-max-bus", type=int, default=8500, help="serve workload: largest feeder")
+    ap.add_argument("--serve-max-seconds", type=float, default=1500.0,
+                    help="serve workload: stop submitting after this wall time and drain (reported as truncated)")
     ap.add_argument("--serve-requests-default", type=int, default=100,
                     help="requests of the serving stream in the default bench line")
     ap.add_argument("--no-serve", action="store_true", help="default bench line without the serving stream")
@@ -234,10 +238,11 @@ def kernel_times(prob, params, stream):
 
 # persistent_smem_kernel<float> on the 8500-class feeder (seed 1, default
 # chunking): DRAM traffic per launch from ncu (dram__bytes_read + write) of
-# the current kernel; None until it has been captured
+# the gathered-exchange kernel (captures at 2000 and 20000 iterations:
+# 14,915,328 and 15,353,856 B; profiles/persistent_smem_kernel_8500class_fp32.md)
 PROFILED_BLOCKS = 296
-TRAFFIC_STAGING_B = None
-TRAFFIC_PER_ITER_B = None
+TRAFFIC_STAGING_B = 14_866_600
+TRAFFIC_PER_ITER_B = 24.4
 # the multi-scenario sweep (64 draws on the same feeder): DRAM bytes of one
 # plain iteration (global update + both local updates) from one cold-cache
 # ncu capture of the three kernels
@@ -362,7 +367,7 @@ def run_ours(args):
         # small per-iteration term, extrapolated to this launch's iterations
         traffic = TRAFFIC_STAGING_B + TRAFFIC_PER_ITER_B * (iters / args.steps)
         traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                        "extrapolated from 2000- and 20000-iteration captures")
+                        "extrapolated from 2000- and 20000-iteration captures of the same kernel")
     if persistent:
         # the whole solve is one launch of persistent_kernel: its duration is
         # the event-timed solve; bytes = iterations x bytes per iteration
@@ -574,10 +579,14 @@ def serve_capacity(args, requests: int, max_bus: int) -> dict:
     for f in fs:
         srv.submit(f)
     done = {}
+    last = t0
     while len(done) < requests:
         srv.step()
         for rid, info in srv.poll():
             done[rid] = info
+        if time.perf_counter() - last > 30:
+            last = time.perf_counter()
+            print(f"capacity: {len(done)}/{requests} done after {last - t0:.0f} s", file=sys.stderr, flush=True)
     wall = time.perf_counter() - t0
     srv.close()
     conv = sum(1 for i in done.values() if i.status == opf.OK)
@@ -604,8 +613,21 @@ def serve_stream(args, requests: int, rate: float, max_bus: int | None = None) -
     nxt = 0
     results = {}
     warm_n = 0
-    while len(results) < requests:
+    last = t0
+    limit = getattr(args, "serve_max_seconds", float("inf"))
+    while len(results) < nxt or nxt < requests:
         now = time.perf_counter() - t0
+        if now > limit and nxt < requests:
+            print(f"serve: wall limit {limit:.0f} s reached, {nxt}/{requests} submitted; draining",
+                  file=sys.stderr, flush=True)
+            requests = nxt              # no further arrivals
+            if len(results) >= nxt:
+                break
+        if time.perf_counter() - last > 30:
+            last = time.perf_counter()
+            conv_now = sum(1 for r in results if results[r].status == opf.OK)
+            print(f"serve: t {now:.0f} s, submitted {nxt}, done {len(results)}, converged {conv_now}",
+                  file=sys.stderr, flush=True)
         while nxt < requests and arrivals[nxt] <= now:
             if done_feeders and rng.random() < 0.3:
                 rid0, f0 = done_feeders[int(rng.integers(0, len(done_feeders)))]
@@ -625,6 +647,7 @@ def serve_stream(args, requests: int, rate: float, max_bus: int | None = None) -
             results[rid] = info
             done_feeders.append((rid, kind[rid][1]))
     wall = time.perf_counter() - t0
+    truncated = requests < len(arrivals)
     ok = [r for r in results if results[r].status == opf.OK]
     miss = [r for r in results if results[r].status != opf.OK]
     lat_ok = np.array([results[r].seconds for r in ok]) if ok else np.zeros(1)
@@ -642,6 +665,7 @@ def serve_stream(args, requests: int, rate: float, max_bus: int | None = None) -
                                                {"p50": pct(lat_miss, 50), "p99": pct(lat_miss, 99)})},
             "latency_all_s": {"p50": pct(lat_all, 50), "p99": pct(lat_all, 99)},
             "warm_requests": warm_n, "wall_s": wall, "server": st,
+            "truncated": ({"planned": len(arrivals), "submitted": requests} if truncated else None),
             "workload": f"{requests} requests, Poisson {rate:.3g}/s, n_bus log-uniform [13, {max_bus}], "
                         f"30% topology switches warm-started, ABS 1e-4, budget max({args.serve_budget_iters}, "
                         f"{args.serve_iters_per_bus} x n_bus) iterations"}
@@ -730,6 +754,7 @@ def run_profile_scenarios(args):
     from paper_2501_08293_b300 import opf
     f = F.feeder_8500(args.seed)
     sc = opf.Scenarios.from_feeder(f, F.load_scenarios(f, args.scenarios, seed=args.seed + 100))
+    sc.set_xupdate(opf.SC_XUPDATE_TENSOR if args.scenario_xupdate == "tensor" else opf.SC_XUPDATE_CUDA_CORES)
     kt = sc.profile(opf.default_params(rho=args.rho, precision=opf.FP32, check_every=50), reps=args.profile_scenarios)
     print("profile scenarios", {k: round(v, 2) for k, v in kt.items()})
     sc.close()
