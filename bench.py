@@ -469,9 +469,12 @@ def run_ours(args):
 
 def run_batch(args):
     """256 feeders of uneven size, each with its own switch state and load
-    draw, iterated together (one cooperative launch, or the batched graph
-    engine with --engine graph); one step = batch-iters iterations of every
-    feeder; value = feeder-iterations per second."""
+    draw, iterated together; chunks in proportion to each feeder's size so
+    that all of them fit co-resident.  Both batch engines are timed (one
+    graph-captured cooperative launch, and the batched graph engine); the
+    line's value is the engine OPF_ENGINE_AUTO picks, the other is reported
+    beside it.  One step = batch-iters iterations of every feeder; value =
+    feeder-iterations per second."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
@@ -482,37 +485,36 @@ def run_batch(args):
     rng = np.random.default_rng(args.seed)
     fs = [F.reconfigure(f, rng) for f in F.feeder_batch(args.batch, args.seed)]
     prec = opf.FP64 if args.precision == "fp64" else opf.FP32
-    graph = args.engine in ("graph", "hostloop")
-    if graph:
-        chunks = [0] * len(fs)         # default chunking: no co-residency limit in the graph engine
-    else:
-        # each feeder's chunk count in proportion to its size, all co-resident
-        cap = opf.batch_capacity(prec)
-        tot_bus = sum(f.n_bus for f in fs)
-        spare = max(0, cap - len(fs))
-        chunks = [1 + int(spare * f.n_bus / tot_bus) for f in fs]
+    cap = opf.batch_capacity(prec)
+    tot_bus = sum(f.n_bus for f in fs)
+    spare = max(0, cap - len(fs))
+    chunks = [1 + int(spare * f.n_bus / tot_bus) for f in fs]
     probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, chunks)]
     bt = opf.Batch(probs)
     K = 50
-    eng = opf.ENGINE_GRAPH if graph else opf.ENGINE_PERSISTENT
-    prm = opf.default_params(rho=args.rho, precision=prec, criterion=opf.CRIT_NEVER, max_iter=args.batch_iters,
-                             check_every=K, engine=eng)
-    for _ in range(args.warmup):
-        bt.solve(prm)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    times = []
+    per_engine = {}
     with ClockSampler(0) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            bt.solve(prm)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-    tot = sum(times)
+        for name, eng in (("persistent", opf.ENGINE_PERSISTENT), ("graph", opf.ENGINE_GRAPH)):
+            prm = opf.default_params(rho=args.rho, precision=prec, criterion=opf.CRIT_NEVER,
+                                     max_iter=args.batch_iters, check_every=K, engine=eng)
+            for _ in range(args.warmup):
+                bt.solve(prm)
+            times = []
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bt.solve(prm)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            per_engine[name] = {"seconds": sum(times),
+                                "value": args.steps * args.batch_iters * len(probs) / sum(times)}
+    picked = "graph" if bt.auto_engine(prec) == opf.ENGINE_GRAPH else "persistent"
+    tot = per_engine[picked]["seconds"]
     w = 8 if prec == opf.FP64 else 4
     bytes_iter = sum(w * (7 * p.dims.n_local + 6 * p.dims.n_global) + w * p.dims.sum_n2
                      + 4 * (2 * p.dims.n_local + p.dims.n_global) for p in probs)
@@ -521,14 +523,13 @@ def run_batch(args):
     achieved = bytes_iter * args.steps * args.batch_iters / tot / 1e9
     # to tolerance (capped): solves per second of the whole batch
     tt = opf.default_params(rho=args.rho, precision=prec, max_iter=args.serve_budget_iters, check_every=K,
-                            engine=eng)
+                            engine=opf.ENGINE_AUTO)
     t0 = time.perf_counter()
     infos = bt.solve(tt)
     tsol = time.perf_counter() - t0
     conv = sum(1 for i in infos if i.status == opf.OK)
-    # per step: one init per feeder, flag clear, the iterations, objectives
     bodies = -(-args.batch_iters // K)
-    launches = len(probs) + 2 + (bodies * (2 * K + 2) if graph else 1)
+    launches = len(probs) + 2 + (bodies * (2 * K + 2) if picked == "graph" else 1)
     print(json.dumps({
         "metric": "batched feeder ADMM iterations/s (256 feeders)", "value": iters / tot,
         "unit": "feeder-iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -537,9 +538,10 @@ def run_batch(args):
         "config": {"workload": f"{len(fs)} synthetic feeders, n_bus ~ U[100, 2500], random switch state and loads",
                    "rho": args.rho, "iters_per_step": args.batch_iters, "ctas": sum(p.dims.n_blocks for p in probs),
                    "buses": int(sum(f.n_bus for f in fs)), "l2": "flushed before each step; data > L2",
-                   "engine": "graph" if graph else "persistent"},
-        "roofline": {"kernel": "batched graph engine (all kernels)" if graph else "batch persistent kernel",
-                     "bound": "hbm", "achieved": achieved,
+                   "engine": picked + " (the one OPF_ENGINE_AUTO picks)"},
+        "engines": per_engine,
+        "roofline": {"kernel": "batched graph engine (all kernels)" if picked == "graph" else
+                     "batch persistent kernel", "bound": "hbm", "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "traffic": None, "peak_kind": kind, "bytes_per_batch_iter": bytes_iter},
         "to_tolerance": {"budget_iters": args.serve_budget_iters, "converged": conv, "of": len(infos),

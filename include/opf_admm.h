@@ -472,7 +472,12 @@ void opf_destroy(opf_problem* p);
  *                          check_every iterations, until every instance has
  *                          stopped; any number of chunks; every entry must
  *                          have the same check_every;
- *   OPF_ENGINE_AUTO        persistent when the chunks fit, else graph.
+ *   OPF_ENGINE_AUTO        persistent when the chunks fit co-resident,
+ *                          except when they fit only with their iterate in
+ *                          global memory and the batch's device data is
+ *                          larger than the L2 cache (the operators then
+ *                          stream from HBM, where the graph engine is
+ *                          faster); else graph.
  * All problems must be uploaded on the current device.  The batch borrows
  * the problems (they must outlive it) and owns a small device and
  * pinned-host buffer for the launch descriptors, plus the cached graph.    */
@@ -484,6 +489,9 @@ int32_t opf_batch_create(opf_problem* const* problems, int32_t n, opf_batch** ou
  * infos[i].status) or an error for the whole batch.                       */
 int32_t opf_batch_solve(opf_batch* b, const opf_params* params, int32_t n_params, void* stream, opf_info* infos);
 void opf_batch_destroy(opf_batch* b);
+/* Engine that OPF_ENGINE_AUTO runs for this batch in this precision
+ * (OPF_ENGINE_PERSISTENT or OPF_ENGINE_GRAPH), on the batch's device.      */
+int32_t opf_batch_engine_for(const opf_batch* b, int32_t precision, int32_t* engine);
 /* Chunks (CTAs) that one batch launch can hold co-resident on the current
  * device: the sum of the problems' chunk counts must not exceed it.        */
 int32_t opf_batch_capacity(int32_t precision, int32_t* max_chunks);

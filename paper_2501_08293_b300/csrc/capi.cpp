@@ -28,6 +28,7 @@ void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters,
                                double* per_cta);
 void device_batch_free(opf_batch* B);
 int device_batch_capacity(int precision);
+int device_batch_auto_engine(const opf_batch* B, int precision);
 void residuals_noalloc(const double* v, const double* z, const double* zp, const double* lam, long long n,
                        double rho, double eps_rel, double* out, cudaStream_t s);
 opf_scenarios* scenarios_create(const opf_bus* buses, int nb, const opf_line* lines, int nl, const opf_gen* gens,
@@ -531,6 +532,15 @@ int32_t opf_batch_solve(opf_batch* b, const opf_params* prm, int32_t n_params, v
                 throw opf::Error(OPF_ERR_INVALID_ARG, "residual balancing needs rb_mu > 1 and rb_tau > 1");
         }
         opf::device_batch_solve(b, prm, n_params, (cudaStream_t)stream, infos);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_batch_engine_for(const opf_batch* b, int32_t precision, int32_t* engine) {
+    return guarded([&]() -> int32_t {
+        if (!b || !engine) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (precision != OPF_FP64 && precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
+        *engine = opf::device_batch_auto_engine(b, precision);
         return OPF_OK;
     });
 }

@@ -342,7 +342,11 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 // i.e. D[s][r] = sum_c P[r][c] u_c(s), in three TF32 products (lo*hi +
 // hi*lo + hi*hi, FP32 accumulation), then x = D + bbar, the dual update
 // and the copy term for the next global update.  Columns and rows past n
-// are zero in the padded operator (and u is zero there).
+// are zero in the padded operator (and u is zero there).  Fragment row g of
+// a block holds scenario 2g and row g + 8 scenario 2g + 1, so a lane's two
+// rows are adjacent scenarios: its A operands, its outputs of one matrix row
+// and their z, lambda, bbar, x are float2 pairs (lanes g = 0..7 of one
+// column cover 64 contiguous bytes).
 __device__ __forceinline__ void sc_small_tc(const ScView& v, const ScComp& cd, int gl, int base, int lane, bool keepx,
                                             float rho, float inv_rho) {
     const int n = cd.nf & 0xFFFF, j0 = cd.loc0, Sp = v.Sp;
@@ -357,37 +361,57 @@ __device__ __forceinline__ void sc_small_tc(const ScView& v, const ScComp& cd, i
     const int rr[2] = {2 * t, 2 * t + 1};
     const int gr[2] = {gr0, gr1};
     const bool var_b = (cd.nf & kVarB) != 0;
+    float bsr[2] = {0.f, 0.f};                     // shared bbar of the lane's two rows
+    if (!var_b)
+        for (int h = 0; h < 2; ++h)
+            if (rr[h] < n) bsr[h] = v.bs[cd.boff + rr[h]];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const int sa = base + 16 * m + g, sb = sa + 8;
-        auto uval = [&](bool live, int gc, int c, int sc) -> float {
-            if (!live) return 0.f;
-            return u_of(v.Z[(size_t)gc * Sp + sc], v.L[(size_t)(j0 + c) * Sp + sc], inv_rho);
+        const int sp = base + 16 * m + 2 * g;      // the lane's scenario pair (sp, sp + 1)
+        auto upair = [&](bool live, int gc, int c) -> float2 {
+            if (!live) return make_float2(0.f, 0.f);
+            const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)gc * Sp + sp);
+            const float2 l = *reinterpret_cast<const float2*>(v.L + (size_t)(j0 + c) * Sp + sp);
+            return make_float2(u_of(z.x, l.x, inv_rho), u_of(z.y, l.y, inv_rho));
         };
+        const float2 u0 = upair(c0, gc0, t), u1 = upair(c1, gc1, t + 4);
         uint32_t ah[4], al[4];
-        split_tf32(uval(c0, gc0, t, sa), ah[0], al[0]);
-        split_tf32(uval(c0, gc0, t, sb), ah[1], al[1]);
-        split_tf32(uval(c1, gc1, t + 4, sa), ah[2], al[2]);
-        split_tf32(uval(c1, gc1, t + 4, sb), ah[3], al[3]);
+        split_tf32(u0.x, ah[0], al[0]);            // A[g][t]      (scenario sp,     column t)
+        split_tf32(u0.y, ah[1], al[1]);            // A[g + 8][t]  (scenario sp + 1, column t)
+        split_tf32(u1.x, ah[2], al[2]);            // A[g][t + 4]
+        split_tf32(u1.y, ah[3], al[3]);            // A[g + 8][t + 4]
         float d[4] = {0.f, 0.f, 0.f, 0.f};
         mma_tf32(d, al, bh0, bh1);
         mma_tf32(d, ah, bl0, bl1);
         mma_tf32(d, ah, bh0, bh1);
+        const unsigned act = (v.amask[sp >> 5] >> (sp & 31)) & 3u;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int r = rr[h & 1];
-            const int sc = (h < 2) ? sa : sb;
+        for (int h = 0; h < 2; ++h) {              // matrix row r = 2t + h: (d[h], d[h + 2]) = scenarios (sp, sp + 1)
+            const int r = rr[h];
             if (r >= n) continue;
-            const size_t e = (size_t)(j0 + r) * Sp + sc;
-            const float z = v.Z[(size_t)gr[h & 1] * Sp + sc];
-            const float l = v.L[e];
-            const float bb = var_b ? v.bv[(size_t)(cd.boff + r) * Sp + sc] : v.bs[cd.boff + r];
-            const float xn = d[h] + bb;
-            const float ln = dual_of(l, rho, z, xn);
-            if ((v.amask[sc >> 5] >> (sc & 31)) & 1u) {
-                v.L[e] = ln;
-                v.W[e] = copy_term(xn, ln, inv_rho);
-                if (keepx) v.X[e] = xn;
+            const size_t e = (size_t)(j0 + r) * Sp + sp;
+            const float2 z = *reinterpret_cast<const float2*>(v.Z + (size_t)gr[h] * Sp + sp);
+            const float2 l = *reinterpret_cast<const float2*>(v.L + e);
+            const float2 bb = var_b ? *reinterpret_cast<const float2*>(v.bv + (size_t)(cd.boff + r) * Sp + sp)
+                                    : make_float2(bsr[h], bsr[h]);
+            const float xn0 = d[h] + bb.x, xn1 = d[h + 2] + bb.y;
+            const float ln0 = dual_of(l.x, rho, z.x, xn0), ln1 = dual_of(l.y, rho, z.y, xn1);
+            const float wn0 = copy_term(xn0, ln0, inv_rho), wn1 = copy_term(xn1, ln1, inv_rho);
+            if (act == 3u) {
+                *reinterpret_cast<float2*>(v.L + e) = make_float2(ln0, ln1);
+                *reinterpret_cast<float2*>(v.W + e) = make_float2(wn0, wn1);
+                if (keepx) *reinterpret_cast<float2*>(v.X + e) = make_float2(xn0, xn1);
+            } else {
+                if (act & 1u) {
+                    v.L[e] = ln0;
+                    v.W[e] = wn0;
+                    if (keepx) v.X[e] = xn0;
+                }
+                if (act & 2u) {
+                    v.L[e + 1] = ln1;
+                    v.W[e + 1] = wn1;
+                    if (keepx) v.X[e + 1] = xn1;
+                }
             }
         }
     }

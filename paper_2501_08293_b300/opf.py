@@ -115,6 +115,7 @@ EXPORTS = {
     "opf_batch_solve": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, C.POINTER(Info)]),
     "opf_batch_destroy": (None, [_P]),
     "opf_batch_capacity": (C.c_int32, [C.c_int32, _I]),
+    "opf_batch_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
     "opf_scenarios_create": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32, C.c_int32,
                                          C.POINTER(C.c_void_p)]),
     "opf_scenarios_solve": (C.c_int32, [_P, C.POINTER(Params), _P, C.POINTER(Info)]),
@@ -451,6 +452,12 @@ class Batch:
         infos = (Info * len(self.problems))()
         _check(lib.opf_batch_solve(self._h, arr, len(plist), _stream_handle(stream), infos), "opf_batch_solve")
         return list(infos)
+
+    def auto_engine(self, precision: int = FP32) -> int:
+        """Engine that ENGINE_AUTO runs for this batch (opf_batch_engine_for)."""
+        e = C.c_int32()
+        _check(lib.opf_batch_engine_for(self._h, int(precision), C.byref(e)), "opf_batch_engine_for")
+        return e.value
 
     def close(self):
         if self._h:

@@ -58,6 +58,8 @@ def test_batch_equals_alone(opf, prec, engine):
         p.close()
     probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, chunks)]
     b = opf.Batch(probs)
+    # a small batch: every chunk fits co-resident in shared memory
+    assert b.auto_engine(prec) == opf.ENGINE_PERSISTENT
     infos = b.solve(params)
     for i, (p, info) in enumerate(zip(probs, infos)):
         ia, sa = alone[i]
