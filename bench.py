@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--profile-scenarios", type=int, default=0,
                     help="launch each multi-scenario kernel this many times outside the graph (64 draws on the "
                          "8500-class feeder; the small case for ncu) and exit")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="only run one batch solve of this many iterations (256 feeders, AUTO engine; the small "
+                         "case for ncu captures)")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run one solve of this many iterations (a small case for ncu captures)")
     return ap.parse_args()
@@ -726,6 +729,30 @@ def run_tune(args):
                       "written": args.tune_out or autotune.DEFAULT_PATH}))
 
 
+def run_profile_batch(args):
+    """One fixed-length solve of the 256-feeder batch with the engine AUTO
+    picks (no timing): the small case for ncu captures."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_08293_b300 import build as B
+    B.build()
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+    rng = np.random.default_rng(args.seed)
+    fs = [F.reconfigure(f, rng) for f in F.feeder_batch(args.batch, args.seed)]
+    cap = opf.batch_capacity(opf.FP32)
+    tot_bus = sum(f.n_bus for f in fs)
+    spare = max(0, cap - len(fs))
+    probs = [opf.Problem.from_feeder(f, chunks=1 + int(spare * f.n_bus / tot_bus)) for f in fs]
+    bt = opf.Batch(probs)
+    infos = bt.solve(opf.default_params(rho=args.rho, precision=opf.FP32, criterion=opf.CRIT_NEVER,
+                                        max_iter=args.profile_batch, check_every=50, engine=opf.ENGINE_AUTO))
+    print("profile batch", "graph" if bt.auto_engine(opf.FP32) == opf.ENGINE_GRAPH else "persistent",
+          infos[0].iters, infos[0].pres)
+    bt.close()
+
+
 def run_profile_solve(args):
     """One fixed-length solve of the 8500-class feeder (no timing, no output
     beyond a status line): the small case used for ncu captures."""
@@ -952,6 +979,8 @@ if __name__ == "__main__":
         run_profile_scenarios(a)
     elif a.profile_solve:
         run_profile_solve(a)
+    elif a.profile_batch:
+        run_profile_batch(a)
     elif a.impl == "reference":
         run_reference(a)
     elif a.workload == "batch":
