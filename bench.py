@@ -84,6 +84,12 @@ def parse():
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="only run one batch solve of this many iterations (256 feeders, AUTO engine; the small "
                          "case for ncu captures)")
+    ap.add_argument("--profile-batch-kernels", type=int, default=0,
+                    help="time each batched-graph kernel over this many back-to-back launches outside the "
+                         "while-node graph (256 feeders; the small case for node-level ncu captures) and exit")
+    ap.add_argument("--batch-chunks", choices=("fit", "auto"), default="fit",
+                    help="batch problems' chunks: 'fit' = in proportion to size so that every chunk fits "
+                         "co-resident, 'auto' = each problem's automatic chunking")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="only run one solve of this many iterations (a small case for ncu captures)")
     return ap.parse_args()
@@ -502,21 +508,18 @@ def run_batch(args):
     B.build()
     from paper_2501_08293_b300 import feeders as F
     from paper_2501_08293_b300 import opf
-    rng = np.random.default_rng(args.seed)
-    fs = [F.reconfigure(f, rng) for f in F.feeder_batch(args.batch, args.seed)]
     prec = opf.FP64 if args.precision == "fp64" else opf.FP32
-    cap = opf.batch_capacity(prec)
-    tot_bus = sum(f.n_bus for f in fs)
-    spare = max(0, cap - len(fs))
-    chunks = [1 + int(spare * f.n_bus / tot_bus) for f in fs]
-    probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, chunks)]
+    fs, probs = batch_problems(args, opf, F)
     bt = opf.Batch(probs)
     K = 50
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     per_engine = {}
     with ClockSampler(0) as clk:
-        for name, eng in (("persistent", opf.ENGINE_PERSISTENT), ("graph", opf.ENGINE_GRAPH)):
+        engines = (("persistent", opf.ENGINE_PERSISTENT), ("graph", opf.ENGINE_GRAPH))
+        if args.batch_chunks == "auto":     # more chunks than fit co-resident: graph engine only
+            engines = engines[1:]
+        for name, eng in engines:
             prm = opf.default_params(rho=args.rho, precision=prec, criterion=opf.CRIT_NEVER,
                                      max_iter=args.batch_iters, check_every=K, engine=eng)
             for _ in range(args.warmup):
@@ -557,6 +560,7 @@ def run_batch(args):
         "dtype": "f64" if prec == opf.FP64 else "f32", "data": "synthetic",
         "config": {"workload": f"{len(fs)} synthetic feeders, n_bus ~ U[100, 2500], random switch state and loads",
                    "rho": args.rho, "iters_per_step": args.batch_iters, "ctas": sum(p.dims.n_blocks for p in probs),
+                   "chunks": args.batch_chunks,
                    "buses": int(sum(f.n_bus for f in fs)), "l2": "flushed before each step; data > L2",
                    "engine": picked + " (the one OPF_ENGINE_AUTO picks)"},
         "engines": per_engine,
@@ -746,23 +750,61 @@ def run_tune(args):
                       "written": args.tune_out or autotune.DEFAULT_PATH}))
 
 
+def batch_problems(args, opf, F):
+    """The C4 batch: 256 feeders of uneven size, each with its own switch
+    state and load draw.  Chunks per problem: 'fit' = in proportion to size
+    so that all of them fit co-resident (every engine can run), 'auto' =
+    each problem's automatic chunking (graph engine only)."""
+    import numpy as np
+    rng = np.random.default_rng(args.seed)
+    fs = [F.reconfigure(f, rng) for f in F.feeder_batch(args.batch, args.seed)]
+    if args.batch_chunks == "auto":
+        return fs, [opf.Problem.from_feeder(f) for f in fs]
+    prec = opf.FP64 if args.precision == "fp64" else opf.FP32
+    cap = opf.batch_capacity(prec)
+    tot_bus = sum(f.n_bus for f in fs)
+    spare = max(0, cap - len(fs))
+    return fs, [opf.Problem.from_feeder(f, chunks=1 + int(spare * f.n_bus / tot_bus)) for f in fs]
+
+
+def batch_kernel_bytes(probs, w):
+    """Algorithmic bytes per iteration of the batched graph engine's two
+    kernels (the split of the survey's per-iteration formula): global update
+    reads x and lambda per copy, the copy list, the segment pointers and four
+    per-global constants and writes z; local update reads the operators,
+    bbar, lambda, the previous x, z per global and the gather index and
+    writes x and lambda."""
+    nl = sum(p.dims.n_local for p in probs)
+    ng = sum(p.dims.n_global for p in probs)
+    n2 = sum(p.dims.sum_n2 for p in probs)
+    return {"z": w * (2 * nl + 5 * ng) + 4 * (nl + ng), "x": w * (5 * nl + ng + n2) + 4 * nl}
+
+
 def run_profile_batch(args):
     """One fixed-length solve of the 256-feeder batch with the engine AUTO
-    picks (no timing): the small case for ncu captures."""
-    import numpy as np
+    picks (no timing): the small case for ncu captures.  With
+    --profile-batch-kernels, each kernel of the batched graph body is instead
+    launched back to back outside the while-node graph and timed."""
     import torch
     torch.cuda.set_device(0)
     from paper_2501_08293_b300 import build as B
     B.build()
     from paper_2501_08293_b300 import feeders as F
     from paper_2501_08293_b300 import opf
-    rng = np.random.default_rng(args.seed)
-    fs = [F.reconfigure(f, rng) for f in F.feeder_batch(args.batch, args.seed)]
-    cap = opf.batch_capacity(opf.FP32)
-    tot_bus = sum(f.n_bus for f in fs)
-    spare = max(0, cap - len(fs))
-    probs = [opf.Problem.from_feeder(f, chunks=1 + int(spare * f.n_bus / tot_bus)) for f in fs]
+    fs, probs = batch_problems(args, opf, F)
     bt = opf.Batch(probs)
+    if args.profile_batch_kernels:
+        prec = opf.FP64 if args.precision == "fp64" else opf.FP32
+        prm = opf.default_params(rho=args.rho, precision=prec, check_every=50)
+        us = bt.profile_kernels(prm, reps=args.profile_batch_kernels)
+        kb = batch_kernel_bytes(probs, 8 if prec == opf.FP64 else 4)
+        peaks, kind = measured_peaks()
+        print(json.dumps({"chunks": args.batch_chunks, "ctas": sum(p.dims.n_blocks for p in probs),
+                          "us": us, "bytes": kb,
+                          "frac": {k: kb[k[0]] / (us[k] * 1e3) / peaks["hbm_gbs"] for k in ("z", "x", "x_chunk")},
+                          "peak_gbs": peaks["hbm_gbs"], "peak_kind": kind}))
+        bt.close()
+        return
     prm = opf.default_params(rho=args.rho, precision=opf.FP32, criterion=opf.CRIT_NEVER,
                              max_iter=args.profile_batch, check_every=50, engine=opf.ENGINE_AUTO)
     bt.solve(prm)                           # builds and instantiates the graph
@@ -1002,7 +1044,7 @@ if __name__ == "__main__":
         run_profile_scenarios(a)
     elif a.profile_solve:
         run_profile_solve(a)
-    elif a.profile_batch:
+    elif a.profile_batch or a.profile_batch_kernels:
         run_profile_batch(a)
     elif a.impl == "reference":
         run_reference(a)

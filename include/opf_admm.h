@@ -495,6 +495,19 @@ int32_t opf_batch_engine_for(const opf_batch* b, int32_t precision, int32_t* eng
 /* Chunks (CTAs) that one batch launch can hold co-resident on the current
  * device: the sum of the problems' chunk counts must not exceed it.        */
 int32_t opf_batch_capacity(int32_t precision, int32_t* max_chunks);
+/* Average device duration in microseconds of each kernel of one iteration
+ * of the batched graph engine (the kernels of its while-node body, launched
+ * here `reps` times back to back in a plain CUDA graph timed with CUDA
+ * events on `stream`): us[0] = global update of every instance, us[1] =
+ * local + dual update on the tile-parallel kernel (iterations without
+ * residual partials), us[2] = local update with residual partials on the
+ * chunk kernel (a check iteration), us[3] = the chunk kernel without
+ * partials (for comparison; the body does not run it).  Uses params->rho, params->precision and params->check_every
+ * (params[0] for every instance); each instance's iterate, duals, global
+ * vector and control block are saved before and restored after (scratch
+ * from cudaMallocAsync on `stream`, freed before returning).  The paper has
+ * no counterpart: a measurement hook.                                      */
+int32_t opf_batch_profile_kernels(opf_batch* b, const opf_params* params, int32_t reps, void* stream, double* us);
 
 /* --------------------------------------------------------------- scenarios
  * Many load scenarios on one feeder topology iterated together (FP32

@@ -24,6 +24,7 @@ void device_free(opf_problem* p);
 int device_auto_engine(const opf_problem* p, int precision);
 void device_profile(opf_problem* p, const opf_params& prm, int reps, cudaStream_t s, double* us);
 void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s, opf_info* infos);
+void device_batch_profile(opf_batch* B, const opf_params& prm, int reps, cudaStream_t s, double* us);
 void device_profile_persistent(opf_problem* p, const opf_params& prm, int iters, cudaStream_t s, double* out,
                                double* per_cta);
 void device_batch_free(opf_batch* B);
@@ -532,6 +533,19 @@ int32_t opf_batch_solve(opf_batch* b, const opf_params* prm, int32_t n_params, v
                 throw opf::Error(OPF_ERR_INVALID_ARG, "residual balancing needs rb_mu > 1 and rb_tau > 1");
         }
         opf::device_batch_solve(b, prm, n_params, (cudaStream_t)stream, infos);
+        return OPF_OK;
+    });
+}
+
+int32_t opf_batch_profile_kernels(opf_batch* b, const opf_params* prm, int32_t reps, void* stream, double* us) {
+    return guarded([&]() -> int32_t {
+        if (!b || !prm || !us) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
+        if (reps < 1 || reps > 100000) throw opf::Error(OPF_ERR_INVALID_ARG, "reps out of [1, 100000]");
+        if (!(prm->rho > 0.0) || !std::isfinite(prm->rho)) throw opf::Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
+        if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
+        if (prm->check_every < 1 || prm->check_every > 4096)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "check_every out of [1, 4096]");
+        opf::device_batch_profile(b, *prm, reps, (cudaStream_t)stream, us);
         return OPF_OK;
     });
 }

@@ -30,7 +30,8 @@ struct Ctl {
     int32_t abort;                // a wait gave up: every CTA leaves
     int32_t halt;                 // a check decided to stop (non-blocking checks): CTAs leave
     int32_t skip_block;           // test hook: this CTA withholds its flag (-1: none)
-    int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait, 4 staging, 5 staging copy never landed
+    int32_t timeout_where;        // 1 neighbour wait, 2 check wait, 3 final wait, 4 staging, 5 staging copy never landed,
+                                  // 6 operator block of a tile (batched graph engine)
     int32_t profile_phases;       // persistent kernel: accumulate per-phase time
     int32_t adaptive;             // residual balancing on
     int32_t rho_changes;
@@ -104,7 +105,7 @@ struct opf_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void* g_buf = nullptr;
-    int g_n = 0, g_nz = 0, g_nx = 0, g_K = 0, g_prec = -1;
+    int g_n = 0, g_nz = 0, g_nx = 0, g_K = 0, g_prec = -1, g_ni = 0;
     // persistent engine: the flag clear, the cooperative launch and the
     // finish kernel captured once as a graph, and what it was captured for
     cudaGraph_t pgraph = nullptr;

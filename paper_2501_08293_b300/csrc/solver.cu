@@ -516,6 +516,10 @@ __device__ __forceinline__ int finalize_body(const View<T>& v) {
         tot[4] = l;
     }
     if (threadIdx.x != 0) return 0;
+    if (ctl->abort) {                   // a bounded wait gave up (status and place already recorded)
+        ctl->stop = 1;
+        return 1;
+    }
     const int it = iter + ndone;
     ctl->iter = it;
     int stop = 0;
@@ -1302,6 +1306,255 @@ __global__ void __launch_bounds__(kXWarps * 32) xb_kernel(const View<T>* views, 
     __syncthreads();
     if (sv.ctl->stop) return;
     x_chunk(sv, m.chunk, q);
+}
+
+// ------------------------------------------- batched graph, tile-parallel
+// Local update of the iterations that take no residual partials, with the
+// batch's tiles in work items of kItemTiles consecutive tiles (any warp may
+// run any tile: x and lambda of a tile do not depend on who computes them,
+// and no partial sums are taken), so the grid fills every SM whatever the
+// problems' chunking.  Each warp copies the operator block of its next
+// small tile into its own shared-memory buffer with one bulk copy (TMA,
+// completion on the warp's mbarrier), issued as soon as the current tile's
+// GEMV has read the buffer, so the copy overlaps the next tile's vector
+// loads and gather.
+constexpr int kItemTiles = 8;
+constexpr int kStageBytes = 4096;          // a small FP32 tile's block: 8 column groups x 4 x 32 lanes x 4 B
+
+template <typename T>
+__device__ __forceinline__ unsigned stage_bytes(const Tile& tl) {
+    if (tl.big || tl.L <= 0) return 0;
+    const unsigned b = (unsigned)(((tl.nmax + 3) >> 2) * 4 * tl.L) * (unsigned)sizeof(T);
+    return b <= (unsigned)kStageBytes ? b : 0;
+}
+
+// Lane 0 starts the bulk copy of tile tl's operator block (if it is staged).
+template <typename T>
+__device__ __forceinline__ void stage_issue(const T* P, const Tile& tl, T* buf, unsigned long long* bar, int lane) {
+    const unsigned b = stage_bytes<T>(tl);
+    if (lane == 0 && b) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, b);
+        bulk_g2s(buf, P + tl.mat0, b, bar);
+    }
+}
+
+// Bounded wait for the warp's staged block (phase parity `ph`): false after
+// 0.5 s without completion (the copy is then waited for once more, again
+// bounded, before the caller gives up).
+__device__ __forceinline__ bool stage_wait(unsigned long long* bar, unsigned ph) {
+    for (int round = 0; round < 2; ++round) {
+        const unsigned long long deadline = now_ns() + 500000000ull;
+        unsigned spins = 0;
+        while (!mbar_try_wait(bar, ph)) {
+            if ((++spins & 1023u) == 0 && now_ns() > deadline) break;
+        }
+        if (mbar_try_wait(bar, ph)) return round == 0;
+    }
+    return false;
+}
+
+// One small or big tile's local and dual update without partials (Eq.
+// closed_2, Eq. ADMM-3); y from the staged block when `staged`.
+template <typename T>
+__device__ __forceinline__ void tile_plain(const View<T>* vp, const Tile& tl, int lane, T rho, T inv_rho,
+                                           const T* sbuf, bool staged, T* us) {
+    const T* zg = vp->zg;
+    const int32_t* gidx = vp->gidx;
+    T* xl = vp->xl;
+    T* lam = vp->lam;
+    if (!tl.big) {
+        const int L = tl.L;
+        const bool act = lane < L;
+        const int j = tl.loc0 + lane;
+        int base = 0;
+        T vv = 0, lo = 0, bb = 0, u = 0;
+        if (act) {
+            base = (vp->meta[j] >> 24) & 0x1F;
+            vv = zg[gidx[j]];
+            lo = ldcg(lam + j);
+            bb = vp->bbar[j];
+            u = u_of(vv, lo, inv_rho);
+        }
+        const T y = tile_gemv(staged ? sbuf : vp->P + tl.mat0, L, lane, tl.nmax, base, u, act);
+        if (act) {
+            const T xn = y + bb;
+            xl[j] = xn;
+            lam[j] = dual_of(lo, rho, vv, xn);
+        }
+    } else {
+        const int n = tl.nmax;
+        for (int r = lane; r < n; r += 32) {
+            const int j = tl.loc0 + r;
+            us[r] = u_of(zg[gidx[j]], ldcg(lam + j), inv_rho);
+        }
+        __syncwarp();
+        const T* Pm = vp->P + tl.mat0;
+        for (int r = lane; r < n; r += 32) {
+            T y = 0;
+            for (int c = 0; c < n; ++c) y = fma(Pm[c * n + r], us[c], y);
+            const int j = tl.loc0 + r;
+            const T vv = zg[gidx[j]];
+            const T lo = ldcg(lam + j);
+            const T xn = y + vp->bbar[j];
+            xl[j] = xn;
+            lam[j] = dual_of(lo, rho, vv, xn);
+        }
+        __syncwarp();
+    }
+}
+
+// Tile descriptor held by lane k of the warp, to every lane.
+__device__ __forceinline__ Tile tile_from_lane(const Tile& mine, int k) {
+    Tile t;
+    t.loc0 = __shfl_sync(0xffffffffu, mine.loc0, k);
+    t.mat0 = __shfl_sync(0xffffffffu, mine.mat0, k);
+    const unsigned lm = __shfl_sync(0xffffffffu, (unsigned)(uint16_t)mine.L | ((unsigned)(uint16_t)mine.nmax << 16), k);
+    t.L = (int16_t)(lm & 0xFFFFu);
+    t.nmax = (int16_t)(lm >> 16);
+    t.big = __shfl_sync(0xffffffffu, mine.big, k);
+    return t;
+}
+
+// This lane's vector loads of a small tile (meta -> shuffle base, gather
+// index, dual, bbar); g = -1 for lanes without a local or other tiles.
+template <typename T>
+__device__ __forceinline__ void vec_issue(const Tile& tl, int lane, const int32_t* meta, const int32_t* gidx,
+                                          const T* lam, const T* bbar, int& base, int& g, T& lo, T& bb) {
+    if (!tl.big && lane < tl.L) {
+        const int j = tl.loc0 + lane;
+        base = (meta[j] >> 24) & 0x1F;
+        g = gidx[j];
+        lo = ldcg(lam + j);
+        bb = bbar[j];
+    } else {
+        base = 0; g = -1; lo = 0; bb = 0;
+    }
+}
+
+// Work item of the tile-parallel local update: instance, tiles [t0, t1).
+struct TileItem {
+    int32_t inst, t0, t1, pad;
+};
+
+// Whether instance c's local update at offset q of the body takes residual
+// partials (then the chunk kernel runs it) or has nothing to do.
+__device__ __forceinline__ bool plain_iteration(const Ctl* c, int q) {
+    const int iter = c->iter, maxit = c->max_iter, K = c->K;
+    if (c->stop || iter + q >= maxit) return false;
+    return q != min(K, maxit - iter) - 1;
+}
+__device__ __forceinline__ bool check_iteration(const Ctl* c, int q) {
+    const int iter = c->iter, maxit = c->max_iter, K = c->K;
+    return !c->stop && iter + q < maxit && q == min(K, maxit - iter) - 1;
+}
+
+// Blocks [0, ntl): warps take work items in turn (tile role).  Blocks
+// [ntl, gridDim.x): instances whose check falls on this offset q (their
+// last round ends before the body's) are run chunk by chunk with partials,
+// as the chunk kernel does (check role; normally they find none and leave).
+template <typename T>
+__global__ void __launch_bounds__(kXWarps * 32, 4) xt_kernel(const View<T>* views, const TileItem* items, int nitems,
+                                                         int ntl, int ninst, int q) {
+    extern __shared__ __align__(128) unsigned char xt_smem[];
+    __shared__ unsigned long long bars[kXWarps];
+    __shared__ T us[kXWarps][kMaxBigN];
+    __shared__ View<T> sv;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (blockIdx.x >= ntl) {
+        __shared__ int wl[kXWarps * 32];
+        __shared__ int nwl;
+        for (int i0 = 0; i0 < ninst; i0 += blockDim.x) {
+            if (threadIdx.x == 0) nwl = 0;
+            __syncthreads();
+            const int i = i0 + threadIdx.x;
+            if (i < ninst && check_iteration(views[i].ctl, q)) wl[atomicAdd(&nwl, 1)] = i;
+            __syncthreads();
+            const int n = nwl;
+            for (int k = 0; k < n; ++k) {
+                if (threadIdx.x == 0) sv = views[wl[k]];
+                __syncthreads();
+                for (int b = blockIdx.x - ntl; b < sv.nblocks; b += gridDim.x - ntl) {
+                    x_chunk(sv, b, q);
+                    __syncthreads();
+                }
+                __syncthreads();                            // sv is rewritten next
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    T* buf = reinterpret_cast<T*>(xt_smem + (size_t)warp * kStageBytes);
+    unsigned long long* bar = &bars[warp];
+    if (lane == 0) mbar_init(bar, 1);
+    __syncwarp();
+    unsigned ph = 0;
+    const int nw = ntl * kXWarps;
+    Tile none;
+    none.loc0 = 0; none.mat0 = 0; none.L = 0; none.nmax = 0; none.big = 0;
+    for (int it = blockIdx.x * kXWarps + warp; it < nitems; it += nw) {
+        const TileItem m = items[it];
+        const View<T>* vp = views + m.inst;
+        const Ctl* c = vp->ctl;
+        if (!plain_iteration(c, q)) continue;
+        const T rho = (T)c->rho, inv_rho = (T)c->inv_rho;
+        const T* P = vp->P;
+        const T* zg = vp->zg;
+        const int32_t* gidx = vp->gidx;
+        const int32_t* meta = vp->meta;
+        const T* bbar = vp->bbar;
+        T* xl = vp->xl;
+        T* lam = vp->lam;
+        // the item's tile descriptors, one per lane, passed round by shuffles
+        const int nt = m.t1 - m.t0;
+        Tile mine = none;
+        if (lane < nt) mine = vp->tiles[m.t0 + lane];
+        Tile cur = tile_from_lane(mine, 0);
+        stage_issue<T>(P, cur, buf, bar, lane);
+        // software pipeline: the next tile's vectors load while this tile runs,
+        // and its gathered global value right after
+        int cb, cg;
+        T clo, cbb;
+        vec_issue<T>(cur, lane, meta, gidx, lam, bbar, cb, cg, clo, cbb);
+        T cvv = cg >= 0 ? zg[cg] : (T)0;
+        for (int k = 0; k < nt; ++k) {
+            const Tile nxt = (k + 1 < nt) ? tile_from_lane(mine, k + 1) : none;
+            int nb, gn;
+            T nlo, nbb;
+            vec_issue<T>(nxt, lane, meta, gidx, lam, bbar, nb, gn, nlo, nbb);
+            const bool staged = stage_bytes<T>(cur) != 0;
+            if (!staged) stage_issue<T>(P, nxt, buf, bar, lane);   // the buffer is free
+            if (cur.big) {
+                tile_plain<T>(vp, cur, lane, rho, inv_rho, buf, false, us[warp]);
+            } else if (cur.L > 0) {
+                const bool act = lane < cur.L;
+                const T u = u_of(cvv, clo, inv_rho);
+                if (staged) {
+                    if (!__all_sync(0xffffffffu, stage_wait(bar, ph))) {
+                        if (lane == 0) {
+                            Ctl* cw = vp->ctl;
+                            if (atomicCAS(&cw->abort, 0, 1) == 0) { cw->status = CTL_TIMEOUT; cw->timeout_where = 6; }
+                        }
+                        return;
+                    }
+                    ph ^= 1u;
+                }
+                const T y = tile_gemv(staged ? buf : P + cur.mat0, cur.L, lane, cur.nmax, cb, u, act);
+                if (staged) {
+                    __syncwarp();                           // every lane has read the buffer
+                    stage_issue<T>(P, nxt, buf, bar, lane);
+                }
+                if (act) {
+                    const int j = cur.loc0 + lane;
+                    const T xn = y + cbb;
+                    xl[j] = xn;
+                    lam[j] = dual_of(clo, rho, cvv, xn);
+                }
+            }
+            cvv = gn >= 0 ? zg[gn] : (T)0;
+            cur = nxt; cb = nb; clo = nlo; cbb = nbb;
+        }
+    }
 }
 
 template <typename T>
@@ -2096,9 +2349,30 @@ int32_t status_of(const Ctl& r, const opf_params& prm) {
 // iterations of every instance (global then local update, one launch each
 // over all instances), the per-instance checks, and sets the condition to
 // "some instance still runs".
+// Grid of the tile-parallel kernel: tile-role CTAs up to what is resident
+// on every SM at once (warps then take items in turn), check-role CTAs one
+// per SM at most.
+constexpr size_t kXtSmem = (size_t)kXWarps * kStageBytes;
+struct XtGrid {
+    int ntl, nchk;
+};
 template <typename T>
-GraphEntry build_batch_graph(const View<T>* dviews, const CtaMap* dmap, const ZMap* dzmap, int* drun, int n, int nz,
-                             int nx, int K) {
+XtGrid xt_grid(int nitems, int nctas) {
+    int dev = 0, sms = 0, per = 0;
+    OPF_CUDA(cudaGetDevice(&dev));
+    OPF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    OPF_CUDA(cudaFuncSetAttribute(xt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXtSmem));
+    OPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, xt_kernel<T>, kXWarps * 32, kXtSmem));
+    XtGrid g;
+    g.ntl = std::max(1, std::min((nitems + kXWarps - 1) / kXWarps, std::max(1, per) * sms));
+    g.nchk = std::max(1, std::min(nctas, sms));
+    return g;
+}
+
+template <typename T>
+GraphEntry build_batch_graph(const View<T>* dviews, const CtaMap* dmap, const ZMap* dzmap, const TileItem* ditems,
+                             int* drun, int n, int nz, int nx, int nitems, int K) {
+    const XtGrid xg = xt_grid<T>(nitems, nx);
     GraphEntry g;
     OPF_CUDA(cudaGraphCreate(&g.graph, 0));
     cudaGraphConditionalHandle h;
@@ -2114,9 +2388,14 @@ GraphEntry build_batch_graph(const View<T>* dviews, const CtaMap* dmap, const ZM
     cudaStream_t cs;
     OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     OPF_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    // iterations without partials on the tile-parallel kernel, the body's
+    // last (the check) on the chunk kernel
     for (int q = 0; q < K; ++q) {
         zb_kernel<T><<<nz, kZThreads, 0, cs>>>(dviews, dzmap, q);
-        xb_kernel<T><<<nx, kXWarps * 32, 0, cs>>>(dviews, dmap, q);
+        if (q < K - 1)
+            xt_kernel<T><<<xg.ntl + xg.nchk, kXWarps * 32, kXtSmem, cs>>>(dviews, ditems, nitems, xg.ntl, n, q);
+        else
+            xb_kernel<T><<<nx, kXWarps * 32, 0, cs>>>(dviews, dmap, q);
     }
     finb_kernel<T><<<n, kFinThreads, 0, cs>>>(dviews, drun);
     batch_cond_kernel<<<1, 1, 0, cs>>>(drun, h);
@@ -2165,23 +2444,42 @@ int batch_auto_engine(const opf_batch* B) {
     return OPF_ENGINE_GRAPH;
 }
 
+// Byte offsets of a batch's descriptors in its device buffer and in the
+// pinned staging copy: control read-back, views, CTA map, global-update
+// map, running counter, claim words; 256-byte aligned slices.
+struct BatchOffsets {
+    size_t ctl, views, map, zmap, run, claim, items, bytes;
+};
+template <typename T>
+BatchOffsets batch_offsets(int n, int nctas, int nz, int nitems) {
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    BatchOffsets o;
+    o.ctl = 0;
+    o.views = up((size_t)n * sizeof(Ctl));
+    o.map = o.views + up((size_t)n * sizeof(View<T>));
+    o.zmap = o.map + up((size_t)nctas * sizeof(CtaMap));
+    o.run = o.zmap + up((size_t)std::max(1, nz) * sizeof(ZMap));
+    o.claim = o.run + 256;                                  // zeroed claim words, one per CTA
+    o.items = o.claim + up((size_t)nctas * sizeof(int32_t));
+    o.bytes = o.items + up((size_t)std::max(1, nitems) * sizeof(TileItem));
+    return o;
+}
+
 template <typename T>
 void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s) {
     const int n = (int)B->probs.size();
     const size_t ctl_off = 0;
-    const size_t views_off = ((size_t)n * sizeof(Ctl) + 255) & ~size_t(255);
-    int nctas = 0, nz = 0;
+    const size_t views_off = batch_offsets<T>(n, 0, 0, 0).views;
+    int nctas = 0, nz = 0, nitems = 0;
     ChunkMax cm;
     for (opf_problem* p : B->probs) {
         nctas += p->pk.nblocks;
         nz += (p->pk.ng + kZThreads - 1) / kZThreads;
+        nitems += ((int)p->pk.tiles.size() + kItemTiles - 1) / kItemTiles;
         cm.add(p->pk);
     }
-    const size_t map_off = views_off + (((size_t)n * sizeof(View<T>) + 255) & ~size_t(255));
-    const size_t zmap_off = map_off + (((size_t)nctas * sizeof(CtaMap) + 255) & ~size_t(255));
-    const size_t run_off = zmap_off + (((size_t)std::max(1, nz) * sizeof(ZMap) + 255) & ~size_t(255));
-    const size_t claim_off = run_off + 256;                 // zeroed claim words, one per CTA
-    const size_t bytes = claim_off + (((size_t)nctas * sizeof(int32_t) + 255) & ~size_t(255));
+    const BatchOffsets bo = batch_offsets<T>(n, nctas, nz, nitems);
+    const size_t map_off = bo.map, zmap_off = bo.zmap, run_off = bo.run, claim_off = bo.claim, bytes = bo.bytes;
     if (bytes > B->dev_bytes) {
         if (B->dev_buf) OPF_CUDA(cudaFreeAsync(B->dev_buf, s));
         B->dev_buf = nullptr;
@@ -2233,6 +2531,11 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     }
     *hrun = running;
     std::memset(B->host_buf + claim_off, 0, bytes - claim_off);
+    TileItem* hitems = reinterpret_cast<TileItem*>(B->host_buf + bo.items);
+    for (int i = 0, k = 0; i < n; ++i) {
+        const int nt = (int)B->probs[i]->pk.tiles.size();
+        for (int t0 = 0; t0 < nt; t0 += kItemTiles) hitems[k++] = TileItem{i, t0, std::min(nt, t0 + kItemTiles), 0};
+    }
     for (int i = 0; i < n; ++i)
         OPF_CUDA(cudaMemcpyAsync(B->probs[i]->ctl, hctl + i, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     char* d = static_cast<char*>(B->dev_buf);
@@ -2322,15 +2625,17 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     if (running > 0) {
         const int K = prm[0].check_every;
         if (!B->gexec || B->g_buf != B->dev_buf || B->g_n != n || B->g_nz != nz || B->g_nx != nctas || B->g_K != K ||
-            B->g_prec != prec) {
+            B->g_prec != prec || B->g_ni != nitems) {
             if (B->gexec) cudaGraphExecDestroy(B->gexec);
             if (B->graph) cudaGraphDestroy(B->graph);
             B->gexec = nullptr;
             B->graph = nullptr;
-            GraphEntry ge = build_batch_graph<T>(dviews, dmap, dzmap, drun, n, nz, nctas, K);
+            const TileItem* ditems = reinterpret_cast<const TileItem*>(d + bo.items);
+            GraphEntry ge = build_batch_graph<T>(dviews, dmap, dzmap, ditems, drun, n, nz, nctas, nitems, K);
             B->graph = ge.graph;
             B->gexec = ge.exec;
             B->g_buf = B->dev_buf; B->g_n = n; B->g_nz = nz; B->g_nx = nctas; B->g_K = K; B->g_prec = prec;
+            B->g_ni = nitems;
         }
         OPF_CUDA(cudaGraphLaunch(B->gexec, s));
     }
@@ -2339,6 +2644,123 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     OPF_CUDA(cudaMemcpyAsync(hctl, dctl, (size_t)n * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     OPF_CUDA(cudaEventRecord(B->done, s));
     B->n_launched = n;
+}
+
+// `reps` back-to-back launches of one kernel of the batched graph body
+// (which: 0 global update, 1 tile-parallel local update, 2 chunk local
+// update with partials, 3 chunk local update without) in a plain graph;
+// microseconds per launch.
+template <typename T>
+double time_batch_graph(const View<T>* dv, const CtaMap* dm, const ZMap* dz, const TileItem* di, int n, int nz,
+                        int nx, int ni, int which, int reps, cudaStream_t s) {
+    const XtGrid xg = xt_grid<T>(ni, nx);
+    cudaStream_t cs;
+    OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    OPF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < reps; ++r) {
+        if (which == 0) zb_kernel<T><<<nz, kZThreads, 0, cs>>>(dv, dz, 0);
+        else if (which == 1) xt_kernel<T><<<xg.ntl + xg.nchk, kXWarps * 32, kXtSmem, cs>>>(dv, di, ni, xg.ntl, n, 0);
+        else xb_kernel<T><<<nx, kXWarps * 32, 0, cs>>>(dv, dm, 0);
+    }
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        throw Error(OPF_ERR_CUDA, std::string("batch profile capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ee));
+    }
+    OPF_CUDA(cudaGraphInstantiate(&ge, g, 0));
+    cudaEvent_t e0, e1;
+    OPF_CUDA(cudaEventCreate(&e0));
+    OPF_CUDA(cudaEventCreate(&e1));
+    OPF_CUDA(cudaGraphLaunch(ge, s));            // warm
+    OPF_CUDA(cudaEventRecord(e0, s));
+    OPF_CUDA(cudaGraphLaunch(ge, s));
+    OPF_CUDA(cudaEventRecord(e1, s));
+    OPF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    OPF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    return 1e3 * (double)ms / reps;
+}
+
+template <typename T>
+void batch_profile(opf_batch* B, const opf_params& prm, int reps, cudaStream_t s, double* us) {
+    const int n = (int)B->probs.size();
+    const int prec = sizeof(T) == 8 ? OPF_FP64 : OPF_FP32;
+    const size_t w = sizeof(T);
+    size_t tot = 0;
+    for (opf_problem* p : B->probs) {
+        sync_state_to(p, prec, s);
+        tot += (2 * (size_t)p->pk.nl + (size_t)p->pk.ng) * w;
+    }
+    // save every instance's iterate, duals, global vector and control block
+    char* save = nullptr;
+    OPF_CUDA(cudaMallocAsync((void**)&save, tot + (size_t)n * sizeof(Ctl), s));
+    size_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        opf_problem* p = B->probs[i];
+        const DevPrec& d = prec == OPF_FP64 ? p->d64 : p->d32;
+        const size_t nl = p->pk.nl, ng = p->pk.ng;
+        OPF_CUDA(cudaMemcpyAsync(save + o, d.xl, nl * w, cudaMemcpyDeviceToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync(save + o + nl * w, d.lam, nl * w, cudaMemcpyDeviceToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync(save + o + 2 * nl * w, d.zg, ng * w, cudaMemcpyDeviceToDevice, s));
+        o += (2 * nl + ng) * w;
+        OPF_CUDA(cudaMemcpyAsync(save + tot + (size_t)i * sizeof(Ctl), p->ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
+    }
+    // a graph-engine launch of zero iterations uploads the views and maps
+    opf_params q = prm;
+    q.engine = OPF_ENGINE_GRAPH;
+    q.max_iter = 0;
+    q.warm_start = 1;
+    batch_launch<T>(B, &q, 1, s);
+    OPF_CUDA(cudaEventSynchronize(B->done));
+    int nctas = 0, nz = 0, ni = 0;
+    for (opf_problem* p : B->probs) {
+        nctas += p->pk.nblocks;
+        nz += (p->pk.ng + kZThreads - 1) / kZThreads;
+        ni += ((int)p->pk.tiles.size() + kItemTiles - 1) / kItemTiles;
+    }
+    const BatchOffsets bo = batch_offsets<T>(n, nctas, nz, ni);
+    char* d = static_cast<char*>(B->dev_buf);
+    const View<T>* dv = reinterpret_cast<const View<T>*>(d + bo.views);
+    const CtaMap* dm = reinterpret_cast<const CtaMap*>(d + bo.map);
+    const ZMap* dz = reinterpret_cast<const ZMap*>(d + bo.zmap);
+    const TileItem* di = reinterpret_cast<const TileItem*>(d + bo.items);
+    Ctl* hctl = reinterpret_cast<Ctl*>(B->host_buf + bo.ctl);
+    // control blocks for timing: nothing skipped (huge bound); K = 1 makes
+    // every local-update launch a check iteration (which == 2)
+    for (int which = 0; which < 4; ++which) {
+        for (int i = 0; i < n; ++i) {
+            Ctl& c = hctl[i];
+            c.stop = 0;
+            c.iter = 0;
+            c.max_iter = INT32_MAX;
+            c.rho = prm.rho;
+            c.inv_rho = 1.0 / prm.rho;
+            c.K = (which == 2) ? 1 : (1 << 20);
+            OPF_CUDA(cudaMemcpyAsync(B->probs[i]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        }
+        us[which] = time_batch_graph<T>(dv, dm, dz, di, n, nz, nctas, ni, which, reps, s);
+    }
+    o = 0;
+    for (int i = 0; i < n; ++i) {
+        opf_problem* p = B->probs[i];
+        const DevPrec& dd = prec == OPF_FP64 ? p->d64 : p->d32;
+        const size_t nl = p->pk.nl, ng = p->pk.ng;
+        OPF_CUDA(cudaMemcpyAsync(dd.xl, save + o, nl * w, cudaMemcpyDeviceToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync(dd.lam, save + o + nl * w, nl * w, cudaMemcpyDeviceToDevice, s));
+        OPF_CUDA(cudaMemcpyAsync(dd.zg, save + o + 2 * nl * w, ng * w, cudaMemcpyDeviceToDevice, s));
+        o += (2 * nl + ng) * w;
+        OPF_CUDA(cudaMemcpyAsync(p->ctl, save + tot + (size_t)i * sizeof(Ctl), sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
+    }
+    OPF_CUDA(cudaFreeAsync(save, s));
+    OPF_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace
@@ -2388,6 +2810,12 @@ void device_batch_solve(opf_batch* B, const opf_params* prm, int nprm, cudaStrea
     const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (infos)
         for (size_t i = 0; i < B->probs.size(); ++i) infos[i].seconds = sec;
+}
+
+void device_batch_profile(opf_batch* B, const opf_params& prm, int reps, cudaStream_t s, double* us) {
+    DeviceGuard g(B->device);
+    if (prm.precision == OPF_FP64) batch_profile<double>(B, prm, reps, s, us);
+    else batch_profile<float>(B, prm, reps, s, us);
 }
 
 // Co-resident CTAs a batch launch can use on the current device (the

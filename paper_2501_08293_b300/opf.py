@@ -116,6 +116,7 @@ EXPORTS = {
     "opf_batch_destroy": (None, [_P]),
     "opf_batch_capacity": (C.c_int32, [C.c_int32, _I]),
     "opf_batch_engine_for": (C.c_int32, [_P, C.c_int32, _I]),
+    "opf_batch_profile_kernels": (C.c_int32, [_P, C.POINTER(Params), C.c_int32, _P, _D]),
     "opf_scenarios_create": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32, C.c_int32,
                                          C.POINTER(C.c_void_p)]),
     "opf_scenarios_solve": (C.c_int32, [_P, C.POINTER(Params), _P, C.POINTER(Info)]),
@@ -452,6 +453,14 @@ class Batch:
         infos = (Info * len(self.problems))()
         _check(lib.opf_batch_solve(self._h, arr, len(plist), _stream_handle(stream), infos), "opf_batch_solve")
         return list(infos)
+
+    def profile_kernels(self, params: Params | None = None, reps: int = 20, stream=None) -> dict:
+        """Average microseconds per launch of each batched-graph kernel (CUDA events)."""
+        p = params if params is not None else default_params()
+        us = np.zeros(4)
+        _check(lib.opf_batch_profile_kernels(self._h, C.byref(p), reps, _stream_handle(stream), _dp(us)),
+               "opf_batch_profile_kernels")
+        return dict(z=us[0], x=us[1], x_partials=us[2], x_chunk=us[3])
 
     def auto_engine(self, precision: int = FP32) -> int:
         """Engine that ENGINE_AUTO runs for this batch (opf_batch_engine_for)."""

@@ -122,3 +122,57 @@ def test_batch_graph_engine_many_chunks(opf):
     b.close()
     for p in probs:
         p.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_graph_partial_last_round(opf, prec):
+    """Iteration budgets that are not multiples of the check interval: each
+    instance's last round ends with a check before the body's last offset,
+    so its check iteration runs on the chunk kernel inside the tile-parallel
+    launch (check role) while the other instances take plain iterations.
+    Every instance still equals its solve alone bit for bit."""
+    fs = feeders_mix()
+    chunks = [1, 4, 1, 3, 2, 8]
+    budgets = [137, 263, 50, 411, 99, 321]
+    params = [opf.default_params(rho=10.0, precision=prec, max_iter=m, check_every=50, criterion=opf.CRIT_NEVER,
+                                 engine=opf.ENGINE_GRAPH) for m in budgets]
+    alone = []
+    for f, c, prm in zip(fs, chunks, params):
+        p = opf.Problem.from_feeder(f, chunks=c)
+        info = p.solve(opf.default_params(rho=10.0, precision=prec, max_iter=prm.max_iter, check_every=50,
+                                          criterion=opf.CRIT_NEVER))
+        alone.append((info, p.state()))
+        p.close()
+    probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, chunks)]
+    b = opf.Batch(probs)
+    infos = b.solve(params)
+    for i, (p, info) in enumerate(zip(probs, infos)):
+        ia, sa = alone[i]
+        assert info.iters == ia.iters == budgets[i], i
+        for x, y in zip(p.state(), sa):
+            assert np.array_equal(x, y), (i, rel(x, y))
+        assert info.pres == ia.pres and info.dres == ia.dres, i
+    b.close()
+    for p in probs:
+        p.close()
+
+
+def test_batch_profile_kernels_restores_state(opf):
+    """The kernel-timing hook of the batched graph engine leaves every
+    instance's iterate, duals and global vector as they were, and a solve
+    afterwards continues as if it had not run."""
+    fs = feeders_mix()[:4]
+    probs = [opf.Problem.from_feeder(f, chunks=c) for f, c in zip(fs, [1, 4, 1, 3])]
+    b = opf.Batch(probs)
+    prm = opf.default_params(rho=10.0, precision=opf.FP32, max_iter=120, check_every=50, criterion=opf.CRIT_NEVER,
+                             engine=opf.ENGINE_GRAPH)
+    b.solve(prm)
+    before = [p.state() for p in probs]
+    us = b.profile_kernels(prm, reps=3)
+    assert all(v > 0 for v in us.values()), us
+    for p, sa in zip(probs, before):
+        for x, y in zip(p.state(), sa):
+            assert np.array_equal(x, y)
+    b.close()
+    for p in probs:
+        p.close()
