@@ -1287,15 +1287,80 @@ struct ZMap {
     int32_t inst, g0;
 };
 
+// Globals per thread of the batched global update, and its CTA count for
+// an instance of ng globals.
+constexpr int kZPer = 2;
+inline int zb_blocks(int ng) { return (ng + kZThreads * kZPer - 1) / (kZThreads * kZPer); }
+
+// Eq. (global_sparse) for kZPer globals g[k] of one instance (g[k] < 0:
+// none): the copy lists are read four entries at a time and all their x,
+// lambda loads are in flight together; each sum still adds the copies in
+// list order, so the result is that of global_value.
+template <typename T>
+__device__ __forceinline__ void global_values_batched(const View<T>& v, const int (&g)[kZPer], T inv_rho,
+                                                      T (&out)[kZPer]) {
+    int b[kZPer], e[kZPer];
+    T s[kZPer], lo[kZPer], hi[kZPer], ik[kZPer], ck[kZPer];
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) {
+        b[k] = g[k] >= 0 ? v.gptr[g[k]] : 0;
+        e[k] = g[k] >= 0 ? v.gptr[g[k] + 1] : 0;
+        lo[k] = g[k] >= 0 ? v.lo[g[k]] : (T)0;
+        hi[k] = g[k] >= 0 ? v.hi[g[k]] : (T)0;
+        ik[k] = g[k] >= 0 ? v.invk[g[k]] : (T)0;
+        ck[k] = g[k] >= 0 ? v.cik[g[k]] : (T)0;
+        s[k] = 0;
+    }
+    const T* xr = v.xl;
+    const T* lr = v.lam;
+    for (int j0 = 0;; j0 += 4) {
+        bool more = false;
+        int l[kZPer][4];
+#pragma unroll
+        for (int k = 0; k < kZPer; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool in = b[k] + j0 + r < e[k];
+                l[k][r] = in ? v.gcol[b[k] + j0 + r] : -1;
+                more |= in;
+            }
+        if (!more) break;
+        T xv[kZPer][4], lv[kZPer][4];
+#pragma unroll
+        for (int k = 0; k < kZPer; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                xv[k][r] = l[k][r] >= 0 ? xr[l[k][r]] : (T)0;
+                lv[k][r] = l[k][r] >= 0 ? lr[l[k][r]] : (T)0;
+            }
+#pragma unroll
+        for (int k = 0; k < kZPer; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (l[k][r] >= 0) s[k] += copy_term(xv[k][r], lv[k][r], inv_rho);
+    }
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) out[k] = global_from_sum(s[k], ik[k], ck[k], inv_rho, lo[k], hi[k]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) zb_kernel(const View<T>* views, const ZMap* zmap, int q) {
     const ZMap m = zmap[blockIdx.x];
     const View<T>& v = views[m.inst];
     const Ctl* ctl = v.ctl;
     if (ctl->stop || ctl->iter + q >= ctl->max_iter) return;
-    const int i = m.g0 + threadIdx.x;
-    if (i >= v.ng) return;
-    v.zg[i] = global_value<T, false>(v, i, v.xl, v.lam, (T)ctl->inv_rho);
+    int g[kZPer];
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) {
+        const int i = m.g0 + k * kZThreads + threadIdx.x;
+        g[k] = i < v.ng ? i : -1;
+    }
+    if (g[0] < 0) return;
+    T z[kZPer];
+    global_values_batched<T>(v, g, (T)ctl->inv_rho, z);
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k)
+        if (g[k] >= 0) v.zg[g[k]] = z[k];
 }
 
 template <typename T>
@@ -2474,7 +2539,7 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
     ChunkMax cm;
     for (opf_problem* p : B->probs) {
         nctas += p->pk.nblocks;
-        nz += (p->pk.ng + kZThreads - 1) / kZThreads;
+        nz += zb_blocks(p->pk.ng);
         nitems += ((int)p->pk.tiles.size() + kItemTiles - 1) / kItemTiles;
         cm.add(p->pk);
     }
@@ -2527,7 +2592,7 @@ void batch_launch(opf_batch* B, const opf_params* prm, int nprm, cudaStream_t s)
         else if (engine == OPF_ENGINE_GRAPH) hctl[i].stop = 1;   // nothing to do: skipped by the graph body
         hviews[i] = view_of<T>(p, prec_of<T>(p));
         for (int b = 0; b < p->pk.nblocks; ++b) hmap[c++] = CtaMap{i, b};
-        for (int g0 = 0; g0 < p->pk.ng; g0 += kZThreads) hzmap[cz++] = ZMap{i, g0};
+        for (int g0 = 0; g0 < p->pk.ng; g0 += kZThreads * kZPer) hzmap[cz++] = ZMap{i, g0};
     }
     *hrun = running;
     std::memset(B->host_buf + claim_off, 0, bytes - claim_off);
@@ -2723,7 +2788,7 @@ void batch_profile(opf_batch* B, const opf_params& prm, int reps, cudaStream_t s
     int nctas = 0, nz = 0, ni = 0;
     for (opf_problem* p : B->probs) {
         nctas += p->pk.nblocks;
-        nz += (p->pk.ng + kZThreads - 1) / kZThreads;
+        nz += zb_blocks(p->pk.ng);
         ni += ((int)p->pk.tiles.size() + kItemTiles - 1) / kItemTiles;
     }
     const BatchOffsets bo = batch_offsets<T>(n, nctas, nz, ni);
