@@ -1514,39 +1514,46 @@ __device__ __forceinline__ bool check_iteration(const Ctl* c, int q) {
     return !c->stop && iter + q < maxit && q == min(K, maxit - iter) - 1;
 }
 
+// Check role of the tile-parallel kernel (kept out of line so that its
+// registers do not constrain the tile role's).
+template <typename T>
+__device__ __noinline__ void xt_check_role(const View<T>* views, int ninst, int ntl, int q) {
+    __shared__ View<T> sv;
+    __shared__ int wl[kXWarps * 32];
+    __shared__ int nwl;
+    for (int i0 = 0; i0 < ninst; i0 += blockDim.x) {
+        if (threadIdx.x == 0) nwl = 0;
+        __syncthreads();
+        const int i = i0 + threadIdx.x;
+        if (i < ninst && check_iteration(views[i].ctl, q)) wl[atomicAdd(&nwl, 1)] = i;
+        __syncthreads();
+        const int n = nwl;
+        for (int k = 0; k < n; ++k) {
+            if (threadIdx.x == 0) sv = views[wl[k]];
+            __syncthreads();
+            for (int b = blockIdx.x - ntl; b < sv.nblocks; b += gridDim.x - ntl) {
+                x_chunk(sv, b, q);
+                __syncthreads();
+            }
+            __syncthreads();                            // sv is rewritten next
+        }
+        __syncthreads();
+    }
+}
+
 // Blocks [0, ntl): warps take work items in turn (tile role).  Blocks
 // [ntl, gridDim.x): instances whose check falls on this offset q (their
 // last round ends before the body's) are run chunk by chunk with partials,
 // as the chunk kernel does (check role; normally they find none and leave).
 template <typename T>
-__global__ void __launch_bounds__(kXWarps * 32, 4) xt_kernel(const View<T>* views, const TileItem* items, int nitems,
-                                                         int ntl, int ninst, int q) {
+__global__ void __launch_bounds__(kXWarps * 32, sizeof(T) == 4 ? 4 : 3)
+    xt_kernel(const View<T>* views, const TileItem* items, int nitems, int ntl, int ninst, int q) {
     extern __shared__ __align__(128) unsigned char xt_smem[];
     __shared__ unsigned long long bars[kXWarps];
     __shared__ T us[kXWarps][kMaxBigN];
-    __shared__ View<T> sv;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (blockIdx.x >= ntl) {
-        __shared__ int wl[kXWarps * 32];
-        __shared__ int nwl;
-        for (int i0 = 0; i0 < ninst; i0 += blockDim.x) {
-            if (threadIdx.x == 0) nwl = 0;
-            __syncthreads();
-            const int i = i0 + threadIdx.x;
-            if (i < ninst && check_iteration(views[i].ctl, q)) wl[atomicAdd(&nwl, 1)] = i;
-            __syncthreads();
-            const int n = nwl;
-            for (int k = 0; k < n; ++k) {
-                if (threadIdx.x == 0) sv = views[wl[k]];
-                __syncthreads();
-                for (int b = blockIdx.x - ntl; b < sv.nblocks; b += gridDim.x - ntl) {
-                    x_chunk(sv, b, q);
-                    __syncthreads();
-                }
-                __syncthreads();                            // sv is rewritten next
-            }
-            __syncthreads();
-        }
+        xt_check_role<T>(views, ninst, ntl, q);
         return;
     }
     T* buf = reinterpret_cast<T*>(xt_smem + (size_t)warp * kStageBytes);
