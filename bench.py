@@ -76,6 +76,9 @@ def parse():
                     help="serving: a request's iteration budget is max(serve-budget-iters, this x n_bus)")
     ap.add_argument("--serve-capacity-requests", type=int, default=120,
                     help="serve workload with --rate 0: cold requests submitted at once to measure capacity")
+    ap.add_argument("--serve-sweep", type=str, default="",
+                    help="serve workload: comma-separated offered loads (fractions of the measured capacity), "
+                         "one stream of --requests each after one capacity measurement, e.g. 0.5,0.8,1.2")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="serve workload with --rate 0: offered load as a fraction of the measured capacity")
     ap.add_argument("--profile-scenarios", type=int, default=0,
@@ -709,11 +712,29 @@ def run_serve(args):
     B.build()
     cap = None
     rate = args.serve_rate
-    if rate <= 0:
+    if rate <= 0 or args.serve_sweep:
         cap = serve_capacity(args, args.serve_capacity_requests, args.serve_workload_max_bus)
         rate = args.serve_load * cap["solves_per_s"]
-    with ClockSampler(0) as clk:
-        r = serve_stream(args, args.requests, rate, args.serve_workload_max_bus)
+    sweep = None
+    if args.serve_sweep:
+        # one stream per offered load; the line's value is the stream at
+        # --serve-load when it is among them, else the first
+        loads = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
+        sweep, main = [], None
+        with ClockSampler(0) as clk:
+            for ld in loads:
+                rs = serve_stream(args, args.requests, ld * cap["solves_per_s"], args.serve_workload_max_bus)
+                sweep.append({"offered_load": ld, "rate_per_s": rs["rate_per_s"],
+                              "converged_solves_per_s": rs["converged_solves_per_s"],
+                              "converged_frac": rs["converged_frac"], "latency_s": rs["latency_s"],
+                              "budget_exhausted": rs["budget_exhausted"]["count"], "wall_s": rs["wall_s"],
+                              "warm_requests": rs["warm_requests"], "truncated": rs["truncated"]})
+                if main is None or ld == args.serve_load:
+                    main = rs
+        r = main
+    else:
+        with ClockSampler(0) as clk:
+            r = serve_stream(args, args.requests, rate, args.serve_workload_max_bus)
     print(json.dumps({
         "metric": "served OPF solves/s at ABS 1e-4 (continuous batching)", "value": r["converged_solves_per_s"],
         "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
@@ -722,7 +743,7 @@ def run_serve(args):
         "latency_s": r["latency_s"], "converged": r["converged"], "converged_frac": r["converged_frac"],
         "budget_exhausted": r["budget_exhausted"], "all_requests": {"solves_per_s": r["solves_per_s"],
                                                                     "latency_s": r["latency_all_s"]},
-        "capacity": cap, "offered_load": (None if cap is None else args.serve_load),
+        "capacity": cap, "offered_load": (None if cap is None else args.serve_load), "sweep": sweep,
         "warm_requests": r["warm_requests"], "wall_s": r["wall_s"], "server": r["server"],
         "clocks": clk.summary(),
     }))

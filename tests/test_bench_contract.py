@@ -54,3 +54,26 @@ def test_no_cpu_fallback_without_a_gpu():
     r = _run_bench(["--steps", "1", "--warmup", "0", "--no-cpu-baseline", "--no-serve"], timeout=600)
     assert r.returncode != 0
     assert not any(ln.strip().startswith("{") for ln in r.stdout.splitlines())
+
+
+def test_batch_kernel_bytes_split_the_survey_formula():
+    """The per-kernel byte counts of the batched graph engine add up to the
+    per-iteration formula the batch line's roofline uses (host-only
+    problems, no device needed)."""
+    import importlib.util
+    from paper_2501_08293_b300 import feeders as F
+    from paper_2501_08293_b300 import opf
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    probs = [opf.Problem.from_feeder(f, upload=False) for f in (F.feeder_13(1), F.feeder_123(2), F.feeder_tiny(5, 1))]
+    try:
+        for w in (4, 8):
+            kb = bench.batch_kernel_bytes(probs, w)
+            total = sum(w * (7 * p.dims.n_local + 6 * p.dims.n_global) + w * p.dims.sum_n2
+                        + 4 * (2 * p.dims.n_local + p.dims.n_global) for p in probs)
+            assert kb["z"] + kb["x"] == total
+            assert kb["z"] > 0 and kb["x"] > kb["z"]
+    finally:
+        for p in probs:
+            p.close()
