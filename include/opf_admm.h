@@ -353,8 +353,10 @@ int32_t opf_get_solution(const opf_problem* p, double* w, double* pg, double* qg
 /* Average device duration in microseconds of each kernel of an iteration,
  * as launched inside the solve graph: for each kernel a CUDA graph of
  * `reps` back-to-back launches is timed with CUDA events on `stream`.
- * us[0] = global update, us[1] = local update + dual update, us[2] = local
- * update with residual partials, us[3] = residual finalize.  Uses
+ * us[0] = global update, us[1] = local update + dual update (the
+ * tile-parallel kernel the graph runs on iterations without residual
+ * partials), us[2] = local update with residual partials (the chunk kernel
+ * of a check iteration), us[3] = residual finalize.  Uses
  * params->rho and params->precision; the iterate, duals and iteration
  * counter are saved before and restored after (scratch is allocated with
  * cudaMallocAsync on `stream` and freed before returning).                 */

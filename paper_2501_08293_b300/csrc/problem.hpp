@@ -154,6 +154,11 @@ struct opf_problem {
     double* partials = nullptr;
     double* tdz = nullptr;
     double* tpart = nullptr;
+    // graph engine's tile-parallel local update: the problem's View in both
+    // precisions (device copies) and its work items of tiles
+    void* xt_views = nullptr;
+    void* xt_items = nullptr;
+    int xt_nitems = 0;
     unsigned long long* phase = nullptr;
     unsigned long long* mbox = nullptr;
     opf::Ctl* ctl = nullptr;

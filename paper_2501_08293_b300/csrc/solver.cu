@@ -1373,9 +1373,10 @@ __global__ void __launch_bounds__(kXWarps * 32) xb_kernel(const View<T>* views, 
     x_chunk(sv, m.chunk, q);
 }
 
-// ------------------------------------------- batched graph, tile-parallel
-// Local update of the iterations that take no residual partials, with the
-// batch's tiles in work items of kItemTiles consecutive tiles (any warp may
+// ---------------------------------------------- graph engines, tile-parallel
+// Local update of the iterations that take no residual partials (graph and
+// host-loop engines, one problem or a batch), with the tiles of every
+// instance in work items of kItemTiles consecutive tiles (any warp may
 // run any tile: x and lambda of a tile do not depend on who computes them,
 // and no partial sums are taken), so the grid fills every SM whatever the
 // problems' chunking.  Each warp copies the operator block of its next
@@ -1629,6 +1630,26 @@ __global__ void __launch_bounds__(kXWarps * 32, sizeof(T) == 4 ? 4 : 3)
     }
 }
 
+// Grid of the tile-parallel kernel: tile-role CTAs up to what is resident
+// on every SM at once (warps then take items in turn), check-role CTAs one
+// per SM at most.
+constexpr size_t kXtSmem = (size_t)kXWarps * kStageBytes;
+struct XtGrid {
+    int ntl, nchk;
+};
+template <typename T>
+XtGrid xt_grid(int nitems, int nctas) {
+    int dev = 0, sms = 0, per = 0;
+    OPF_CUDA(cudaGetDevice(&dev));
+    OPF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    OPF_CUDA(cudaFuncSetAttribute(xt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXtSmem));
+    OPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, xt_kernel<T>, kXWarps * 32, kXtSmem));
+    XtGrid g;
+    g.ntl = std::max(1, std::min((nitems + kXWarps - 1) / kXWarps, std::max(1, per) * sms));
+    g.nchk = std::max(1, std::min(nctas, sms));
+    return g;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFinThreads) finb_kernel(const View<T>* views, int* running) {
     const View<T>& v = views[blockIdx.x];
@@ -1832,7 +1853,7 @@ struct Arena {
 struct Layout {
     size_t lo, hi, invk, cik, zg, lo32, hi32, invk32, cik32, zg32;
     size_t gptr, gcol, gidx, meta, tiles, blocks, halo_gid, halo_own, nbrs, hcp, hci, flags, cost, partials, phase, ctl, mbox;
-    size_t tdz, tpart, hcx, ext;
+    size_t tdz, tpart, hcx, ext, xtv, xti;
     size_t xl, lam, xl2, lam2, bbar, xl0, xl32, lam32, xl2_32, lam2_32, bbar32, xl0_32, P64, P32;
     size_t total;
 };
@@ -1859,6 +1880,8 @@ Layout layout_of(const opf_problem* p) {
     L.mbox = a.take<unsigned long long>((size_t)k.nl * 4);     // 2 slots x 2 words (f64)
     L.tdz = a.take<double>(std::max(1, k.nl));
     L.tpart = a.take<double>((size_t)2 * ((k.ng + kZThreads - 1) / kZThreads + 1));
+    L.xtv = a.take<View<double>>(2);
+    L.xti = a.take<TileItem>(std::max<size_t>(1, (k.tiles.size() + kItemTiles - 1) / kItemTiles));
     L.xl = a.take<double>(k.nl); L.lam = a.take<double>(k.nl); L.xl2 = a.take<double>(k.nl); L.lam2 = a.take<double>(k.nl);
     L.bbar = a.take<double>(k.nl); L.xl0 = a.take<double>(k.nl);
     L.xl32 = a.take<float>(k.nl); L.lam32 = a.take<float>(k.nl); L.xl2_32 = a.take<float>(k.nl); L.lam2_32 = a.take<float>(k.nl);
@@ -1908,13 +1931,33 @@ void enqueue_init(opf_problem* p, cudaStream_t s) {
     OPF_CUDA(cudaGetLastError());
 }
 
+// The problem's View on the device (slot 0 FP32, slot 1 FP64), as the
+// tile-parallel kernel reads it.
 template <typename T>
-void enqueue_iterations(opf_problem* p, int K, int form, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+const View<T>* device_view(const opf_problem* p) {
+    return reinterpret_cast<const View<T>*>(static_cast<const char*>(p->xt_views) +
+                                            (sizeof(T) == 8 ? sizeof(View<double>) : 0));
+}
+
+// One graph body (or host-loop round) of K iterations: the global update,
+// then the local update -- tile-parallel on the positions without residual
+// partials, the chunk kernel on the last (the check) -- and the finalize.
+// xg: the tile kernel's grid (computed here when null; a caller that
+// captures the body computes it before the capture begins).
+template <typename T>
+void enqueue_iterations(opf_problem* p, int K, int form, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
+                        const XtGrid* xg = nullptr) {
     View<T> v = view_of<T>(p, prec_of<T>(p));
     const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
+    const XtGrid g = xg ? *xg : xt_grid<T>(p->xt_nitems, p->pk.nblocks);
+    const View<T>* dv = device_view<T>(p);
+    const TileItem* di = static_cast<const TileItem*>(p->xt_items);
     for (int q = 0; q < K; ++q) {
         z_kernel<T><<<zb, kZThreads, 0, s>>>(v, q);
-        x_kernel<T><<<p->pk.nblocks, kXWarps * 32, 0, s>>>(v, q);
+        if (q < K - 1)
+            xt_kernel<T><<<g.ntl + g.nchk, kXWarps * 32, kXtSmem, s>>>(dv, di, p->xt_nitems, g.ntl, 1, q);
+        else
+            x_kernel<T><<<p->pk.nblocks, kXWarps * 32, 0, s>>>(v, q);
     }
     if (form == OPF_RES_TEXTBOOK) textbook_kernel<T><<<zb, kZThreads, 0, s>>>(v);
     finalize_kernel<T><<<1, kFinThreads, 0, s>>>(v, h, use_cond);
@@ -1939,11 +1982,12 @@ GraphEntry& get_graph(opf_problem* p, int K, int form) {
     cudaGraphNode_t cnode;
     OPF_CUDA(cudaGraphAddNode(&cnode, g.graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const XtGrid xg = xt_grid<T>(p->xt_nitems, p->pk.nblocks);
     cudaStream_t cs;
     OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     OPF_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     try {
-        enqueue_iterations<T>(p, K, form, cs, h, 1);
+        enqueue_iterations<T>(p, K, form, cs, h, 1, &xg);
     } catch (...) {
         cudaGraph_t tmp;
         cudaStreamEndCapture(cs, &tmp);
@@ -2135,6 +2179,7 @@ template <typename T>
 double time_graph(opf_problem* p, int which, int reps, cudaStream_t s) {
     View<T> v = view_of<T>(p, prec_of<T>(p));
     const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
+    const XtGrid xg = xt_grid<T>(p->xt_nitems, p->pk.nblocks);
     cudaStream_t cs;
     OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
@@ -2142,7 +2187,10 @@ double time_graph(opf_problem* p, int which, int reps, cudaStream_t s) {
     OPF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < reps; ++r) {
         if (which == 0) z_kernel<T><<<zb, kZThreads, 0, cs>>>(v, 0);
-        else if (which <= 2) x_kernel<T><<<p->pk.nblocks, kXWarps * 32, 0, cs>>>(v, 0);
+        else if (which == 1)
+            xt_kernel<T><<<xg.ntl + xg.nchk, kXWarps * 32, kXtSmem, cs>>>(
+                device_view<T>(p), static_cast<const TileItem*>(p->xt_items), p->xt_nitems, xg.ntl, 1, 0);
+        else if (which == 2) x_kernel<T><<<p->pk.nblocks, kXWarps * 32, 0, cs>>>(v, 0);
         else finalize_kernel<T><<<1, kFinThreads, 0, cs>>>(v, 0, 0);
     }
     OPF_CUDA(cudaStreamEndCapture(cs, &g));
@@ -2210,6 +2258,9 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     p->mbox = (unsigned long long*)(a + L.mbox);
     p->tdz = (double*)(a + L.tdz);
     p->tpart = (double*)(a + L.tpart);
+    p->xt_views = a + L.xtv;
+    p->xt_items = a + L.xti;
+    p->xt_nitems = (int)((k.tiles.size() + kItemTiles - 1) / kItemTiles);
     p->ctl = (Ctl*)(a + L.ctl);
     if (!p->ctl_host) OPF_CUDA(cudaMallocHost((void**)&p->ctl_host, sizeof(Ctl)));
     std::memset(p->ctl_host, 0, sizeof(Ctl));
@@ -2249,6 +2300,16 @@ void device_upload(opf_problem* p, void* arena, size_t bytes, cudaStream_t s) {
     OPF_CUDA(cudaMemsetAsync(p->partials, 0, (size_t)k.nblocks * 16 * sizeof(double), s));
     OPF_CUDA(cudaMemsetAsync(p->flags, 0, (size_t)k.nblocks * sizeof(int32_t), s));
     OPF_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(Ctl), s));
+    // the graph engine's tile-parallel kernel reads the View from the device
+    static_assert(sizeof(View<float>) == sizeof(View<double>), "view slots");
+    const View<double> vd = view_of<double>(p, p->d64);
+    const View<float> vf = view_of<float>(p, p->d32);
+    std::vector<TileItem> items;
+    for (int t0 = 0; t0 < (int)k.tiles.size(); t0 += kItemTiles)
+        items.push_back(TileItem{0, t0, std::min((int)k.tiles.size(), t0 + kItemTiles), 0});
+    h2d(p->xt_views, &vf, sizeof(vf));
+    h2d((char*)p->xt_views + sizeof(View<double>), &vd, sizeof(vd));
+    h2d(p->xt_items, items.data(), items.size() * sizeof(TileItem));
     enqueue_init<double>(p, s);
     enqueue_init<float>(p, s);
     OPF_CUDA(cudaStreamSynchronize(s));
@@ -2421,26 +2482,6 @@ int32_t status_of(const Ctl& r, const opf_params& prm) {
 // iterations of every instance (global then local update, one launch each
 // over all instances), the per-instance checks, and sets the condition to
 // "some instance still runs".
-// Grid of the tile-parallel kernel: tile-role CTAs up to what is resident
-// on every SM at once (warps then take items in turn), check-role CTAs one
-// per SM at most.
-constexpr size_t kXtSmem = (size_t)kXWarps * kStageBytes;
-struct XtGrid {
-    int ntl, nchk;
-};
-template <typename T>
-XtGrid xt_grid(int nitems, int nctas) {
-    int dev = 0, sms = 0, per = 0;
-    OPF_CUDA(cudaGetDevice(&dev));
-    OPF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    OPF_CUDA(cudaFuncSetAttribute(xt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXtSmem));
-    OPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, xt_kernel<T>, kXWarps * 32, kXtSmem));
-    XtGrid g;
-    g.ntl = std::max(1, std::min((nitems + kXWarps - 1) / kXWarps, std::max(1, per) * sms));
-    g.nchk = std::max(1, std::min(nctas, sms));
-    return g;
-}
-
 template <typename T>
 GraphEntry build_batch_graph(const View<T>* dviews, const CtaMap* dmap, const ZMap* dzmap, const TileItem* ditems,
                              int* drun, int n, int nz, int nx, int nitems, int K) {
