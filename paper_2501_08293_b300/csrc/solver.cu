@@ -418,13 +418,78 @@ __device__ __forceinline__ int decide(Ctl* ctl, const double* s, int it) {
 }
 
 // ----------------------------------------------------- graph / hostloop
+// Globals per thread of the graph engines' global update, and its CTA
+// count for an instance of ng globals.
+constexpr int kZPer = 2;
+inline int zb_blocks(int ng) { return (ng + kZThreads * kZPer - 1) / (kZThreads * kZPer); }
+
+// Eq. (global_sparse) for kZPer globals g[k] of one instance (g[k] < 0:
+// none): the copy lists are read four entries at a time and all their x,
+// lambda loads are in flight together; each sum still adds the copies in
+// list order, so the result is that of global_value.
+template <typename T>
+__device__ __forceinline__ void global_values_batched(const View<T>& v, const int (&g)[kZPer], T inv_rho,
+                                                      T (&out)[kZPer]) {
+    int b[kZPer], e[kZPer];
+    T s[kZPer], lo[kZPer], hi[kZPer], ik[kZPer], ck[kZPer];
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) {
+        b[k] = g[k] >= 0 ? v.gptr[g[k]] : 0;
+        e[k] = g[k] >= 0 ? v.gptr[g[k] + 1] : 0;
+        lo[k] = g[k] >= 0 ? v.lo[g[k]] : (T)0;
+        hi[k] = g[k] >= 0 ? v.hi[g[k]] : (T)0;
+        ik[k] = g[k] >= 0 ? v.invk[g[k]] : (T)0;
+        ck[k] = g[k] >= 0 ? v.cik[g[k]] : (T)0;
+        s[k] = 0;
+    }
+    const T* xr = v.xl;
+    const T* lr = v.lam;
+    for (int j0 = 0;; j0 += 4) {
+        bool more = false;
+        int l[kZPer][4];
+#pragma unroll
+        for (int k = 0; k < kZPer; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool in = b[k] + j0 + r < e[k];
+                l[k][r] = in ? v.gcol[b[k] + j0 + r] : -1;
+                more |= in;
+            }
+        if (!more) break;
+        T xv[kZPer][4], lv[kZPer][4];
+#pragma unroll
+        for (int k = 0; k < kZPer; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                xv[k][r] = l[k][r] >= 0 ? xr[l[k][r]] : (T)0;
+                lv[k][r] = l[k][r] >= 0 ? lr[l[k][r]] : (T)0;
+            }
+#pragma unroll
+        for (int k = 0; k < kZPer; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (l[k][r] >= 0) s[k] += copy_term(xv[k][r], lv[k][r], inv_rho);
+    }
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) out[k] = global_from_sum(s[k], ik[k], ck[k], inv_rho, lo[k], hi[k]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) z_kernel(View<T> v, int q) {
     const Ctl* ctl = v.ctl;
     if (ctl->iter + q >= ctl->max_iter) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.ng) return;
-    v.zg[i] = global_value<T, false>(v, i, v.xl, v.lam, (T)ctl->inv_rho);
+    int g[kZPer];
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) {
+        const int i = blockIdx.x * (kZThreads * kZPer) + k * kZThreads + threadIdx.x;
+        g[k] = i < v.ng ? i : -1;
+    }
+    if (g[0] < 0) return;
+    T z[kZPer];
+    global_values_batched<T>(v, g, (T)ctl->inv_rho, z);
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k)
+        if (g[k] >= 0) v.zg[g[k]] = z[k];
 }
 
 // Local + dual update of chunk b for iteration offset q of a graph body.
@@ -1287,62 +1352,6 @@ struct ZMap {
     int32_t inst, g0;
 };
 
-// Globals per thread of the batched global update, and its CTA count for
-// an instance of ng globals.
-constexpr int kZPer = 2;
-inline int zb_blocks(int ng) { return (ng + kZThreads * kZPer - 1) / (kZThreads * kZPer); }
-
-// Eq. (global_sparse) for kZPer globals g[k] of one instance (g[k] < 0:
-// none): the copy lists are read four entries at a time and all their x,
-// lambda loads are in flight together; each sum still adds the copies in
-// list order, so the result is that of global_value.
-template <typename T>
-__device__ __forceinline__ void global_values_batched(const View<T>& v, const int (&g)[kZPer], T inv_rho,
-                                                      T (&out)[kZPer]) {
-    int b[kZPer], e[kZPer];
-    T s[kZPer], lo[kZPer], hi[kZPer], ik[kZPer], ck[kZPer];
-#pragma unroll
-    for (int k = 0; k < kZPer; ++k) {
-        b[k] = g[k] >= 0 ? v.gptr[g[k]] : 0;
-        e[k] = g[k] >= 0 ? v.gptr[g[k] + 1] : 0;
-        lo[k] = g[k] >= 0 ? v.lo[g[k]] : (T)0;
-        hi[k] = g[k] >= 0 ? v.hi[g[k]] : (T)0;
-        ik[k] = g[k] >= 0 ? v.invk[g[k]] : (T)0;
-        ck[k] = g[k] >= 0 ? v.cik[g[k]] : (T)0;
-        s[k] = 0;
-    }
-    const T* xr = v.xl;
-    const T* lr = v.lam;
-    for (int j0 = 0;; j0 += 4) {
-        bool more = false;
-        int l[kZPer][4];
-#pragma unroll
-        for (int k = 0; k < kZPer; ++k)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const bool in = b[k] + j0 + r < e[k];
-                l[k][r] = in ? v.gcol[b[k] + j0 + r] : -1;
-                more |= in;
-            }
-        if (!more) break;
-        T xv[kZPer][4], lv[kZPer][4];
-#pragma unroll
-        for (int k = 0; k < kZPer; ++k)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                xv[k][r] = l[k][r] >= 0 ? xr[l[k][r]] : (T)0;
-                lv[k][r] = l[k][r] >= 0 ? lr[l[k][r]] : (T)0;
-            }
-#pragma unroll
-        for (int k = 0; k < kZPer; ++k)
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (l[k][r] >= 0) s[k] += copy_term(xv[k][r], lv[k][r], inv_rho);
-    }
-#pragma unroll
-    for (int k = 0; k < kZPer; ++k) out[k] = global_from_sum(s[k], ik[k], ck[k], inv_rho, lo[k], hi[k]);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) zb_kernel(const View<T>* views, const ZMap* zmap, int q) {
     const ZMap m = zmap[blockIdx.x];
@@ -1953,7 +1962,7 @@ void enqueue_iterations(opf_problem* p, int K, int form, cudaStream_t s, cudaGra
     const View<T>* dv = device_view<T>(p);
     const TileItem* di = static_cast<const TileItem*>(p->xt_items);
     for (int q = 0; q < K; ++q) {
-        z_kernel<T><<<zb, kZThreads, 0, s>>>(v, q);
+        z_kernel<T><<<zb_blocks(p->pk.ng), kZThreads, 0, s>>>(v, q);
         if (q < K - 1)
             xt_kernel<T><<<g.ntl + g.nchk, kXWarps * 32, kXtSmem, s>>>(dv, di, p->xt_nitems, g.ntl, 1, q);
         else
@@ -2178,7 +2187,6 @@ void sync_state_to(opf_problem* p, int prec, cudaStream_t s) {
 template <typename T>
 double time_graph(opf_problem* p, int which, int reps, cudaStream_t s) {
     View<T> v = view_of<T>(p, prec_of<T>(p));
-    const int zb = (p->pk.ng + kZThreads - 1) / kZThreads;
     const XtGrid xg = xt_grid<T>(p->xt_nitems, p->pk.nblocks);
     cudaStream_t cs;
     OPF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -2186,7 +2194,7 @@ double time_graph(opf_problem* p, int which, int reps, cudaStream_t s) {
     cudaGraphExec_t ge = nullptr;
     OPF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < reps; ++r) {
-        if (which == 0) z_kernel<T><<<zb, kZThreads, 0, cs>>>(v, 0);
+        if (which == 0) z_kernel<T><<<zb_blocks(p->pk.ng), kZThreads, 0, cs>>>(v, 0);
         else if (which == 1)
             xt_kernel<T><<<xg.ntl + xg.nchk, kXWarps * 32, kXtSmem, cs>>>(
                 device_view<T>(p), static_cast<const TileItem*>(p->xt_items), p->xt_nitems, xg.ntl, 1, 0);
