@@ -2537,10 +2537,14 @@ GraphEntry build_batch_graph(const View<T>* dviews, const CtaMap* dmap, const ZM
 // control blocks into pinned memory; B->done is recorded at the end.
 // Engine that OPF_ENGINE_AUTO runs for a batch: persistent when every
 // chunk fits co-resident, unless the chunks fit only with their iterate in
-// global memory and the batch's device data is larger than L2 -- then the
+// global memory and what one iteration touches in this precision (vectors,
+// index lists and the padded operators) is larger than L2 -- then the
 // operators stream from HBM and the graph engine (full occupancy, no
-// neighbour waits) is the faster one (256 feeders of 100-2500 buses on
-// B300: 824k vs 668k feeder-iterations/s).
+// neighbour waits, tile-parallel local update) is the faster one.  On B300,
+// feeders of 100-2500 buses, feeder-iterations/s persistent / graph: 16
+// feeders (37 MB per iteration) 1.10M / 0.56M, 32 (72 MB) 1.23M / 0.96M,
+// 64 (156 MB) 0.93M / 0.95M, 128 (312 MB) 0.88M / 1.17M, 256 (634 MB)
+// 0.67M / 1.21M.
 template <typename T>
 int batch_auto_engine(const opf_batch* B) {
     int nctas = 0;
@@ -2549,7 +2553,8 @@ int batch_auto_engine(const opf_batch* B) {
     for (opf_problem* p : B->probs) {
         nctas += p->pk.nblocks;
         cm.add(p->pk);
-        batch_bytes += layout_of(p).total;
+        const size_t nl = (size_t)p->pk.nl, ng = (size_t)p->pk.ng;
+        batch_bytes += sizeof(T) * (7 * nl + 6 * ng + (size_t)p->pk.mat_elems) + 4 * (2 * nl + ng);
     }
     const SmemPlan sp = smem_plan_of<T>(cm);
     const size_t gsmem = (size_t)std::max(1, cm.halo) * sizeof(T);
