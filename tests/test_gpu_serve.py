@@ -109,3 +109,35 @@ def test_admission_by_memory(opf):
     st = srv.stats()
     assert st["evicted"] >= 5 and st["resident_bytes"] <= budget
     srv.close()
+
+
+def test_served_fp64_matches_oracle(opf):
+    """Requests served in a mix (FP64, rho = 100, residuals checked every 50
+    iterations) stop where the FP64 oracle stops with the same check
+    interval, at the oracle's iterate (element-wise, 1e-9), and report its
+    objective.  Ties the server to the paper's Algorithm 1 directly, not only
+    through the solve alone."""
+    from oracle import admm as OA, model as OM, precompute as OP
+
+    def rel(a, b):
+        nb = float(np.linalg.norm(b))
+        d = a - b
+        scale = np.abs(b) + float(np.max(np.abs(b)))
+        return max(float(np.linalg.norm(d)) / nb, float(np.max(np.abs(d) / scale)))
+
+    fs = [F.feeder_13(1), F.feeder_123(2), F.feeder_tiny(5, 1)]
+    srv = opf.Server(precision=0, rho=100.0, max_iter=200000, check_every=50, round_iters=500)
+    ids = [srv.submit(fs[0]), srv.submit(fs[1])]
+    srv.step()
+    ids.append(srv.submit(fs[2]))
+    done = drain(srv, len(fs))
+    for k in (0, 2):
+        f, info = fs[k], done[ids[k]]
+        m = OM.build_feeder(f)
+        s = OA.ADMM(m, OP.precompute(m), 100.0)
+        o = s.run(200000, criterion=OA.CRIT_ABS, check_every=50)
+        assert info.status == opf.OK and info.iters == o["iters"], (k, info.iters, o["iters"])
+        xg, xl, lam = srv.problem(ids[k]).state()
+        assert rel(xg, s.x) <= 1e-9 and rel(xl, s.z) <= 1e-9, k
+        assert abs(info.objective - o["objective"]) <= 1e-9 * abs(o["objective"])
+    srv.close()
