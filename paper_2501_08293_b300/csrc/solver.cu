@@ -1429,54 +1429,33 @@ __device__ __forceinline__ bool stage_wait(unsigned long long* bar, unsigned ph)
     return false;
 }
 
-// One small or big tile's local and dual update without partials (Eq.
-// closed_2, Eq. ADMM-3); y from the staged block when `staged`.
+// A big tile's local and dual update without partials (Eq. closed_2, Eq.
+// ADMM-3): u staged in the warp's us, each lane's rows over the full
+// operator in global memory (the order of every engine).
 template <typename T>
-__device__ __forceinline__ void tile_plain(const View<T>* vp, const Tile& tl, int lane, T rho, T inv_rho,
-                                           const T* sbuf, bool staged, T* us) {
+__device__ __forceinline__ void tile_big_plain(const View<T>* vp, const Tile& tl, int lane, T rho, T inv_rho, T* us) {
     const T* zg = vp->zg;
     const int32_t* gidx = vp->gidx;
     T* xl = vp->xl;
     T* lam = vp->lam;
-    if (!tl.big) {
-        const int L = tl.L;
-        const bool act = lane < L;
-        const int j = tl.loc0 + lane;
-        int base = 0;
-        T vv = 0, lo = 0, bb = 0, u = 0;
-        if (act) {
-            base = (vp->meta[j] >> 24) & 0x1F;
-            vv = zg[gidx[j]];
-            lo = ldcg(lam + j);
-            bb = vp->bbar[j];
-            u = u_of(vv, lo, inv_rho);
-        }
-        const T y = tile_gemv(staged ? sbuf : vp->P + tl.mat0, L, lane, tl.nmax, base, u, act);
-        if (act) {
-            const T xn = y + bb;
-            xl[j] = xn;
-            lam[j] = dual_of(lo, rho, vv, xn);
-        }
-    } else {
-        const int n = tl.nmax;
-        for (int r = lane; r < n; r += 32) {
-            const int j = tl.loc0 + r;
-            us[r] = u_of(zg[gidx[j]], ldcg(lam + j), inv_rho);
-        }
-        __syncwarp();
-        const T* Pm = vp->P + tl.mat0;
-        for (int r = lane; r < n; r += 32) {
-            T y = 0;
-            for (int c = 0; c < n; ++c) y = fma(Pm[c * n + r], us[c], y);
-            const int j = tl.loc0 + r;
-            const T vv = zg[gidx[j]];
-            const T lo = ldcg(lam + j);
-            const T xn = y + vp->bbar[j];
-            xl[j] = xn;
-            lam[j] = dual_of(lo, rho, vv, xn);
-        }
-        __syncwarp();
+    const int n = tl.nmax;
+    for (int r = lane; r < n; r += 32) {
+        const int j = tl.loc0 + r;
+        us[r] = u_of(zg[gidx[j]], ldcg(lam + j), inv_rho);
     }
+    __syncwarp();
+    const T* Pm = vp->P + tl.mat0;
+    for (int r = lane; r < n; r += 32) {
+        T y = 0;
+        for (int c = 0; c < n; ++c) y = fma(Pm[c * n + r], us[c], y);
+        const int j = tl.loc0 + r;
+        const T vv = zg[gidx[j]];
+        const T lo = ldcg(lam + j);
+        const T xn = y + vp->bbar[j];
+        xl[j] = xn;
+        lam[j] = dual_of(lo, rho, vv, xn);
+    }
+    __syncwarp();
 }
 
 // Tile descriptor held by lane k of the warp, to every lane.
@@ -1607,7 +1586,7 @@ __global__ void __launch_bounds__(kXWarps * 32, sizeof(T) == 4 ? 4 : 3)
             const bool staged = stage_bytes<T>(cur) != 0;
             if (!staged) stage_issue<T>(P, nxt, buf, bar, lane);   // the buffer is free
             if (cur.big) {
-                tile_plain<T>(vp, cur, lane, rho, inv_rho, buf, false, us[warp]);
+                tile_big_plain<T>(vp, cur, lane, rho, inv_rho, us[warp]);
             } else if (cur.L > 0) {
                 const bool act = lane < cur.L;
                 const T u = u_of(cvv, clo, inv_rho);
