@@ -315,9 +315,8 @@ def run_ours(args):
     value = iters_all / tot
     ms_per_step = 1e3 * tot / args.steps
 
-    # algorithmic bytes of one iteration, each array touched once (the
-    # survey's per-iteration formula): w (7 Nl + 6 Ng) + w sum n_s^2 +
-    # 4 (2 Nl + Ng).  7 Nl: the global update reads x_s and lambda, the local
+    # algorithmic bytes of one iteration, each array touched once:
+    # w (7 Nl + 6 Ng) + w sum n_s^2 + 4 (2 Nl + Ng).  7 Nl: the global update reads x_s and lambda, the local
     # and dual updates read x_s(prev), lambda and bbar and write x_s and
     # lambda; 6 Ng: invk, cik, lo, hi read and x written by the global
     # update, x gathered once by the local update; int32: gidx and the CSR
@@ -792,7 +791,8 @@ def batch_problems(args, opf, F):
 
 def batch_kernel_bytes(probs, w):
     """Algorithmic bytes per iteration of the batched graph engine's two
-    kernels (the split of the survey's per-iteration formula): global update
+    kernels (the per-iteration formula w (7 Nl + 6 Ng) + w sum n_s^2 +
+    4 (2 Nl + Ng), split between them): global update
     reads x and lambda per copy, the copy list, the segment pointers and four
     per-global constants and writes z; local update reads the operators,
     bbar, lambda, the previous x, z per global and the gather index and

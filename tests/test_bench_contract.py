@@ -56,7 +56,7 @@ def test_no_cpu_fallback_without_a_gpu():
     assert not any(ln.strip().startswith("{") for ln in r.stdout.splitlines())
 
 
-def test_batch_kernel_bytes_split_the_survey_formula():
+def test_batch_kernel_bytes_split_the_iteration_formula():
     """The per-kernel byte counts of the batched graph engine add up to the
     per-iteration formula the batch line's roofline uses (host-only
     problems, no device needed)."""
