@@ -530,8 +530,9 @@ typedef struct opf_scenarios opf_scenarios;
 int32_t opf_scenarios_create(const opf_bus* buses, int32_t n_bus, const opf_line* lines, int32_t n_line,
                              const opf_gen* gens, int32_t n_gen, const opf_load* loads, int32_t n_load,
                              int32_t n_scenarios, opf_scenarios** out);
-/* params: precision must be OPF_FP32 and adaptive_rho 0; warm_start continues
- * every scenario from its current state.  infos: n_scenarios entries (may
+/* params: precision must be OPF_FP32, adaptive_rho 0 and check_every in
+ * [1, 4096] (the solve graph holds that many iterations of kernel nodes);
+ * warm_start continues every scenario from its current state.  infos: n_scenarios entries (may
  * be NULL); status per scenario as for opf_admm_solve.                     */
 int32_t opf_scenarios_solve(opf_scenarios* sc, const opf_params* params, void* stream, opf_info* infos);
 /* State of one scenario in the canonical orders (host, caller-owned; any

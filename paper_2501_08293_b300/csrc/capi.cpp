@@ -353,7 +353,7 @@ int32_t opf_profile_kernels(opf_problem* p, const opf_params* prm, int32_t reps,
         if (!p || !prm || !us) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
         if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "profile before upload");
         if (reps < 1 || reps > 100000) throw opf::Error(OPF_ERR_INVALID_ARG, "reps out of [1, 100000]");
-        if (!(prm->rho > 0.0)) throw opf::Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
+        if (!(prm->rho > 0.0) || !std::isfinite(prm->rho)) throw opf::Error(OPF_ERR_INVALID_ARG, "rho must be > 0");
         if (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) throw opf::Error(OPF_ERR_INVALID_ARG, "bad precision");
         opf::device_profile(p, *prm, reps, (cudaStream_t)stream, us);
         return OPF_OK;
@@ -365,7 +365,8 @@ int32_t opf_profile_persistent(opf_problem* p, const opf_params* prm, int32_t it
         if (!p || !prm || !out) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
         if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "profile before upload");
         if (iters < 1) throw opf::Error(OPF_ERR_INVALID_ARG, "iters must be >= 1");
-        if (!(prm->rho > 0.0) || (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) || prm->check_every < 1)
+        if (!(prm->rho > 0.0) || !std::isfinite(prm->rho) || (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) ||
+            prm->check_every < 1 || prm->check_every > 4096)
             throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
         opf::device_profile_persistent(p, *prm, iters, (cudaStream_t)stream, out, nullptr);
         return OPF_OK;
@@ -378,7 +379,8 @@ int32_t opf_profile_persistent_ctas(opf_problem* p, const opf_params* prm, int32
         if (!p || !prm || !per_cta) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
         if (!p->uploaded) throw opf::Error(OPF_ERR_STATE, "profile before upload");
         if (iters < 1) throw opf::Error(OPF_ERR_INVALID_ARG, "iters must be >= 1");
-        if (!(prm->rho > 0.0) || (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) || prm->check_every < 1)
+        if (!(prm->rho > 0.0) || !std::isfinite(prm->rho) || (prm->precision != OPF_FP64 && prm->precision != OPF_FP32) ||
+            prm->check_every < 1 || prm->check_every > 4096)
             throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
         double agg[8];
         opf::device_profile_persistent(p, *prm, iters, (cudaStream_t)stream, agg, per_cta);
@@ -586,8 +588,11 @@ int32_t opf_scenarios_solve(opf_scenarios* sc, const opf_params* prm, void* stre
         if (prm->adaptive_rho) throw opf::Error(OPF_ERR_INVALID_ARG, "scenarios: residual balancing not supported");
         if (prm->residual_form != OPF_RES_PAPER)
             throw opf::Error(OPF_ERR_INVALID_ARG, "scenarios: only the paper's residual form (OPF_RES_PAPER)");
-        if (!(prm->rho > 0.0) || prm->check_every < 1 || prm->max_iter < 0)
+        if (!(prm->rho > 0.0) || !std::isfinite(prm->rho) || prm->max_iter < 0)
             throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
+        // the solve graph's body holds check_every iterations of kernel nodes
+        if (prm->check_every < 1 || prm->check_every > 4096)
+            throw opf::Error(OPF_ERR_INVALID_ARG, "check_every out of [1, 4096]");
         opf::scenarios_solve(sc, *prm, (cudaStream_t)stream, infos);
         return OPF_OK;
     });
@@ -613,7 +618,8 @@ int32_t opf_scenarios_dims(const opf_scenarios* sc, int32_t* n_global, int32_t* 
 int32_t opf_scenarios_profile(opf_scenarios* sc, const opf_params* prm, int32_t reps, void* stream, double* us) {
     return guarded([&]() -> int32_t {
         if (!sc || !prm || !us) throw opf::Error(OPF_ERR_INVALID_ARG, "NULL argument");
-        if (reps < 1 || !(prm->rho > 0.0)) throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
+        if (reps < 1 || reps > 100000 || !(prm->rho > 0.0) || !std::isfinite(prm->rho))
+            throw opf::Error(OPF_ERR_INVALID_ARG, "bad parameters");
         opf::scenarios_profile(sc, *prm, reps, (cudaStream_t)stream, us);
         return OPF_OK;
     });

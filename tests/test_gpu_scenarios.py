@@ -117,6 +117,10 @@ def test_scenarios_reject_bad_input(opf):
     with pytest.raises(opf.OpfError):
         sc.solve(opf.default_params(precision=opf.FP64))
     with pytest.raises(opf.OpfError):
+        sc.solve(opf.default_params(precision=opf.FP32, check_every=4097))
+    with pytest.raises(opf.OpfError):
+        sc.solve(opf.default_params(precision=opf.FP32, rho=float("inf")))
+    with pytest.raises(opf.OpfError):
         sc.state(3)
     sc.close()
 
