@@ -576,7 +576,9 @@ void opf_scenarios_destroy(opf_scenarios* sc);
  * precompute (in submit) and uploads (in step, on a side stream) overlap the
  * round running on the device.  A request with warm_from = id of a finished
  * resident request starts from that feeder's iterate for every local copy
- * whose component and global variable are unchanged (a topology switch).
+ * whose component and global variable are unchanged (a topology switch);
+ * when the budget cannot hold both and nothing else is active or
+ * evictable, the source is evicted and the request starts cold.
  * Rounds are whole multiples of params.check_every and all engines compute
  * bit-identical iterates, so a request's result does not depend on the mix.
  * Not thread-safe across steps; submit may be called between steps.        */

@@ -10,7 +10,9 @@
 //      stays resident for warm starts until memory is needed;
 //   2. admit queued requests in arrival order while a slot, the device
 //      memory budget and the co-resident chunk capacity allow (finished
-//      instances are evicted least recently used first); uploads run on a
+//      instances are evicted least recently used first; a request's own
+//      warm-start source last, and only when nothing is active, in which
+//      case it starts cold); uploads run on a
 //      side stream, overlapping the round still queued on the main stream;
 //      a request that modifies a resident feeder (warm_from) starts from
 //      that feeder's iterate, copied on the device for every local copy
@@ -153,7 +155,15 @@ bool admit(opf_server* S, Request& r) {
             Request& q = kv.second;
             if (q.state == REQ_DONE && q.resident && q.id != r.warm_from && (!lru || q.last_use < lru->last_use)) lru = &q;
         }
-        if (!lru) return false;
+        if (!lru) {
+            // only the warm-start source is left to evict; with no instance
+            // active nothing else will free memory, so the request gives up
+            // its warm start (cold start below) instead of waiting forever
+            auto src = S->reqs.find(r.warm_from);
+            if (!S->active.empty() || src == S->reqs.end() || !src->second.resident) return false;
+            evict(S, src->second);
+            continue;
+        }
         evict(S, *lru);
     }
     opf::device_upload(r.p, nullptr, 0, S->upload);

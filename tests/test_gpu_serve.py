@@ -111,6 +111,32 @@ def test_admission_by_memory(opf):
     srv.close()
 
 
+def test_warm_start_source_evicted_when_budget_holds_one(opf):
+    """A warm-start request whose source feeder and itself do not fit the
+    memory budget together, with nothing else active: the source is evicted
+    and the request runs cold to convergence instead of waiting for memory
+    that nothing would free."""
+    f = F.feeder_123(1)
+    g = F.reconfigure(f, np.random.default_rng(3))
+    nch = chunks_for(f)
+    bf = opf.Problem.from_feeder(f, chunks=nch, upload=False).dims.device_bytes
+    bg = opf.Problem.from_feeder(g, chunks=nch, upload=False).dims.device_bytes
+    budget = max(bf, bg) + min(bf, bg) // 2
+    srv = opf.Server(device_budget_bytes=budget, precision=1, rho=10.0, max_iter=200000, check_every=50,
+                     round_iters=500)
+    a = srv.submit(f, chunks=nch)
+    assert drain(srv, 1)[a].status == opf.OK
+    b = srv.submit(g, warm_from=a, chunks=nch)
+    info = drain(srv, 1, max_steps=2000)[b]
+    alone = opf.Problem.from_feeder(g, chunks=nch)
+    ref = alone.solve(opf.default_params(precision=1, rho=10.0, max_iter=200000, check_every=50))
+    st = srv.stats()
+    assert info.status == opf.OK and info.iters == ref.iters
+    assert st["warm_started"] == 0 and st["evicted"] >= 1 and st["resident_bytes"] <= budget
+    alone.close()
+    srv.close()
+
+
 def test_served_fp64_matches_oracle(opf):
     """Requests served in a mix (FP64, rho = 100, residuals checked every 50
     iterations) stop where the FP64 oracle stops with the same check
