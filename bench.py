@@ -380,7 +380,9 @@ def run_ours(args):
         # small per-iteration term, extrapolated to this launch's iterations
         traffic = TRAFFIC_STAGING_B + TRAFFIC_PER_ITER_B * (iters / args.steps)
         traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                        "extrapolated from 2000- and 20000-iteration captures of the same kernel")
+                        "extrapolated from 2000- and 20000-iteration captures of the same kernel with a residual "
+                        "check every 50 iterations (an upper bound at a longer check interval: the per-iteration "
+                        "term includes the snapshot writes of the checks)")
     if persistent:
         # the whole solve is one launch of persistent_kernel: its duration is
         # the event-timed solve; bytes = iterations x bytes per iteration
