@@ -266,9 +266,9 @@ int32_t opf_tuning_lookup(int32_t n_bus, int32_t* work_per_chunk, int32_t* max_c
 
 /* New parameters for in-service lines of an uploaded problem: records[k]
  * replaces line line_idx[k] (impedances r, x; shunts; taps; flow bounds).
- * Ends, phases and the service state must not change (a topology change
- * needs a new problem, see opf_server_submit's warm start), else
- * OPF_ERR_INVALID_ARG before anything changes.  The touched components'
+ * Ends, phases and the service state must not change (a switch in or out
+ * of service is opf_set_line_status), else OPF_ERR_INVALID_ARG before
+ * anything changes.  The touched components'
  * operators of Eq. (closed_2) are recomputed on the device in FP64
  * (Cholesky of A_s A_s^T; the rows of a line are of full rank) and written
  * into both precisions; the iterate and duals are kept, so a following
